@@ -1,0 +1,467 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test names the part of the oracle it pins and the reason a plausible slip
+(dropped term, wrong sign, wrong index, transposed operand) would fail it.
+CPU only.
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+import ile_synth as S
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_lib):
+    return oracle_lib
+
+
+def _grid_time(p, j):
+    return p.t_lo + j * (p.t_hi - p.t_lo) / (p.n_t - 1)
+
+
+def _regrid(p, t0):
+    """Same data, Q re-evaluated (by definition) on grids starting at t0[k]."""
+    q = copy.copy(p)
+    q.q_t0 = np.asarray(t0, float)
+    wf = p.meta["waveforms"]
+    rng = np.random.default_rng(p.meta["seed"] + 7919)
+    Q = np.zeros_like(p.Q)
+    data = []
+    for k in range(p.n_det):
+        d = wf.strain(p.meta["a_true"][k], p.meta["t_true"] + p.meta["dt_true"][k])
+        if p.meta["noise"]:
+            d = d + wf.noise(k, rng)
+        data.append(d)
+        Q[k] = wf.overlap_series(k, d, q.q_t0[k] + np.arange(p.n_q) / p.fs)
+    q.Q = Q
+    return q, data
+
+
+# ---- P6: spin-weighted harmonics ---------------------------------------------------------
+
+@pytest.mark.parametrize("iota,phi", [(0.3, 0.1), (1.2, -2.0), (2.9, 4.0), (0.0, 0.5), (math.pi, 1.0)])
+def test_p6_l2_closed_forms(orc, iota, phi):
+    """-2Y_2m against the textbook closed forms (a wrong factorial, power or
+    sign in the Wigner-d sum fails at least one m)."""
+    c, s = math.cos(iota), math.sin(iota)
+    exp = {
+        2: math.sqrt(5 / (64 * math.pi)) * (1 + c) ** 2,
+        1: math.sqrt(5 / (16 * math.pi)) * s * (1 + c),
+        0: math.sqrt(15 / (32 * math.pi)) * s * s,
+        -1: math.sqrt(5 / (16 * math.pi)) * s * (1 - c),
+        -2: math.sqrt(5 / (64 * math.pi)) * (1 - c) ** 2,
+    }
+    for m, a in exp.items():
+        assert abs(orc.sYlm(2, m, iota, phi) - a * np.exp(1j * m * phi)) < 1e-14
+
+
+def test_p6_orthonormality(orc):
+    """Integral of Y_lm conj(Y_l'm') over the sphere is the identity for all
+    21 modes with 2 <= l <= 4 (Gauss-Legendre in cos(theta) x uniform phi)."""
+    x, w = np.polynomial.legendre.leggauss(24)
+    nphi = 16
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    modes = S.MODE_ORDER
+    Y = np.array([[[orc.sYlm(l, m, math.acos(xx), ph) for ph in phis] for xx in x] for (l, m) in modes])
+    G = np.einsum("aij,bij,i->ab", Y, np.conj(Y), w) * (2 * np.pi / nphi)
+    assert np.max(np.abs(G - np.eye(len(modes)))) < 1e-12
+
+
+def test_p6_reflection_symmetry(orc):
+    """-2Y_l,-m(theta, phi) = (-1)^l conj(-2Y_lm(pi - theta, phi)) for l <= 4:
+    the reflection identity of the Wigner-d functions (checked against the
+    l = 2 closed forms above), which fails for a wrong sign of k or m in the sum."""
+    for l in (2, 3, 4):
+        for m in range(-l, l + 1):
+            for iota in (0.4, 1.9):
+                lhs = orc.sYlm(l, -m, iota, 0.7)
+                rhs = (-1) ** l * np.conj(orc.sYlm(l, m, math.pi - iota, 0.7))
+                assert abs(lhs - rhs) < 1e-14
+
+
+# ---- P7 / P8: detector response and delays ---------------------------------------------
+
+def test_p7_response_thorne_closed_form(orc):
+    """Arms along x and y, gmst = 0: F_+ and F_x against the detector-frame
+    closed forms with source polar angle th = pi/2 - delta and azimuth alpha:
+      F_+ = 1/2 (1 + cos^2 th) cos 2a cos 2psi - cos th sin 2a sin 2psi
+      F_x = 1/2 (1 + cos^2 th) cos 2a sin 2psi + cos th sin 2a cos 2psi
+    The sky basis used here measures psi from the other axis and in the other
+    sense, so the textbook angle is pi/2 - psi; with that map both components
+    agree exactly (a wrong basis vector or a sign in F_x breaks it)."""
+    D = 0.5 * (np.outer([1, 0, 0], [1, 0, 0]) - np.outer([0, 1, 0], [0, 1, 0]))
+    rng = np.random.default_rng(4)
+    for _ in range(50):
+        a, d, psi = rng.uniform(0, 2 * np.pi), rng.uniform(-1.5, 1.5), rng.uniform(0, np.pi)
+        th = math.pi / 2 - d
+        fp, fx = orc.antenna(D, a, d, psi, 0.0)
+        p = math.pi / 2 - psi
+        ep = 0.5 * (1 + math.cos(th) ** 2) * math.cos(2 * a) * math.cos(2 * p) - math.cos(th) * math.sin(2 * a) * math.sin(2 * p)
+        ex = 0.5 * (1 + math.cos(th) ** 2) * math.cos(2 * a) * math.sin(2 * p) + math.cos(th) * math.sin(2 * a) * math.cos(2 * p)
+        assert abs(fp - ep) < 1e-13 and abs(fx - ex) < 1e-13
+
+
+def test_p7_response_invariants(orc):
+    """|F|^2 is psi-independent; F(psi + pi/2) = -F(psi); the wave is
+    transverse (D = s s^T gives F = 0)."""
+    tens, _ = S.detector_geometry("L1")
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        a, d, g = rng.uniform(0, 2 * np.pi), rng.uniform(-1.5, 1.5), rng.uniform(0, 2 * np.pi)
+        vals = [orc.antenna(tens, a, d, psi, g) for psi in (0.1, 0.8, 2.5)]
+        n2 = [x * x + y * y for x, y in vals]
+        assert max(n2) - min(n2) < 1e-14
+        f0 = orc.antenna(tens, a, d, 0.3, g)
+        f1 = orc.antenna(tens, a, d, 0.3 + math.pi / 2, g)
+        assert abs(f0[0] + f1[0]) < 1e-14 and abs(f0[1] + f1[1]) < 1e-14
+        s = np.array([math.cos(d) * math.cos(a - g), math.cos(d) * math.sin(a - g), math.sin(d)])
+        fz = orc.antenna(np.outer(s, s), a, d, 0.3, g)
+        assert abs(fz[0]) < 1e-14 and abs(fz[1]) < 1e-14
+
+
+def test_p8_delay_bounds(orc):
+    """|dt_k - dt_k'| <= |x_k - x_k'|/c, with equality along the baseline; a
+    source over a detector's vertex arrives |x|/c before the geocentre."""
+    _, xh = S.detector_geometry("H1")
+    _, xl = S.detector_geometry("L1")
+    base = np.linalg.norm(xh - xl) / S.C_SI
+    rng = np.random.default_rng(6)
+    for _ in range(200):
+        a, d = rng.uniform(0, 2 * np.pi), math.asin(rng.uniform(-1, 1))
+        assert abs(orc.delay(xh, a, d, 0.4) - orc.delay(xl, a, d, 0.4)) <= base * (1 + 1e-12)
+    b = (xh - xl) / np.linalg.norm(xh - xl)
+    d, a = math.asin(b[2]), math.atan2(b[1], b[0]) + 0.4
+    assert abs((orc.delay(xl, a, d, 0.4) - orc.delay(xh, a, d, 0.4)) - base) < 1e-15
+    u = xh / np.linalg.norm(xh)
+    assert abs(orc.delay(xh, math.atan2(u[1], u[0]) + 0.4, math.asin(u[2]), 0.4)
+               + np.linalg.norm(xh) / S.C_SI) < 1e-15
+
+
+# ---- the decomposed likelihood vs the direct strain likelihood ---------------------------
+
+def test_p5_decomposition_equals_direct_strain_likelihood(orc):
+    """At a bin whose detector arrival times fall on Q samples, the oracle's
+    ln L (Eq. def:lnL:Decomposed with kappa = 1/4) equals
+    sum_k <h_k|d_k> - 1/2 <h_k|h_k> with h_k = Re sum_lm c_k,lm h_lm computed
+    straight from the frequency-domain waveforms.  A wrong conjugate, a missing
+    Re, V vs conj(V), the 1/4, or a transposed U all break this identity."""
+    p = S.make_problem(("H1", "L1", "V1"), 9, 4096.0, n_t=401, snr=15.0, noise=True, seed=3)
+    wf = p.meta["waveforms"]
+    th = S.prior_samples(4, 11)
+    _, _, c, dt = orc.coeffs(p, th)
+    for i in range(4):
+        j = 50 + 70 * i
+        tj = _grid_time(p, j)
+        q, data = _regrid(p, [tj + dt[i, k] - 300 / p.fs for k in range(3)])
+        _, bins, _ = orc.lnL(q, th[i:i + 1], want_bins=True)
+        exp = 0.0
+        for k in range(3):
+            h = wf.strain(c[i, k], tj + dt[i, k])
+            exp += np.real(wf.inner(k, h, data[k])) - 0.5 * np.real(wf.inner(k, h, h))
+        assert abs(bins[0, j] - exp) < 1e-11 * max(1.0, abs(exp))
+
+
+def _realisable(orc, snr=20.0, noise=False, seed=21, n_modes=9):
+    """A noise-free injection generated from F_k Y_lm at theta_true, with Q
+    grids aligned so that t_true + dt_k falls on a Q sample."""
+    th_true = np.array([1.1, 0.4, 0.7, 2.1, 1.0, 400.0])
+    probe = S.make_problem(("H1", "L1", "V1"), n_modes, 4096.0, n_t=401, snr=snr, noise=noise, seed=seed)
+    F, Y, _, dt = orc.coeffs(probe, th_true)
+    a0 = np.outer(F[0], Y[0])
+    j_true = 200
+    t_true = _grid_time(probe, j_true)
+    t0 = [t_true + dt[0, k] - 400 / probe.fs for k in range(3)]
+    p = S.make_problem(("H1", "L1", "V1"), n_modes, 4096.0, n_t=401, snr=snr, noise=noise, seed=seed,
+                       a0=a0, dt_true=dt[0], t_true=t_true, d_true=th_true[5], gmst=probe.gmst, q_t0=t0)
+    return p, th_true, j_true
+
+
+def test_p5_injection_peak_is_half_rho_squared(orc):
+    """Noise-free consistent injection: ln L(theta_true, t_true) = rho^2/2
+    exactly, and theta_true is a local maximum."""
+    p, th_true, j = _realisable(orc)
+    _, bins, _ = orc.lnL(p, th_true, want_bins=True)
+    assert abs(bins[0, j] - 0.5 * p.meta["snr"] ** 2) < 1e-10 * p.meta["snr"] ** 2
+    assert np.argmax(bins[0]) == j
+    rng = np.random.default_rng(3)
+    pert = th_true + rng.normal(0, 1e-3, (64, 6)) * np.array([1, 1, 1, 1, 1, 100.0])
+    _, bp, _ = orc.lnL(p, pert, want_bins=True)
+    assert np.all(bp[:, j] < bins[0, j])
+
+
+def test_p4_quadratic_in_inverse_distance(orc):
+    """ln L_j(x) with x = D_ref/D is exactly A x - B x^2, so its maximum sits at
+    x* = A / 2B; a 3-point fit with a free constant returns C = 0 and predicts
+    a 4th distance."""
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(3, 8)
+    for i in range(3):
+        xs, vals = [], []
+        for D in (150.0, 300.0, 600.0, 900.0):
+            t = th[i].copy()
+            t[5] = D
+            _, b, _ = orc.lnL(p, t, want_bins=True)
+            xs.append(p.d_ref / D)
+            vals.append(b[0])
+        xs, vals = np.array(xs), np.array(vals)
+        A = np.stack([xs[:3], -xs[:3] ** 2, np.ones(3)], 1)
+        sol = np.linalg.solve(A, vals[:3])
+        assert np.max(np.abs(sol[2])) < 1e-9 * np.max(np.abs(vals))
+        pred = sol[0] * xs[3] - sol[1] * xs[3] ** 2
+        assert np.max(np.abs(pred - vals[3])) < 1e-9 * np.max(np.abs(vals))
+        assert np.all(sol[1] > 0)
+
+
+# ---- P1 / P2 / P3: symmetries and the template term --------------------------------------
+
+def test_p1_psi_plus_pi(orc):
+    p = S.single_large_problem()
+    th = S.prior_samples(20, 9)
+    a = orc.lnL(p, th)
+    t2 = th.copy()
+    t2[:, 2] += math.pi
+    assert np.max(np.abs(orc.lnL(p, t2) - a)) < 1e-11 * max(1, np.max(np.abs(a)))
+
+
+def test_p2_quadrupole_phase_symmetries(orc):
+    """(2,+-2) only: phi -> phi + pi leaves ln L unchanged, and so does
+    (psi, phi) -> (psi + pi/2, phi + pi/2) (F -> -F, Y_2+-2 -> -Y_2+-2).
+    With odd-m modes present phi -> phi + pi must change ln L."""
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(20, 10)
+    a = orc.lnL(p, th)
+    t2 = th.copy()
+    t2[:, 3] += math.pi
+    assert np.max(np.abs(orc.lnL(p, t2) - a)) < 1e-11 * np.max(np.abs(a))
+    t3 = th.copy()
+    t3[:, 2] += math.pi / 2
+    t3[:, 3] += math.pi / 2
+    assert np.max(np.abs(orc.lnL(p, t3) - a)) < 1e-11 * np.max(np.abs(a))
+    p3 = S.make_problem(("H1", "L1"), 4, 4096.0, seed=12)
+    b = orc.lnL(p3, th)
+    assert np.max(np.abs(orc.lnL(p3, t2) - b)) > 1e-3
+
+
+def test_p3_gram_inputs_and_nonnegative_template(orc):
+    """U Hermitian, V symmetric; the template term is real and >= 0 for every
+    sample (with Q = 0, ln L_j = -quad <= 0 at every bin)."""
+    p = S.single_large_problem()
+    for k in range(p.n_det):
+        assert np.max(np.abs(p.U[k] - p.U[k].conj().T)) < 1e-12 * np.max(np.abs(p.U[k]))
+        assert np.max(np.abs(p.V[k] - p.V[k].T)) < 1e-12 * np.max(np.abs(p.V[k]))
+    z = copy.copy(p)
+    z.Q = np.zeros_like(p.Q)
+    th = S.prior_samples(200, 13)
+    ll, bins, quad = orc.lnL(z, th, want_bins=True)
+    assert np.all(quad >= 0)
+    assert np.all(np.abs(bins + quad[:, None]) == 0)
+
+
+def test_template_term_equals_half_signal_norm(orc):
+    """quad(c) = 1/2 sum_k <h_k|h_k> for h_k = Re sum c h_lm, from waveforms."""
+    p = S.make_problem(("H1", "L1", "V1"), 21, 4096.0, snr=10.0, seed=14)
+    wf = p.meta["waveforms"]
+    th = S.prior_samples(5, 15)
+    _, _, c, _ = orc.coeffs(p, th)
+    _, _, quad = orc.lnL(p, th, want_bins=True)
+    for i in range(5):
+        exp = sum(0.5 * np.real(wf.inner(k, wf.strain(c[i, k]), wf.strain(c[i, k]))) for k in range(3))
+        assert abs(quad[i] - exp) < 1e-11 * exp
+
+
+def test_quad_norm_half_matches_quarter_with_rescaled_grams(orc):
+    """The 1/2 normalisation with (U, V)/2 reproduces the paper's 1/4 form."""
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(10, 16)
+    a = orc.lnL(p, th)
+    h = copy.copy(p)
+    h.quad_norm = 1
+    h.U = p.U / 2
+    h.V = p.V / 2
+    assert np.max(np.abs(orc.lnL(h, th) - a)) < 1e-11 * np.max(np.abs(a))
+
+
+# ---- P11 / P12: time marginalisation and interpolation ----------------------------------
+
+def test_p12_interpolation_exact_for_linear_q(orc):
+    """Q linear in time is reproduced exactly by the interpolation at any
+    shifted time; the shift itself comes from the oracle's delays."""
+    p = copy.copy(S.make_problem(("H1", "L1"), 3, 4096.0, seed=17))
+    rng = np.random.default_rng(1)
+    A = rng.normal(size=(2, 3)) + 1j * rng.normal(size=(2, 3))
+    Bc = rng.normal(size=(2, 3)) + 1j * rng.normal(size=(2, 3))
+    ts = [p.q_t0[k] + np.arange(p.n_q) / p.fs for k in range(2)]
+    p.Q = np.stack([A[k][:, None] + Bc[k][:, None] * ts[k][None, :] for k in range(2)])
+    p.U = np.zeros_like(p.U)
+    p.V = np.zeros_like(p.V)
+    th = S.prior_samples(5, 18)
+    _, _, c, dt = orc.coeffs(p, th)
+    _, bins, _ = orc.lnL(p, th, want_bins=True)
+    tj = p.t_lo + np.arange(p.n_t) * (p.t_hi - p.t_lo) / (p.n_t - 1)
+    for i in range(5):
+        exp = sum(np.real(np.sum(np.conj(c[i, k])[:, None] * (A[k][:, None] + Bc[k][:, None] * (tj + dt[i, k])[None, :]), 0))
+                  for k in range(2))
+        assert np.max(np.abs(bins[i] - exp)) < 1e-10
+
+
+def test_p11_lse_no_overflow_and_shift(orc):
+    """A loud signal (ln L ~ 1e4) does not overflow, and ln L_tmarg equals the
+    log of the bin mean; adding C to every ln w shifts ln Z by C and leaves
+    n_eff, n_ESS unchanged."""
+    p = copy.copy(S.plain_fp64_problem())
+    p.Q = p.Q * 50.0
+    p.U = p.U * 50.0
+    p.V = p.V * 50.0
+    th = S.prior_samples(50, 19)
+    ll, bins, _ = orc.lnL(p, th, want_bins=True)
+    assert np.all(np.isfinite(ll)) and np.max(ll) > 3000
+    mx = bins.max(1)
+    ref = mx + np.log(np.mean(np.exp(bins - mx[:, None]), 1))
+    assert np.max(np.abs(ll - ref)) < 1e-9 * np.max(np.abs(ll))
+    lnw = np.random.default_rng(2).normal(0, 3, 1000)
+    r0, r1 = orc.reduce(lnw), orc.reduce(lnw + 1234.5)
+    assert abs(r1["lnZ"] - r0["lnZ"] - 1234.5) < 1e-9
+    assert abs(r1["n_eff"] - r0["n_eff"]) < 1e-9 * r0["n_eff"]
+    assert abs(r1["n_ess"] - r0["n_ess"]) < 1e-9 * r0["n_ess"]
+
+
+def test_reduce_definitions_brute_force(orc):
+    """ln Z, n_eff, n_ESS, sigma against their definitions in long double via
+    math.fsum on small samples (no max-subtraction)."""
+    lnw = np.random.default_rng(3).normal(0, 1, 500)
+    r = orc.reduce(lnw)
+    w = np.exp(lnw)
+    s1, s2 = math.fsum(w), math.fsum(w * w)
+    assert abs(r["lnZ"] - math.log(s1 / 500)) < 1e-12
+    assert abs(r["n_eff"] - s1 / w.max()) < 1e-10 * r["n_eff"]
+    assert abs(r["n_ess"] - s1 * s1 / s2) < 1e-10 * r["n_ess"]
+    assert abs(r["sigma_lnZ"] - math.sqrt(s2 / s1 ** 2 - 1 / 500)) < 1e-10
+
+
+def test_window_violation_is_an_error(orc):
+    p = copy.copy(S.plain_fp64_problem())
+    p.q_t0 = np.array([-0.06, -0.1])
+    with pytest.raises(ValueError):
+        orc.lnL(p, S.prior_samples(200, 1))
+
+
+# ---- P9 / P10 / P13 / P14: sampler and estimator ---------------------------------------
+
+def load_philox_kat():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            w = [int(x, 16) for x in line.split()]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_p14_philox_known_answers(orc):
+    """Philox4x32-10 known-answer values published with the generator."""
+    kat = load_philox_kat()
+    assert len(kat) == 3
+    for ctr, key, out in kat:
+        assert list(orc.philox4x32_10(ctr, key)) == out
+
+
+def test_p13_uniform_histogram_draws_the_prior(orc):
+    """Iteration 0 (uniform masses) draws the isotropic prior exactly, with
+    ln p - ln p_s = 0; Kolmogorov-Smirnov against each 1-D prior CDF."""
+    from scipy import stats
+    sm = orc.Sampler(n_bins=32, seed=77)
+    th, lr, bins = sm.draw(40000)
+    assert np.all(lr == 0)
+    cdfs = [lambda a: a / (2 * np.pi), lambda d: (np.sin(d) + 1) / 2, lambda s: s / np.pi,
+            lambda f: f / (2 * np.pi), lambda i: (1 - np.cos(i)) / 2,
+            lambda D: (D ** 3 - 100.0 ** 3) / (1000.0 ** 3 - 100.0 ** 3)]
+    for d in range(6):
+        assert stats.kstest(th[:, d], cdfs[d]).pvalue > 1e-3
+    assert np.all(bins >= 0) and np.all(bins < 32)
+
+
+def test_p13_histogram_density_and_weights(orc):
+    """A non-uniform histogram: bin occupancy follows its masses (chi-square)
+    and ln p - ln p_s = -sum_d ln(B P_d[b_d])."""
+    from scipy import stats
+    sm = orc.Sampler(n_bins=16, seed=78)
+    rng = np.random.default_rng(0)
+    sm.P = rng.uniform(0.2, 2.0, (6, 16))
+    sm.P /= sm.P.sum(1, keepdims=True)
+    n = 60000
+    th, lr, bins = sm.draw(n)
+    for d in range(6):
+        cnt = np.bincount(bins[:, d], minlength=16)
+        assert stats.chisquare(cnt, n * sm.P[d]).pvalue > 1e-4
+    exp = -np.sum(np.log(16 * sm.P[np.arange(6)[None, :], bins]), 1)
+    assert np.max(np.abs(lr - exp)) < 1e-12
+    # the draw's v within the chosen bin: alpha = 2 pi v must sit inside bin b
+    v = th[:, 0] / (2 * np.pi)
+    assert np.all(np.floor(v * 16) == bins[:, 0])
+
+
+def test_p13_adapt_converges_to_binned_target(orc):
+    """Adapting on an analytic Gaussian weight in one unit coordinate moves
+    that dimension's P_d to (1-eps) x the target's binned mass + eps/B and
+    leaves the other dimensions near uniform (MC error ~1e-3)."""
+    from scipy import stats
+    n = 300000
+    base = orc.Sampler(n_bins=20, seed=79, floor=0.1)
+    th, lr, bins = base.draw(n)
+    v = np.stack([th[:, 0] / (2 * np.pi), (np.sin(th[:, 1]) + 1) / 2, th[:, 2] / np.pi, th[:, 3] / (2 * np.pi),
+                  (1 - np.cos(th[:, 4])) / 2, (th[:, 5] ** 3 - 1e6) / (1e9 - 1e6)], 1)
+    mu, sd = 0.37, 0.12
+    edges = np.linspace(0, 1, 21)
+    mass = np.diff(stats.norm.cdf(edges, mu, sd))
+    mass /= mass.sum()
+    target = 0.9 * mass + 0.1 / 20
+    for d in range(6):
+        sm = orc.Sampler(n_bins=20, seed=79, floor=0.1)
+        sm.adapt(bins, -0.5 * ((v[:, d] - mu) / sd) ** 2 + lr)
+        assert np.max(np.abs(sm.P[d] - target)) < 0.006
+        others = np.delete(np.arange(6), d)
+        assert np.max(np.abs(sm.P[others] - 0.05)) < 0.006
+
+
+def test_p9_zero_signal(orc):
+    """Q = U = V = 0: ln L_tmarg = 0 exactly; with p_s = p, ln Z = 0 and
+    n_eff = n_ESS = N; with an adapted p_s, ln Z = ln mean(p/p_s) -> 0 within 4 sigma."""
+    p = S.zero_problem(S.plain_fp64_problem())
+    sm = orc.Sampler(n_bins=16, seed=80)
+    res = orc.run_adapt(p, sm, 1, 5000, adapt_last=False)
+    it = res["iterations"][0]
+    assert np.all(res["lnL"][0] == 0.0)
+    assert it["lnZ"] == 0.0 and it["n_eff"] == 5000 and it["n_ess"] == 5000
+    sm.P = np.random.default_rng(1).uniform(0.3, 3, (6, 16))
+    sm.P /= sm.P.sum(1, keepdims=True)
+    res = orc.run_adapt(p, sm, 1, 20000)
+    it = res["iterations"][0]
+    assert abs(it["lnZ"]) < 4 * it["sigma_lnZ"] + 1e-12
+
+
+@pytest.mark.slow
+def test_p10_mc_matches_quadrature(orc):
+    """Tiny problem (1 detector, modes (2,+-2), 101 bins, SNR 4): the Monte
+    Carlo ln Z, before and after one adaptation, agrees with a 6-D
+    Gauss-Legendre product quadrature over the unit cube of prior CDF
+    coordinates within 4 sigma (plus the quadrature's own error)."""
+    p = S.make_problem(("H1",), 2, 4096.0, n_t=101, snr=4.0, noise=False, seed=23)
+    npts = 7
+    x, w = np.polynomial.legendre.leggauss(npts)
+    x, w = 0.5 * (x + 1), 0.5 * w
+    grids = np.meshgrid(*([x] * 6), indexing="ij")
+    v = np.stack([g.ravel() for g in grids], 1)
+    wt = np.prod(np.stack(np.meshgrid(*([w] * 6), indexing="ij")), 0).ravel()
+    th = np.stack([2 * np.pi * v[:, 0], np.arcsin(2 * v[:, 1] - 1), np.pi * v[:, 2], 2 * np.pi * v[:, 3],
+                   np.arccos(1 - 2 * v[:, 4]), np.cbrt(1e6 + v[:, 5] * (1e9 - 1e6))], 1)
+    ll = orc.lnL(p, th)
+    mx = ll.max()
+    lnZ_q = mx + math.log(np.sum(wt * np.exp(ll - mx)))
+    sm = orc.Sampler(n_bins=16, seed=81)
+    res = orc.run_adapt(p, sm, 2, 200000)
+    for it in res["iterations"]:
+        assert abs(it["lnZ"] - lnZ_q) < 4 * it["sigma_lnZ"] + 2e-3
