@@ -1,0 +1,198 @@
+/*
+ * rift_ile.h - C ABI of the GB300 (sm_103a) library for the extrinsic-marginalised
+ * likelihood integral (ILE) of arXiv:2505.11655 ("Narrowing RIFT").
+ *
+ * For one intrinsic point the library takes the per-detector mode overlaps
+ * Q_k,lm(t) and the Gram matrices U_k, V_k (Sec. II A, Eq. (QUV)) and, for
+ * extrinsic samples theta = (alpha, delta, psi, phi, iota, D), evaluates
+ *
+ *   ln L(theta, t) = (D_ref/D) Re sum_k sum_lm conj(F_k Y_lm) Q_k,lm(t + dt_k)
+ *                    - kappa (D_ref/D)^2 sum_k sum_lm,l'm' [ |F_k|^2 conj(Y_lm) Y_l'm' U_k
+ *                                                           + Re(F_k^2 Y_lm Y_l'm' V_k) ]
+ *   (Sec. II A, Eq. (def:lnL:Decomposed); kappa = 1/4 as printed),
+ *
+ * marginalises it over a uniform grid of geocentric times (App. timing: every
+ * evaluation is time marginalised), and reduces exp(ln L) p/p_s over samples
+ * to ln Z, n_eff and n_ESS (Sec. II B Eq. (lnL:MonteCarlo); Sec. II C
+ * Eq. (neff); Sec. IV A).  Samples come from a product-form adaptive
+ * histogram sampling prior kept on the device (Sec. II B, "adaptive
+ * Cartesian" integrator).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status: RIFT_OK (0) or a negative RIFT_E* code.
+ *     No C++ exception crosses this boundary.  rift_ile_strerror() names a code.
+ *   - A handle is used by one host thread at a time.  Its work is ordered on the
+ *     CUDA stream given at creation (NULL = the legacy default stream).
+ *   - Pointers tagged with a `mem` argument are host memory (RIFT_MEM_HOST) or
+ *     device memory of the handle's GPU (RIFT_MEM_DEVICE).  The caller owns them
+ *     and keeps them valid until the call returns; calls with device outputs
+ *     return after the results are written (they synchronise the stream).
+ *   - Complex arrays are interleaved (re, im) float64 pairs ("complex128").
+ *   - The handle owns every device buffer it allocates; rift_ile_destroy frees them.
+ */
+#ifndef RIFT_ILE_H
+#define RIFT_ILE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define RIFT_OK 0
+#define RIFT_EINVAL -1     /* invalid argument, size or configuration                          */
+#define RIFT_ENOMEM -2     /* device or host allocation failed                                  */
+#define RIFT_ECUDA -3      /* a CUDA runtime call or kernel launch failed                       */
+#define RIFT_ERANGE -4     /* a time-shifted Q interpolation node would leave the Q window      */
+#define RIFT_ENONFINITE -5 /* a NaN or infinity reached the likelihood or its reduction        */
+#define RIFT_ETIMEOUT -6   /* a bounded device wait gave up                                     */
+#define RIFT_ESTATE -7     /* call out of order (e.g. no overlaps set) or a bad state blob      */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+#define RIFT_MEM_HOST 0
+#define RIFT_MEM_DEVICE 1
+
+#define RIFT_QUAD_QUARTER 0 /* kappa = 1/4, as printed in Eq. (def:lnL:Decomposed) */
+#define RIFT_QUAD_HALF 1    /* kappa = 1/2 (equivalent to QUARTER with U, V doubled)  */
+
+#define RIFT_FP64 0  /* every step in float64: the plain reference GPU path               */
+#define RIFT_FP32 1  /* float32 bulk arithmetic; float64 delays, log-sum-exp and sums      */
+#define RIFT_MIXED 2 /* FP32, then float64 re-evaluation of the samples that carry weight  */
+
+#define RIFT_MAX_DET 4
+#define RIFT_MAX_MODES 32
+#define RIFT_MAX_ITER 64
+#define RIFT_MAX_BINS 1024
+
+typedef struct rift_ile rift_ile_t;
+
+/* Problem description.  All pointers are HOST memory, copied during
+ * rift_ile_create; the caller keeps ownership.
+ *
+ *   det_tensor [n_det][3][3]  detector response tensors D_k (Earth-fixed frame)
+ *   det_pos_m  [n_det][3]     detector vertex positions x_k (m); dt_k = -x_k . n / c (Sec. II A)
+ *   gmst_rad                  Greenwich sidereal angle of the reference epoch (an input)
+ *   lm         [n_modes][2]   (l, m) of each mode; 2 <= l <= 6, |m| <= l, no duplicates
+ *   fs_hz, n_q, q_t0_s[n_det] Q_k,lm is sampled at q_t0_s[k] + i / fs_hz, i = 0..n_q-1
+ *                             (seconds relative to the reference epoch)
+ *   t_lo_s, t_hi_s, n_t       geocentric time grid t_j = t_lo + j (t_hi - t_lo)/(n_t - 1),
+ *                             the time marginal is the mean of exp(ln L) over it
+ *   d_ref_mpc                 D_ref of Eq. (strain_mode); d_min/max the distance prior range
+ *   quad_norm                 RIFT_QUAD_QUARTER or RIFT_QUAD_HALF
+ *   precision                 RIFT_FP64, RIFT_FP32 or RIFT_MIXED
+ *   n_bins                    histogram bins per dimension of the sampling prior (2..1024)
+ *   adapt_floor               mixing floor eps in [0, 1): P <- (1-eps) H/sum H + eps/B
+ *   adapt_temper              exponent beta > 0 applied to the weights when adapting
+ *   seed                      key of the counter-based generator (Philox4x32-10)
+ *   max_samples               largest sample batch of one iteration (sizes device buffers)
+ *
+ * Validation: RIFT_EINVAL for bad sizes or modes; RIFT_ERANGE unless, for every
+ * detector and every sky position, t_lo - |x_k|/c and t_hi + |x_k|/c map inside
+ * [q_t0_s[k], q_t0_s[k] + (n_q - 2)/fs_hz] (a Q index outside the window is an error,
+ * never a clamp). */
+typedef struct {
+    int32_t n_det;
+    const double *det_tensor;
+    const double *det_pos_m;
+    double gmst_rad;
+    int32_t n_modes;
+    const int32_t *lm;
+    double fs_hz;
+    int32_t n_q;
+    const double *q_t0_s;
+    double t_lo_s, t_hi_s;
+    int32_t n_t;
+    double d_ref_mpc, d_min_mpc, d_max_mpc;
+    int32_t quad_norm;
+    int32_t precision;
+    int32_t n_bins;
+    double adapt_floor;
+    double adapt_temper;
+    uint64_t seed;
+    int64_t max_samples;
+} rift_ile_config;
+
+/* Result of a marginalisation or an adaptive run (host struct, filled by the call).
+ * Pooled values use every sample of every iteration of the call, each weighted
+ * by the sampling prior it was drawn from:
+ *   lnZ = ln( (1/N) sum_i w_i ),  w_i = L_tmarg,i p_i / p_s,i      (Eq. (lnL:MonteCarlo))
+ *   sigma_lnZ = sqrt( sum w^2 / (sum w)^2 - 1/N )                   (relative error of the mean)
+ *   n_eff = sum w / max w                                           (Eq. (neff))
+ *   n_ess = (sum w)^2 / sum w^2                                     (Sec. IV A)
+ *   lnL_max = largest time-marginalised ln L seen.
+ * *_iter[g] are the same quantities for iteration g alone.  time_ms[]: device
+ * time of the call measured with CUDA events (0 draw+sort, 1 likelihood,
+ * 2 reduce+adapt, 3 whole call). */
+typedef struct {
+    double lnZ, sigma_lnZ, n_eff, n_ess, lnL_max;
+    int64_t n_total;
+    int32_t n_iter;
+    int32_t status;
+    double lnZ_iter[RIFT_MAX_ITER];
+    double sigma_iter[RIFT_MAX_ITER];
+    double n_eff_iter[RIFT_MAX_ITER];
+    double n_ess_iter[RIFT_MAX_ITER];
+    double time_ms[4];
+} rift_ile_result;
+
+/* Create a handle: validate `cfg`, copy it, allocate device buffers for
+ * cfg->max_samples samples.  `cuda_stream` is a cudaStream_t (or NULL).
+ * On error *out is NULL and nothing stays allocated. */
+int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **out);
+
+/* Set Q [n_det][n_modes][n_q], U and V [n_det][n_modes][n_modes] (complex128,
+ * Sec. II A Eq. (QUV)).  The library keeps float64 copies and a float32
+ * split-plane copy of Q (plane 2m = Re Q_m, plane 2m+1 = Im Q_m).
+ * RIFT_EINVAL unless U_k is Hermitian and V_k symmetric to 1e-10 relative to
+ * their largest entry (Sec. V A symmetry relations); RIFT_ENONFINITE on NaN/Inf. */
+int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const void *V, int mem);
+
+/* Evaluate n samples theta [n][6] = (alpha, delta, psi, phi, iota, D):
+ *   lnL_tmarg [n]      time-marginalised ln L = ln( (1/n_t) sum_j exp(ln L(theta, t_j)) )
+ *   lnL_t [n][n_t]     ln L at every bin, or NULL
+ * theta and the outputs live in `mem`.  Any n >= 0 is accepted (processed in
+ * batches of max_samples).  Uses the handle's precision mode. */
+int rift_ile_eval(rift_ile_t *h, const double *theta, int64_t n, int mem, double *lnL_tmarg, double *lnL_t);
+
+/* Per-sample ingredients of the likelihood for inspection and parity checks:
+ *   c [n][n_det][n_modes] complex128 = (D_ref/D) F_k Y_lm(iota, -phi),
+ *   dt [n][n_det] arrival delays (s), quad [n] the template (quadratic) term.
+ * Any output may be NULL.  Computed in float64 in RIFT_FP64 mode, float32 otherwise. */
+int rift_ile_coeffs(rift_ile_t *h, const double *theta, int64_t n, int mem, double *c, double *dt, double *quad);
+
+/* One Monte Carlo batch: draw n_samples from the current sampling prior (no
+ * adaptation), evaluate, reduce.  1 <= n_samples <= max_samples. */
+int rift_ile_marginalize(rift_ile_t *h, int64_t n_samples, rift_ile_result *out);
+
+/* n_iter iterations of draw -> evaluate -> reduce -> adapt, all on the device;
+ * results pooled over the iterations (see rift_ile_result). 1 <= n_iter <= RIFT_MAX_ITER. */
+int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_result *out);
+
+/* Samples of the most recent batch (in draw order): theta [n][6], ln p - ln p_s [n],
+ * time-marginalised ln L [n], ln w [n]; any output may be NULL; *n_out receives
+ * the batch size.  For parity checks of the device's own sample stream. */
+int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus_lnps, double *lnL_tmarg,
+                        double *lnw, int64_t *n_out);
+
+/* Sampler state (histogram masses, counter, seed) as an opaque versioned blob.
+ * get: if buf is NULL, *len receives the size; otherwise *len must be >= it.
+ * set: restores a blob from get (RIFT_ESTATE if malformed or of another shape). */
+int rift_ile_get_state(const rift_ile_t *h, void *buf, size_t *len);
+int rift_ile_set_state(rift_ile_t *h, const void *buf, size_t len);
+
+/* Histogram masses P [6][n_bins] (host) of the current sampling prior. */
+int rift_ile_get_sampler(const rift_ile_t *h, double *P);
+
+/* Number of kernels this handle has launched since creation (diagnostics: lets a
+ * caller count device launches inside a timed region).  Returns -1 for NULL. */
+int64_t rift_ile_kernel_launches(const rift_ile_t *h);
+
+void rift_ile_destroy(rift_ile_t *h);
+const char *rift_ile_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIFT_ILE_H */

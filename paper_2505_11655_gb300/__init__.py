@@ -1,0 +1,306 @@
+"""Python binding of the GB300 ILE library (arXiv:2505.11655 hot path).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``librift_ile.so`` behind the C ABI declared in
+``include/rift_ile.h``.  The functions here carry the same names as the C
+entry points.  Host arrays are numpy arrays; device arrays are torch CUDA
+tensors (their ``data_ptr()`` is passed through), torch being used for device
+memory and streams only.
+
+There is no CPU fallback: importing the binding without the built library
+raises, and so does any call that the library rejects.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB as _LIB_PATH
+from .build import build as _build
+
+RIFT_OK, RIFT_EINVAL, RIFT_ENOMEM, RIFT_ECUDA = 0, -1, -2, -3
+RIFT_ERANGE, RIFT_ENONFINITE, RIFT_ETIMEOUT, RIFT_ESTATE = -4, -5, -6, -7
+RIFT_MEM_HOST, RIFT_MEM_DEVICE = 0, 1
+RIFT_QUAD_QUARTER, RIFT_QUAD_HALF = 0, 1
+RIFT_FP64, RIFT_FP32, RIFT_MIXED = 0, 1, 2
+RIFT_MAX_ITER = 64
+
+EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
+            "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
+            "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_destroy", "rift_ile_strerror"]
+
+
+class RiftError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+class rift_ile_config(C.Structure):
+    _fields_ = [
+        ("n_det", C.c_int32), ("det_tensor", C.c_void_p), ("det_pos_m", C.c_void_p), ("gmst_rad", C.c_double),
+        ("n_modes", C.c_int32), ("lm", C.c_void_p), ("fs_hz", C.c_double), ("n_q", C.c_int32),
+        ("q_t0_s", C.c_void_p), ("t_lo_s", C.c_double), ("t_hi_s", C.c_double), ("n_t", C.c_int32),
+        ("d_ref_mpc", C.c_double), ("d_min_mpc", C.c_double), ("d_max_mpc", C.c_double),
+        ("quad_norm", C.c_int32), ("precision", C.c_int32), ("n_bins", C.c_int32), ("adapt_floor", C.c_double),
+        ("adapt_temper", C.c_double), ("seed", C.c_uint64), ("max_samples", C.c_int64),
+    ]
+
+
+class rift_ile_result(C.Structure):
+    _fields_ = [
+        ("lnZ", C.c_double), ("sigma_lnZ", C.c_double), ("n_eff", C.c_double), ("n_ess", C.c_double),
+        ("lnL_max", C.c_double), ("n_total", C.c_int64), ("n_iter", C.c_int32), ("status", C.c_int32),
+        ("lnZ_iter", C.c_double * RIFT_MAX_ITER), ("sigma_iter", C.c_double * RIFT_MAX_ITER),
+        ("n_eff_iter", C.c_double * RIFT_MAX_ITER), ("n_ess_iter", C.c_double * RIFT_MAX_ITER),
+        ("time_ms", C.c_double * 4),
+    ]
+
+    def as_dict(self):
+        n = self.n_iter
+        return dict(lnZ=self.lnZ, sigma_lnZ=self.sigma_lnZ, n_eff=self.n_eff, n_ess=self.n_ess,
+                    lnL_max=self.lnL_max, n_total=self.n_total, n_iter=n, status=self.status,
+                    lnZ_iter=list(self.lnZ_iter[:n]), sigma_iter=list(self.sigma_iter[:n]),
+                    n_eff_iter=list(self.n_eff_iter[:n]), n_ess_iter=list(self.n_ess_iter[:n]),
+                    time_ms=list(self.time_ms))
+
+
+_lib = None
+
+
+def load(build_if_missing: bool = False):
+    """Load librift_ile.so (optionally building it first).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build()
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"CUDA library not built: {_LIB_PATH} (run paper_2505_11655_gb300/build.py)")
+    L = C.CDLL(_LIB_PATH)
+    vp, i32, i64 = C.c_void_p, C.c_int32, C.c_int64
+    L.rift_ile_create.argtypes = [C.POINTER(rift_ile_config), vp, C.POINTER(vp)]
+    L.rift_ile_set_overlaps.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.rift_ile_eval.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+    L.rift_ile_coeffs.argtypes = [vp, vp, i64, C.c_int, vp, vp, vp]
+    L.rift_ile_marginalize.argtypes = [vp, i64, C.POINTER(rift_ile_result)]
+    L.rift_ile_adapt.argtypes = [vp, i32, i64, C.POINTER(rift_ile_result)]
+    L.rift_ile_last_batch.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.POINTER(i64)]
+    L.rift_ile_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
+    L.rift_ile_set_state.argtypes = [vp, vp, C.c_size_t]
+    L.rift_ile_get_sampler.argtypes = [vp, vp]
+    L.rift_ile_kernel_launches.argtypes = [vp]
+    L.rift_ile_kernel_launches.restype = C.c_int64
+    L.rift_ile_destroy.argtypes = [vp]
+    L.rift_ile_destroy.restype = None
+    L.rift_ile_strerror.argtypes = [C.c_int]
+    L.rift_ile_strerror.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("rift_ile_destroy", "rift_ile_strerror", "rift_ile_kernel_launches"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().rift_ile_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != RIFT_OK:
+        raise RiftError(rc, what)
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _mem(a):
+    if isinstance(a, np.ndarray):
+        return RIFT_MEM_HOST
+    if hasattr(a, "is_cuda"):
+        if not a.is_cuda:
+            raise ValueError("torch tensors must be on the GPU; pass numpy arrays for host memory")
+        return RIFT_MEM_DEVICE
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+# ---------------------------------------------------------------------------------- C-named calls
+
+def rift_ile_create(cfg: rift_ile_config, stream=None):
+    h = C.c_void_p()
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(load().rift_ile_create(C.byref(cfg), st, C.byref(h)), "rift_ile_create")
+    return h
+
+
+def rift_ile_set_overlaps(h, Q, U, V):
+    mem = _mem(Q)
+    if _mem(U) != mem or _mem(V) != mem:
+        raise ValueError("Q, U, V must live in the same memory")
+    _check(load().rift_ile_set_overlaps(h, _ptr(Q), _ptr(U), _ptr(V), mem), "rift_ile_set_overlaps")
+
+
+def rift_ile_eval(h, theta, n, lnL_tmarg, lnL_t=None):
+    _check(load().rift_ile_eval(h, _ptr(theta), int(n), _mem(theta), _ptr(lnL_tmarg), _ptr(lnL_t)), "rift_ile_eval")
+
+
+def rift_ile_coeffs(h, theta, n, c=None, dt=None, quad=None):
+    _check(load().rift_ile_coeffs(h, _ptr(theta), int(n), _mem(theta), _ptr(c), _ptr(dt), _ptr(quad)),
+           "rift_ile_coeffs")
+
+
+def rift_ile_marginalize(h, n_samples):
+    r = rift_ile_result()
+    _check(load().rift_ile_marginalize(h, int(n_samples), C.byref(r)), "rift_ile_marginalize")
+    return r
+
+
+def rift_ile_adapt(h, n_iter, n_per_iter):
+    r = rift_ile_result()
+    _check(load().rift_ile_adapt(h, int(n_iter), int(n_per_iter), C.byref(r)), "rift_ile_adapt")
+    return r
+
+
+def rift_ile_last_batch(h, theta=None, lnp_minus_lnps=None, lnL_tmarg=None, lnw=None, mem=RIFT_MEM_HOST):
+    n = C.c_int64()
+    _check(load().rift_ile_last_batch(h, mem, _ptr(theta), _ptr(lnp_minus_lnps), _ptr(lnL_tmarg), _ptr(lnw),
+                                      C.byref(n)), "rift_ile_last_batch")
+    return n.value
+
+
+def rift_ile_get_state(h) -> bytes:
+    n = C.c_size_t()
+    _check(load().rift_ile_get_state(h, None, C.byref(n)), "rift_ile_get_state")
+    buf = C.create_string_buffer(n.value)
+    _check(load().rift_ile_get_state(h, buf, C.byref(n)), "rift_ile_get_state")
+    return buf.raw[: n.value]
+
+
+def rift_ile_set_state(h, blob: bytes):
+    _check(load().rift_ile_set_state(h, blob, len(blob)), "rift_ile_set_state")
+
+
+def rift_ile_get_sampler(h, n_bins):
+    P = np.empty((6, n_bins))
+    _check(load().rift_ile_get_sampler(h, _ptr(P)), "rift_ile_get_sampler")
+    return P
+
+
+def rift_ile_kernel_launches(h):
+    return int(load().rift_ile_kernel_launches(h))
+
+
+def rift_ile_destroy(h):
+    if h:
+        load().rift_ile_destroy(h)
+
+
+def rift_ile_strerror(code):
+    return strerror(code)
+
+
+# ---------------------------------------------------------------------------------- convenience
+
+class ILE:
+    """One handle for one intrinsic point.  ``prob`` carries the problem's host
+    arrays (the attributes of ``ile_synth.Problem``)."""
+
+    def __init__(self, prob, precision=RIFT_FP32, max_samples=1 << 20, n_bins=64, adapt_floor=0.1,
+                 adapt_temper=1.0, seed=1, stream=None, set_overlaps=True):
+        self._keep = dict(
+            det_tensor=np.ascontiguousarray(prob.det_tensor, np.float64),
+            det_pos=np.ascontiguousarray(prob.det_pos, np.float64),
+            lm=np.ascontiguousarray(prob.lm, np.int32),
+            q_t0=np.ascontiguousarray(prob.q_t0, np.float64),
+        )
+        k = self._keep
+        self.n_det, self.n_modes, self.n_t, self.n_bins = k["det_tensor"].shape[0], k["lm"].shape[0], prob.n_t, n_bins
+        self.cfg = rift_ile_config(
+            self.n_det, _ptr(k["det_tensor"]), _ptr(k["det_pos"]), float(prob.gmst), self.n_modes, _ptr(k["lm"]),
+            float(prob.fs), int(prob.n_q), _ptr(k["q_t0"]), float(prob.t_lo), float(prob.t_hi), int(prob.n_t),
+            float(prob.d_ref), float(prob.d_min), float(prob.d_max), int(prob.quad_norm), int(precision),
+            int(n_bins), float(adapt_floor), float(adapt_temper), int(seed), int(max_samples))
+        self.h = rift_ile_create(self.cfg, stream)
+        if set_overlaps:
+            self.set_overlaps(prob.Q, prob.U, prob.V)
+
+    def set_overlaps(self, Q, U, V):
+        if isinstance(Q, np.ndarray):
+            Q, U, V = (np.ascontiguousarray(x, np.complex128) for x in (Q, U, V))
+        rift_ile_set_overlaps(self.h, Q, U, V)
+
+    def eval(self, theta, want_bins=False):
+        if isinstance(theta, np.ndarray):
+            th = np.ascontiguousarray(theta, np.float64).reshape(-1, 6)
+            out = np.empty(th.shape[0])
+            bins = np.empty((th.shape[0], self.n_t)) if want_bins else None
+        else:
+            import torch
+            th = theta.reshape(-1, 6).contiguous()
+            out = torch.empty(th.shape[0], dtype=torch.float64, device=th.device)
+            bins = torch.empty((th.shape[0], self.n_t), dtype=torch.float64, device=th.device) if want_bins else None
+        rift_ile_eval(self.h, th, th.shape[0], out, bins)
+        return (out, bins) if want_bins else out
+
+    def coeffs(self, theta):
+        th = np.ascontiguousarray(theta, np.float64).reshape(-1, 6)
+        n = th.shape[0]
+        c = np.empty((n, self.n_det, self.n_modes), np.complex128)
+        dt = np.empty((n, self.n_det))
+        quad = np.empty(n)
+        rift_ile_coeffs(self.h, th, n, c, dt, quad)
+        return c, dt, quad
+
+    def marginalize(self, n):
+        return rift_ile_marginalize(self.h, n).as_dict()
+
+    def adapt(self, n_iter, n_per_iter):
+        return rift_ile_adapt(self.h, n_iter, n_per_iter).as_dict()
+
+    def last_batch(self, n):
+        th, lr, ll, lw = np.empty((n, 6)), np.empty(n), np.empty(n), np.empty(n)
+        m = rift_ile_last_batch(self.h, th, lr, ll, lw)
+        return th[:m], lr[:m], ll[:m], lw[:m]
+
+    def kernel_launches(self):
+        return rift_ile_kernel_launches(self.h)
+
+    def sampler(self):
+        return rift_ile_get_sampler(self.h, self.n_bins)
+
+    def get_state(self):
+        return rift_ile_get_state(self.h)
+
+    def set_state(self, blob):
+        rift_ile_set_state(self.h, blob)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rift_ile_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,745 @@
+// Host core of the ILE library: configuration checks, device buffers, the order of
+// kernel launches for each entry point of include/rift_ile.h, and result assembly.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <set>
+#include <utility>
+#include <vector>
+
+#include "ile_kernels.h"
+
+using namespace rift;
+
+namespace {
+
+constexpr uint64_t kStateMagic = 0x31454C4954464952ull;   // "RIFTILE1"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint64_t magic;
+    uint32_t version;
+    uint32_t n_bins;
+    uint64_t seed;
+    uint32_t iteration;
+    uint32_t reserved;
+};
+
+// Q window padding of the float32 planes: one chunk window past the end.
+constexpr int kQPad = 256 + 16;
+
+}  // namespace
+
+struct rift_ile {
+    rift_ile_config cfg{};
+    std::vector<double> det_tensor, det_pos, q_t0;
+    std::vector<int32_t> lm;
+    cudaStream_t stream = nullptr;
+    Problem prob{};
+    bool have_overlaps = false;
+    int64_t cap = 0;           // samples per device batch
+    // overlaps
+    double2 *Q64 = nullptr, *U64 = nullptr, *V64 = nullptr;
+    float *Qr32 = nullptr;
+    float2 *U32 = nullptr, *V32 = nullptr;
+    int *bin_i = nullptr;
+    float *bin_f = nullptr;
+    // per-sample buffers
+    double *theta = nullptr, *lnpw = nullptr, *lnL = nullptr, *lnw = nullptr;
+    uint64_t *bins = nullptr;
+    uint32_t *key = nullptr, *perm = nullptr, *counts = nullptr;
+    // reductions and sampler
+    double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
+    double *P = nullptr, *C = nullptr;
+    int *err = nullptr;
+    double *host_out = nullptr;   // pinned: stats + final + err
+    uint32_t iteration = 0;
+    int64_t last_n = 0;
+    int64_t launches = 0;
+    cudaEvent_t ev[RIFT_MAX_ITER][4];
+    bool events_made = false;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T> int dalloc(rift_ile_t *h, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+        cudaGetLastError();
+        return RIFT_ENOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return RIFT_OK;
+}
+
+void release(rift_ile_t *h)
+{
+    if (!h)
+        return;
+    if (h->stream)
+        cudaStreamSynchronize(h->stream);
+    else
+        cudaDeviceSynchronize();
+    for (void *p : h->allocs)
+        cudaFree(p);
+    h->allocs.clear();
+    if (h->host_out)
+        cudaFreeHost(h->host_out);
+    if (h->events_made)
+        for (auto &row : h->ev)
+            for (auto &e : row)
+                cudaEventDestroy(e);
+    delete h;
+}
+
+double factorial(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i)
+        r *= i;
+    return r;
+}
+
+// Wigner small-d d^l_{m',2}(beta) written as a sum over s of
+//   (-1)^(m'-2+s) sqrt((l+m')!(l-m')!(l+2)!(l-2)!) / ((l+2-s)! s! (m'-2+s)! (l-m'-s)!)
+//   cos(beta/2)^(2l+2-m'-2s) sin(beta/2)^(m'-2+2s),
+// so that -2Y_lm(beta, .) = sqrt((2l+1)/4pi) d^l_{m,2}(beta) e^{i m .}.
+int wigner_table(int l, int m, double *coef, int8_t *pc, int8_t *ps)
+{
+    const double norm = std::sqrt((2.0 * l + 1.0) / (4.0 * kPi));
+    const double root = std::sqrt(factorial(l + m) * factorial(l - m) * factorial(l + 2) * factorial(l - 2));
+    int s0 = std::max(0, 2 - m), s1 = std::min(l + 2, l - m);
+    int nt = 0;
+    for (int s = s0; s <= s1; ++s) {
+        int sign_exp = m - 2 + s;
+        double sign = (std::abs(sign_exp) % 2) ? -1.0 : 1.0;
+        double v = sign * root / (factorial(l + 2 - s) * factorial(s) * factorial(m - 2 + s) * factorial(l - m - s));
+        if (nt >= kMaxWTerms)
+            return -1;
+        coef[nt] = norm * v;
+        pc[nt] = (int8_t)(2 * l + 2 - m - 2 * s);
+        ps[nt] = (int8_t)(m - 2 + 2 * s);
+        ++nt;
+    }
+    return nt;
+}
+
+int map_err(int flags)
+{
+    if (flags & kErrRange)
+        return RIFT_ERANGE;
+    if (flags & kErrNonFinite)
+        return RIFT_ENONFINITE;
+    return RIFT_OK;
+}
+
+#define CK(call)                                                                                                        \
+    do {                                                                                                                \
+        cudaError_t e_ = (call);                                                                                        \
+        if (e_ != cudaSuccess) {                                                                                        \
+            if (std::getenv("RIFT_ILE_DEBUG"))                                                                          \
+                std::fprintf(stderr, "rift_ile: %s at %s:%d: %s\n", #call, __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            cudaGetLastError();                                                                                         \
+            return RIFT_ECUDA;                                                                                          \
+        }                                                                                                               \
+    } while (0)
+
+#define RK(call)                 \
+    do {                         \
+        int r_ = (call);         \
+        if (r_ != RIFT_OK)       \
+            return r_;           \
+    } while (0)
+
+SamplerDev sampler_of(const rift_ile_t *h)
+{
+    SamplerDev S;
+    S.P = h->P;
+    S.C = h->C;
+    S.B = h->cfg.n_bins;
+    S.d_min = h->cfg.d_min_mpc;
+    S.d_max = h->cfg.d_max_mpc;
+    S.floor_eps = h->cfg.adapt_floor;
+    S.temper = h->cfg.adapt_temper;
+    S.seed = h->cfg.seed;
+    return S;
+}
+
+int validate(const rift_ile_config *c)
+{
+    if (!c || c->n_det < 1 || c->n_det > RIFT_MAX_DET || c->n_modes < 1 || c->n_modes > RIFT_MAX_MODES)
+        return RIFT_EINVAL;
+    if (!c->det_tensor || !c->det_pos_m || !c->lm || !c->q_t0_s)
+        return RIFT_EINVAL;
+    if (!(c->fs_hz > 0) || c->n_q < 2 || c->n_t < 1 || !(c->t_hi_s >= c->t_lo_s))
+        return RIFT_EINVAL;
+    if (!(c->d_ref_mpc > 0) || !(c->d_min_mpc > 0) || !(c->d_max_mpc > c->d_min_mpc))
+        return RIFT_EINVAL;
+    if (c->quad_norm != RIFT_QUAD_QUARTER && c->quad_norm != RIFT_QUAD_HALF)
+        return RIFT_EINVAL;
+    if (c->precision != RIFT_FP64 && c->precision != RIFT_FP32 && c->precision != RIFT_MIXED)
+        return RIFT_EINVAL;
+    if (c->n_bins < 2 || c->n_bins > RIFT_MAX_BINS || !(c->adapt_floor >= 0 && c->adapt_floor < 1) ||
+        !(c->adapt_temper > 0))
+        return RIFT_EINVAL;
+    if (c->max_samples < 1 || c->max_samples > (int64_t)0x7fffffff)
+        return RIFT_EINVAL;
+    std::set<std::pair<int, int>> seen;
+    for (int i = 0; i < c->n_modes; ++i) {
+        int l = c->lm[2 * i], m = c->lm[2 * i + 1];
+        if (l < 2 || l > kMaxL || m < -l || m > l || !seen.insert({l, m}).second)
+            return RIFT_EINVAL;
+    }
+    for (int k = 0; k < c->n_det; ++k) {
+        for (int i = 0; i < 9; ++i)
+            if (!std::isfinite(c->det_tensor[9 * k + i]))
+                return RIFT_EINVAL;
+        double r = 0;
+        for (int i = 0; i < 3; ++i) {
+            if (!std::isfinite(c->det_pos_m[3 * k + i]))
+                return RIFT_EINVAL;
+            r += c->det_pos_m[3 * k + i] * c->det_pos_m[3 * k + i];
+        }
+        double rc = std::sqrt(r) / kC;
+        double umin = (c->t_lo_s - rc - c->q_t0_s[k]) * c->fs_hz;
+        double umax = (c->t_hi_s + rc - c->q_t0_s[k]) * c->fs_hz;
+        if (!(umin >= 1e-3) || !(umax <= (double)(c->n_q - 2) - 1e-3))
+            return RIFT_ERANGE;
+    }
+    return RIFT_OK;
+}
+
+// Builds float32 planes and Gram copies from the float64 device copies; flags NaN/Inf.
+__global__ void prep_overlaps_kernel(const double2 *__restrict__ Q64, const double2 *__restrict__ U64,
+                                     const double2 *__restrict__ V64, int K, int M, int n_q, int n_q_pad,
+                                     float *__restrict__ Qr32, float2 *__restrict__ U32, float2 *__restrict__ V32,
+                                     int *err)
+{
+    const int64_t total = (int64_t)K * 2 * M * n_q_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t row = e / n_q_pad;
+        int c = (int)(e - row * n_q_pad);
+        int k = (int)(row / (2 * M)), r = (int)(row % (2 * M));
+        float v = 0.f;
+        if (c < n_q) {
+            double2 q = Q64[((int64_t)k * M + r / 2) * n_q + c];
+            double x = (r & 1) ? q.y : q.x;
+            if (!isfinite(x))
+                atomicOr(err, kErrNonFinite);
+            v = (float)x;
+        }
+        Qr32[e] = v;
+    }
+    const int64_t g = (int64_t)K * M * M;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g; e += (int64_t)gridDim.x * blockDim.x) {
+        double2 u = U64[e], v = V64[e];
+        if (!isfinite(u.x) || !isfinite(u.y) || !isfinite(v.x) || !isfinite(v.y))
+            atomicOr(err, kErrNonFinite);
+        U32[e] = make_float2((float)u.x, (float)u.y);
+        V32[e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+int sync_and_err(rift_ile_t *h, int *flags_out = nullptr)
+{
+    int flags = 0;
+    CK(cudaMemcpyAsync(&h->host_out[0], h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(&flags, &h->host_out[0], sizeof(int));
+    if (flags_out)
+        *flags_out = flags;
+    return map_err(flags);
+}
+
+bool use_fp32(const rift_ile_t *h) { return h->cfg.precision != RIFT_FP64; }
+
+// ln L for n device-resident samples (theta [n][6]); perm/key scratch from the handle.
+int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t, const double *lnpw,
+                double *lnw)
+{
+    if (!use_fp32(h)) {
+        CK(launch_lnl_fp64(h->prob, theta, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->stream));
+        h->launches += 1;
+        return RIFT_OK;
+    }
+    h->launches += 5;   // keys, count, scan, scatter, tiled likelihood
+    CK(launch_keys(theta, n, h->key, h->stream));
+    CK(launch_sort(h->key, n, h->counts, h->perm, h->stream));
+    CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err,
+                       h->stream));
+    return RIFT_OK;
+}
+
+// One draw -> sort -> likelihood -> reduce (-> adapt) iteration into stats slot `slot`.
+int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_pooled)
+{
+    SamplerDev S = sampler_of(h);
+    CK(cudaEventRecord(h->ev[slot][0], h->stream));
+    CK(launch_draw(S, h->iteration, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    if (use_fp32(h))
+        CK(launch_sort(h->key, n, h->counts, h->perm, h->stream));
+    CK(cudaEventRecord(h->ev[slot][1], h->stream));
+    if (use_fp32(h))
+        CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, h->theta, h->perm, n, h->lnL, nullptr, h->lnpw,
+                           h->lnw, h->err, h->stream));
+    else
+        CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
+    CK(cudaEventRecord(h->ev[slot][2], h->stream));
+    CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, slot, h->pooled, reset_pooled ? 1 : 0, h->err,
+                     h->stream));
+    if (adapt)
+        CK(launch_adapt(S, h->bins, h->lnw, n, h->stats, slot, h->hist_partial, h->stream));
+    CK(cudaEventRecord(h->ev[slot][3], h->stream));
+    h->launches += 1 + (use_fp32(h) ? 3 : 0) + 1 + 2 + (adapt ? 2 : 0);
+    h->iteration += 1;
+    h->last_n = n;
+    return RIFT_OK;
+}
+
+int finish_result(rift_ile_t *h, int n_iter, rift_ile_result *out)
+{
+    CK(launch_pooled_final(h->pooled, h->final_out, h->stream));
+    h->launches += 1;
+    // host_out layout: [0] err word, [1..8) final, [8..) stats
+    CK(cudaMemcpyAsync(&h->host_out[1], h->final_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&h->host_out[8], h->stats, sizeof(double) * 8 * n_iter, cudaMemcpyDeviceToHost, h->stream));
+    int flags = 0;
+    int rc = sync_and_err(h, &flags);
+    if (!out)
+        return rc;
+    std::memset(out, 0, sizeof(*out));
+    const double *f = &h->host_out[1];
+    out->lnZ = f[0];
+    out->sigma_lnZ = f[1];
+    out->n_eff = f[2];
+    out->n_ess = f[3];
+    out->lnL_max = f[4];
+    out->n_total = (int64_t)f[5];
+    out->n_iter = n_iter;
+    out->status = rc;
+    for (int g = 0; g < n_iter; ++g) {
+        const double *s = &h->host_out[8 + 8 * g];
+        out->lnZ_iter[g] = s[0];
+        out->sigma_iter[g] = s[1];
+        out->n_eff_iter[g] = s[2];
+        out->n_ess_iter[g] = s[3];
+        float a = 0, b = 0, c = 0, d = 0;
+        cudaEventElapsedTime(&a, h->ev[g][0], h->ev[g][1]);
+        cudaEventElapsedTime(&b, h->ev[g][1], h->ev[g][2]);
+        cudaEventElapsedTime(&c, h->ev[g][2], h->ev[g][3]);
+        cudaEventElapsedTime(&d, h->ev[g][0], h->ev[g][3]);
+        out->time_ms[0] += a;
+        out->time_ms[1] += b;
+        out->time_ms[2] += c;
+        out->time_ms[3] += d;
+    }
+    return rc;
+}
+
+}  // namespace
+
+// ============================================================================ ABI
+
+extern "C" {
+
+const char *rift_ile_strerror(int code)
+{
+    switch (code) {
+    case RIFT_OK: return "ok";
+    case RIFT_EINVAL: return "invalid argument";
+    case RIFT_ENOMEM: return "out of memory";
+    case RIFT_ECUDA: return "CUDA error";
+    case RIFT_ERANGE: return "time-shifted Q index outside the Q window";
+    case RIFT_ENONFINITE: return "non-finite value in inputs or results";
+    case RIFT_ETIMEOUT: return "bounded device wait timed out";
+    case RIFT_ESTATE: return "call out of order or malformed state";
+    default: return "unknown status";
+    }
+}
+
+int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **out)
+{
+    if (!out)
+        return RIFT_EINVAL;
+    *out = nullptr;
+    int v = validate(cfg);
+    if (v != RIFT_OK)
+        return v;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return RIFT_ECUDA;
+    }
+    rift_ile_t *h = new (std::nothrow) rift_ile_t();
+    if (!h)
+        return RIFT_ENOMEM;
+    h->cfg = *cfg;
+    const int K = cfg->n_det, M = cfg->n_modes;
+    h->det_tensor.assign(cfg->det_tensor, cfg->det_tensor + 9 * K);
+    h->det_pos.assign(cfg->det_pos_m, cfg->det_pos_m + 3 * K);
+    h->q_t0.assign(cfg->q_t0_s, cfg->q_t0_s + K);
+    h->lm.assign(cfg->lm, cfg->lm + 2 * M);
+    h->cfg.det_tensor = h->det_tensor.data();
+    h->cfg.det_pos_m = h->det_pos.data();
+    h->cfg.q_t0_s = h->q_t0.data();
+    h->cfg.lm = h->lm.data();
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->cap = cfg->max_samples;
+
+    Problem &P = h->prob;
+    P.K = K;
+    P.M = M;
+    P.n_q = cfg->n_q;
+    P.n_t = cfg->n_t;
+    P.n_q_pad = ((cfg->n_q + 3) & ~3) + kQPad;
+    P.fs = cfg->fs_hz;
+    P.t_lo = cfg->t_lo_s;
+    P.t_step = cfg->n_t > 1 ? (cfg->t_hi_s - cfg->t_lo_s) / (cfg->n_t - 1) : 0.0;
+    P.gmst = cfg->gmst_rad;
+    P.d_ref = cfg->d_ref_mpc;
+    P.kappa = cfg->quad_norm == RIFT_QUAD_HALF ? 0.5 : 0.25;
+    for (int k = 0; k < K; ++k) {
+        const double *D = cfg->det_tensor + 9 * k;
+        P.Dten[k][0] = D[0];
+        P.Dten[k][1] = D[4];
+        P.Dten[k][2] = D[8];
+        P.Dten[k][3] = 0.5 * (D[1] + D[3]);
+        P.Dten[k][4] = 0.5 * (D[2] + D[6]);
+        P.Dten[k][5] = 0.5 * (D[5] + D[7]);
+        for (int i = 0; i < 3; ++i)
+            P.xpos[k][i] = cfg->det_pos_m[3 * k + i] / kC;
+        P.q_t0[k] = cfg->q_t0_s[k];
+    }
+    for (int m = 0; m < M; ++m) {
+        P.mode_m[m] = cfg->lm[2 * m + 1];
+        int nt = wigner_table(cfg->lm[2 * m], cfg->lm[2 * m + 1], P.wcoef[m], P.wpc[m], P.wps[m]);
+        if (nt < 0) {
+            delete h;
+            return RIFT_EINVAL;
+        }
+        P.wn[m] = (int8_t)nt;
+    }
+
+    int rc = RIFT_OK;
+    const int64_t N = h->cap;
+    const int B = cfg->n_bins;
+    if ((rc = dalloc(h, &h->Q64, (size_t)K * M * cfg->n_q)) || (rc = dalloc(h, &h->U64, (size_t)K * M * M)) ||
+        (rc = dalloc(h, &h->V64, (size_t)K * M * M)) || (rc = dalloc(h, &h->Qr32, (size_t)K * 2 * M * P.n_q_pad)) ||
+        (rc = dalloc(h, &h->U32, (size_t)K * M * M)) || (rc = dalloc(h, &h->V32, (size_t)K * M * M)) ||
+        (rc = dalloc(h, &h->bin_i, (size_t)cfg->n_t)) || (rc = dalloc(h, &h->bin_f, (size_t)cfg->n_t)) ||
+        (rc = dalloc(h, &h->theta, (size_t)N * 6)) || (rc = dalloc(h, &h->lnpw, (size_t)N)) ||
+        (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
+        (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
+        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kCells + 1)) ||
+        (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||
+        (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
+        (rc = dalloc(h, &h->stats, (size_t)8 * RIFT_MAX_ITER)) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
+        (rc = dalloc(h, &h->final_out, (size_t)8)) || (rc = dalloc(h, &h->P, (size_t)6 * B)) ||
+        (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->err, (size_t)4))) {
+        release(h);
+        return rc;
+    }
+    if (cudaMallocHost(&h->host_out, sizeof(double) * (8 + 8 * RIFT_MAX_ITER + 8)) != cudaSuccess) {
+        cudaGetLastError();
+        h->host_out = nullptr;
+        release(h);
+        return RIFT_ENOMEM;
+    }
+    for (auto &row : h->ev)
+        for (auto &e : row)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                release(h);
+                return RIFT_ECUDA;
+            }
+    h->events_made = true;
+
+    // time-bin split table: j * beta = bin_i + bin_f
+    std::vector<int> bi(cfg->n_t);
+    std::vector<float> bf(cfg->n_t);
+    for (int j = 0; j < cfg->n_t; ++j) {
+        double jb = (cfg->n_t > 1 ? j * (cfg->t_hi_s - cfg->t_lo_s) / (cfg->n_t - 1) : 0.0) * cfg->fs_hz;
+        double fl = std::floor(jb);
+        bi[j] = (int)fl;
+        bf[j] = (float)(jb - fl);
+        if (bf[j] >= 1.0f)
+            bf[j] = 0x1.fffffep-1f;
+    }
+    std::vector<double> P0((size_t)6 * B, 1.0 / B);
+    if (cudaMemcpyAsync(h->bin_i, bi.data(), sizeof(int) * cfg->n_t, cudaMemcpyHostToDevice, h->stream) ||
+        cudaMemcpyAsync(h->bin_f, bf.data(), sizeof(float) * cfg->n_t, cudaMemcpyHostToDevice, h->stream) ||
+        cudaMemcpyAsync(h->P, P0.data(), sizeof(double) * 6 * B, cudaMemcpyHostToDevice, h->stream) ||
+        cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream) || launch_build_cdf(sampler_of(h), h->stream) ||
+        cudaStreamSynchronize(h->stream)) {
+        cudaGetLastError();
+        release(h);
+        return RIFT_ECUDA;
+    }
+    P.Q64 = h->Q64;
+    P.U64 = h->U64;
+    P.V64 = h->V64;
+    P.Qr32 = h->Qr32;
+    P.U32 = h->U32;
+    P.V32 = h->V32;
+    *out = h;
+    return RIFT_OK;
+}
+
+void rift_ile_destroy(rift_ile_t *h) { release(h); }
+
+int64_t rift_ile_kernel_launches(const rift_ile_t *h) { return h ? h->launches : -1; }
+
+int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const void *V, int mem)
+{
+    if (!h || !Q || !U || !V || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    const int K = h->prob.K, M = h->prob.M, nq = h->prob.n_q;
+    const size_t qb = sizeof(double2) * (size_t)K * M * nq, gb = sizeof(double2) * (size_t)K * M * M;
+    const cudaMemcpyKind kind = mem == RIFT_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // symmetry checks on host copies of U, V (Sec. V A: U^* = U^T, V = V^T)
+    std::vector<double> hu(2 * (size_t)K * M * M), hv(2 * (size_t)K * M * M);
+    if (mem == RIFT_MEM_HOST) {
+        std::memcpy(hu.data(), U, gb);
+        std::memcpy(hv.data(), V, gb);
+    } else {
+        CK(cudaMemcpyAsync(hu.data(), U, gb, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(hv.data(), V, gb, cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    for (int k = 0; k < K; ++k) {
+        double su = 0, sv = 0;
+        for (size_t e = 0; e < (size_t)2 * M * M; ++e) {
+            double a = std::fabs(hu[2 * (size_t)k * M * M + e]), b = std::fabs(hv[2 * (size_t)k * M * M + e]);
+            if (!std::isfinite(a) || !std::isfinite(b))
+                return RIFT_ENONFINITE;
+            su = std::max(su, a);
+            sv = std::max(sv, b);
+        }
+        for (int a = 0; a < M; ++a)
+            for (int b = 0; b < M; ++b) {
+                size_t ab = 2 * (((size_t)k * M + a) * M + b), ba = 2 * (((size_t)k * M + b) * M + a);
+                if (std::fabs(hu[ab] - hu[ba]) > 1e-10 * su || std::fabs(hu[ab + 1] + hu[ba + 1]) > 1e-10 * su)
+                    return RIFT_EINVAL;
+                if (std::fabs(hv[ab] - hv[ba]) > 1e-10 * sv || std::fabs(hv[ab + 1] - hv[ba + 1]) > 1e-10 * sv)
+                    return RIFT_EINVAL;
+            }
+    }
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    CK(cudaMemcpyAsync(h->Q64, Q, qb, kind, h->stream));
+    CK(cudaMemcpyAsync(h->U64, U, gb, kind, h->stream));
+    CK(cudaMemcpyAsync(h->V64, V, gb, kind, h->stream));
+    int64_t tot = (int64_t)K * 2 * M * h->prob.n_q_pad;
+    int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
+    prep_overlaps_kernel<<<grid, 256, 0, h->stream>>>(h->Q64, h->U64, h->V64, K, M, nq, h->prob.n_q_pad, h->Qr32,
+                                                      h->U32, h->V32, h->err);
+    CK(cudaGetLastError());
+    h->launches += 1;
+    int rc = sync_and_err(h);
+    h->have_overlaps = (rc == RIFT_OK);
+    return rc;
+}
+
+int rift_ile_eval(rift_ile_t *h, const double *theta, int64_t n, int mem, double *lnL_tmarg, double *lnL_t)
+{
+    if (!h || n < 0 || (n > 0 && (!theta || !lnL_tmarg)) || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    if (!h->have_overlaps)
+        return RIFT_ESTATE;
+    if (n == 0)
+        return RIFT_OK;
+    const int nt = h->prob.n_t;
+    int64_t chunk = h->cap;
+    double *stage_t = nullptr;
+    if (lnL_t && mem == RIFT_MEM_HOST) {
+        chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, (int64_t)(64 << 20) / nt));
+        void *q = nullptr;
+        if (cudaMalloc(&q, sizeof(double) * (size_t)chunk * nt) != cudaSuccess) {
+            cudaGetLastError();
+            return RIFT_ENOMEM;
+        }
+        stage_t = static_cast<double *>(q);
+    }
+    int rc = RIFT_OK;
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    h->last_n = 0;   // the staging buffers no longer hold a drawn batch
+    for (int64_t i0 = 0; i0 < n && rc == RIFT_OK; i0 += chunk) {
+        const int64_t c = std::min(chunk, n - i0);
+        const double *th = theta + 6 * i0;
+        double *o = lnL_tmarg + i0;
+        double *ot = lnL_t ? lnL_t + i0 * nt : nullptr;
+        if (mem == RIFT_MEM_HOST) {
+            if (cudaMemcpyAsync(h->theta, th, sizeof(double) * 6 * c, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+                rc = RIFT_ECUDA;
+                break;
+            }
+            rc = eval_device(h, h->theta, c, h->lnL, stage_t, nullptr, nullptr);
+            if (rc == RIFT_OK &&
+                (cudaMemcpyAsync(o, h->lnL, sizeof(double) * c, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+                 (ot && cudaMemcpyAsync(ot, stage_t, sizeof(double) * c * nt, cudaMemcpyDeviceToHost, h->stream) !=
+                            cudaSuccess)))
+                rc = RIFT_ECUDA;
+        } else {
+            rc = eval_device(h, th, c, o, ot, nullptr, nullptr);
+        }
+    }
+    int rc2 = sync_and_err(h);
+    if (stage_t)
+        cudaFree(stage_t);
+    return rc != RIFT_OK ? rc : rc2;
+}
+
+int rift_ile_coeffs(rift_ile_t *h, const double *theta, int64_t n, int mem, double *c, double *dt, double *quad)
+{
+    if (!h || n < 0 || (n > 0 && !theta) || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    if (!h->have_overlaps)
+        return RIFT_ESTATE;
+    if (n == 0)
+        return RIFT_OK;
+    const bool fp64 = h->cfg.precision == RIFT_FP64;
+    const int K = h->prob.K, M = h->prob.M;
+    if (mem == RIFT_MEM_DEVICE) {
+        CK(launch_coeffs(h->prob, fp64, theta, n, reinterpret_cast<double2 *>(c), dt, quad, h->stream));
+        return sync_and_err(h);
+    }
+    const int64_t chunk = std::min<int64_t>(h->cap, 1 << 16);
+    double2 *dc = nullptr;
+    double *ddt = nullptr, *dq = nullptr;
+    std::vector<void *> tmp;
+    auto grab = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        tmp.push_back(q);
+        return q;
+    };
+    dc = static_cast<double2 *>(grab(sizeof(double2) * chunk * K * M));
+    ddt = static_cast<double *>(grab(sizeof(double) * chunk * K));
+    dq = static_cast<double *>(grab(sizeof(double) * chunk));
+    int rc = (dc && ddt && dq) ? RIFT_OK : RIFT_ENOMEM;
+    for (int64_t i0 = 0; i0 < n && rc == RIFT_OK; i0 += chunk) {
+        const int64_t m = std::min(chunk, n - i0);
+        if (cudaMemcpyAsync(h->theta, theta + 6 * i0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, h->stream) ||
+            launch_coeffs(h->prob, fp64, h->theta, m, c ? dc : nullptr, dt ? ddt : nullptr, quad ? dq : nullptr,
+                          h->stream) ||
+            (c && cudaMemcpyAsync(c + 2 * i0 * K * M, dc, sizeof(double2) * m * K * M, cudaMemcpyDeviceToHost,
+                                  h->stream)) ||
+            (dt && cudaMemcpyAsync(dt + i0 * K, ddt, sizeof(double) * m * K, cudaMemcpyDeviceToHost, h->stream)) ||
+            (quad && cudaMemcpyAsync(quad + i0, dq, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream)))
+            rc = RIFT_ECUDA;
+    }
+    cudaStreamSynchronize(h->stream);
+    for (void *q : tmp)
+        cudaFree(q);
+    h->last_n = 0;
+    cudaGetLastError();
+    return rc;
+}
+
+int rift_ile_marginalize(rift_ile_t *h, int64_t n_samples, rift_ile_result *out)
+{
+    if (!h || n_samples < 1 || n_samples > h->cap)
+        return RIFT_EINVAL;
+    if (!h->have_overlaps)
+        return RIFT_ESTATE;
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    RK(run_iteration(h, n_samples, 0, false, true));
+    return finish_result(h, 1, out);
+}
+
+int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_result *out)
+{
+    if (!h || n_iter < 1 || n_iter > RIFT_MAX_ITER || n_per_iter < 1 || n_per_iter > h->cap)
+        return RIFT_EINVAL;
+    if (!h->have_overlaps)
+        return RIFT_ESTATE;
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    for (int g = 0; g < n_iter; ++g)
+        RK(run_iteration(h, n_per_iter, g, true, g == 0));
+    return finish_result(h, n_iter, out);
+}
+
+int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus_lnps, double *lnL_tmarg, double *lnw,
+                        int64_t *n_out)
+{
+    if (!h || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    const int64_t n = h->last_n;
+    if (n_out)
+        *n_out = n;
+    if (n == 0)
+        return RIFT_ESTATE;
+    const cudaMemcpyKind kind = mem == RIFT_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (theta)
+        CK(cudaMemcpyAsync(theta, h->theta, sizeof(double) * 6 * n, kind, h->stream));
+    if (lnp_minus_lnps)
+        CK(cudaMemcpyAsync(lnp_minus_lnps, h->lnpw, sizeof(double) * n, kind, h->stream));
+    if (lnL_tmarg)
+        CK(cudaMemcpyAsync(lnL_tmarg, h->lnL, sizeof(double) * n, kind, h->stream));
+    if (lnw)
+        CK(cudaMemcpyAsync(lnw, h->lnw, sizeof(double) * n, kind, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RIFT_OK;
+}
+
+int rift_ile_get_sampler(const rift_ile_t *h, double *P)
+{
+    if (!h || !P)
+        return RIFT_EINVAL;
+    CK(cudaMemcpyAsync(P, h->P, sizeof(double) * 6 * h->cfg.n_bins, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RIFT_OK;
+}
+
+int rift_ile_get_state(const rift_ile_t *h, void *buf, size_t *len)
+{
+    if (!h || !len)
+        return RIFT_EINVAL;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * 6 * h->cfg.n_bins;
+    if (!buf) {
+        *len = need;
+        return RIFT_OK;
+    }
+    if (*len < need)
+        return RIFT_EINVAL;
+    StateHeader hd{kStateMagic, kStateVersion, (uint32_t)h->cfg.n_bins, h->cfg.seed, h->iteration, 0};
+    std::memcpy(buf, &hd, sizeof(hd));
+    int rc = rift_ile_get_sampler(h, reinterpret_cast<double *>(static_cast<char *>(buf) + sizeof(hd)));
+    if (rc != RIFT_OK)
+        return rc;
+    *len = need;
+    return RIFT_OK;
+}
+
+int rift_ile_set_state(rift_ile_t *h, const void *buf, size_t len)
+{
+    if (!h || !buf)
+        return RIFT_EINVAL;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * 6 * h->cfg.n_bins;
+    if (len != need)
+        return RIFT_ESTATE;
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.n_bins != (uint32_t)h->cfg.n_bins)
+        return RIFT_ESTATE;
+    const double *P = reinterpret_cast<const double *>(static_cast<const char *>(buf) + sizeof(hd));
+    for (int e = 0; e < 6 * h->cfg.n_bins; ++e)
+        if (!(P[e] >= 0.0) || !std::isfinite(P[e]))
+            return RIFT_ESTATE;
+    h->cfg.seed = hd.seed;
+    h->iteration = hd.iteration;
+    CK(cudaMemcpyAsync(h->P, P, sizeof(double) * 6 * h->cfg.n_bins, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_build_cdf(sampler_of(h), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->last_n = 0;
+    return RIFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Shared device-side definitions of the ILE library (internal, not part of the ABI).
+//
+// Geometry follows arXiv:2505.11655 Sec. II A:
+//   source direction n = (cos d cos(a-g), cos d sin(a-g), sin d), arrival delay
+//   dt_k = -x_k . n / c; complex response F = F_+ - i F_x; harmonic
+//   -2Y_lm(iota, phi_* - phi) with phi_* = 0 (App. conventions, Eq. (hlm));
+//   mode coefficient c_k,lm = (D_ref/D) F_k Y_lm.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rift_ile.h"
+
+namespace rift {
+
+constexpr double kC = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxDet = RIFT_MAX_DET;
+constexpr int kMaxModes = RIFT_MAX_MODES;
+constexpr int kMaxL = 6;        // largest supported l
+constexpr int kMaxWTerms = 5;   // terms of the Wigner-d sum for l <= 6, spin weight -2
+constexpr int kMaxPow = 2 * kMaxL + 2;   // largest power of cos(iota/2), sin(iota/2)
+
+// Error flags raised by kernels (OR-ed into a device word).
+constexpr int kErrRange = 1;
+constexpr int kErrNonFinite = 2;
+
+// Everything a kernel needs about one problem, passed by value (< 4 KB).
+struct Problem {
+    int K, M, n_q, n_t;
+    int n_q_pad;            // row pitch (floats) of the float32 Q planes
+    double fs, t_lo, t_step, gmst, d_ref, kappa;
+    double Dten[kMaxDet][6];   // response tensor: xx, yy, zz, xy, xz, yz
+    double xpos[kMaxDet][3];   // vertex position / c (seconds)
+    double q_t0[kMaxDet];
+    int mode_m[kMaxModes];
+    // -2Y_lm(iota, .) = sum_t wcoef[t] cos(iota/2)^wpc[t] sin(iota/2)^wps[t]  (normalisation folded in)
+    double wcoef[kMaxModes][kMaxWTerms];
+    int8_t wpc[kMaxModes][kMaxWTerms];
+    int8_t wps[kMaxModes][kMaxWTerms];
+    int8_t wn[kMaxModes];
+    const double2 *Q64;     // [K][M][n_q]
+    const double2 *U64;     // [K][M][M]
+    const double2 *V64;
+    const float *Qr32;      // [K][2M][n_q_pad] split planes, zero padded
+    const float2 *U32;
+    const float2 *V32;
+};
+
+// ---------------------------------------------------------------- complex helpers
+template <typename T> struct Cx { T re, im; };
+
+template <typename T> __device__ __forceinline__ Cx<T> cmul(Cx<T> a, Cx<T> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+__device__ __forceinline__ void sincos_t(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float *s, float *c) { sincosf(x, s, c); }
+
+// ---------------------------------------------------------------- sky geometry
+// Sky trigonometry of one sample, evaluated once in float64.
+struct Sky {
+    double cd, sd, ch, sh;   // cos/sin of declination and of (alpha - gmst)
+};
+
+__device__ __forceinline__ Sky sky_of(double alpha, double delta, double gmst)
+{
+    Sky s;
+    sincos(delta, &s.sd, &s.cd);
+    sincos(alpha - gmst, &s.sh, &s.ch);
+    return s;
+}
+
+// dt_k = -(x_k . n) / c  (x stored already divided by c).
+__device__ __forceinline__ double arrival_delay(const Problem &P, int k, const Sky &s)
+{
+    return -(P.xpos[k][0] * s.cd * s.ch + P.xpos[k][1] * s.cd * s.sh + P.xpos[k][2] * s.sd);
+}
+
+// Complex response F = F_+ - i F_x for polarisation psi.  With the sky basis
+//   e_a = (-sin h, cos h, 0), e_d = (-sin d cos h, -sin d sin h, cos d)
+// and A = e_a.D.e_a, B = e_d.D.e_d, C = e_a.D.e_d, the polarisation frame
+// X = -cos psi e_a + sin psi e_d, Y = sin psi e_a + cos psi e_d gives
+//   F_+ = cos 2psi (A - B) - 2 sin 2psi C,   F_x = -sin 2psi (A - B) - 2 cos 2psi C,
+// i.e. F = (A - B + 2 i C) exp(2 i psi).
+template <typename T>
+__device__ __forceinline__ Cx<T> response(const Problem &P, int k, const Sky &s, T c2psi, T s2psi)
+{
+    const double *D = P.Dten[k];
+    T ea0 = (T)(-s.sh), ea1 = (T)s.ch;
+    T ed0 = (T)(-s.sd * s.ch), ed1 = (T)(-s.sd * s.sh), ed2 = (T)s.cd;
+    T xx = (T)D[0], yy = (T)D[1], zz = (T)D[2], xy = (T)D[3], xz = (T)D[4], yz = (T)D[5];
+    // D e_a and D e_d
+    T da0 = xx * ea0 + xy * ea1, da1 = xy * ea0 + yy * ea1, da2 = xz * ea0 + yz * ea1;
+    T dd0 = xx * ed0 + xy * ed1 + xz * ed2;
+    T dd1 = xy * ed0 + yy * ed1 + yz * ed2;
+    T dd2 = xz * ed0 + yz * ed1 + zz * ed2;
+    T A = ea0 * da0 + ea1 * da1;
+    T B = ed0 * dd0 + ed1 * dd1 + ed2 * dd2;
+    T Cc = ed0 * da0 + ed1 * da1 + ed2 * da2;
+    T pr = A - B, pi = (T)2 * Cc;
+    return {pr * c2psi - pi * s2psi, pr * s2psi + pi * c2psi};
+}
+
+// -2Y_lm(iota, -phi) for mode index mi, given powers of cos(iota/2), sin(iota/2).
+template <typename T>
+__device__ __forceinline__ Cx<T> harmonic(const Problem &P, int mi, const T *cpow, const T *spow, T phi)
+{
+    T d = 0;
+    for (int t = 0; t < P.wn[mi]; ++t)
+        d += (T)P.wcoef[mi][t] * cpow[P.wpc[mi][t]] * spow[P.wps[mi][t]];
+    T sp, cp;
+    sincos_t(-(T)P.mode_m[mi] * phi, &sp, &cp);
+    return {d * cp, d * sp};
+}
+
+template <typename T>
+__device__ __forceinline__ void half_angle_powers(T iota, T *cpow, T *spow)
+{
+    T sh, ch;
+    sincos_t((T)0.5 * iota, &sh, &ch);
+    cpow[0] = 1;
+    spow[0] = 1;
+#pragma unroll
+    for (int p = 1; p <= kMaxPow; ++p) {
+        cpow[p] = cpow[p - 1] * ch;
+        spow[p] = spow[p - 1] * sh;
+    }
+}
+
+// ---------------------------------------------------------------- counter-based RNG
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
+// multiplies, key advanced by the Weyl increments between rounds.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = {hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// 53-bit uniform in [0, 1) from two words (27 high bits of a, 26 of b).
+__device__ __forceinline__ double unit53(uint32_t a, uint32_t b)
+{
+    unsigned long long v = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+    return (double)v * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------- sort key
+// Sky cell of a sample in a 128 x 128 grid over (sin delta, alpha), visited in
+// boustrophedon order so that consecutive cells are neighbours on the sky and
+// samples close in key have close arrival delays at every detector.
+constexpr int kCellSide = 128;
+constexpr int kCells = kCellSide * kCellSide;
+
+__device__ __forceinline__ uint32_t sky_cell(double alpha, double delta)
+{
+    double z = 0.5 * (sin(delta) + 1.0);
+    double a = alpha * (1.0 / (2.0 * kPi));
+    a -= floor(a);
+    int r = min(kCellSide - 1, max(0, (int)(z * kCellSide)));
+    int c = min(kCellSide - 1, max(0, (int)(a * kCellSide)));
+    if (r & 1)
+        c = kCellSide - 1 - c;
+    return (uint32_t)(r * kCellSide + c);
+}
+
+}  // namespace rift

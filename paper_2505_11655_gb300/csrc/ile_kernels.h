@@ -1,0 +1,62 @@
+// Internal launcher interface between the host core and the kernel translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ile_common.cuh"
+
+namespace rift {
+
+// Per-bin split of j * beta (beta = bin spacing x fs): j*beta = bin_i[j] + bin_f[j], 0 <= bin_f < 1.
+struct BinTable {
+    const int *bin_i;
+    const float *bin_f;
+};
+
+// ln L over the time grid for n samples theta[n][6] (float64 everywhere).
+//   lnL_tmarg[n] (required), lnL_t[n][n_t] (optional), lnw[i] = lnL_tmarg[i] + lnpw[i] when both given.
+cudaError_t launch_lnl_fp64(const Problem &P, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
+                            const double *lnpw, double *lnw, int *err, cudaStream_t st);
+
+// Float32 tiled path.  perm[n] lists sample indices in sky-cell order; outputs are
+// written at the original index.
+cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
+                            double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
+                            cudaStream_t st);
+size_t lnl_fp32_smem_bytes(const Problem &P);
+
+// Per-sample coefficients: c[n][K][M] (complex), dt[n][K], quad[n]; any may be null.
+cudaError_t launch_coeffs(const Problem &P, bool fp64, const double *theta, int64_t n, double2 *c, double *dt,
+                          double *quad, cudaStream_t st);
+
+// ---- sampler, sort and reductions ----------------------------------------------------------
+struct SamplerDev {
+    double *P;       // [6][B] masses
+    double *C;       // [6][B+1] running sums
+    int B;
+    double d_min, d_max;
+    double floor_eps, temper;
+    uint64_t seed;
+};
+
+cudaError_t launch_draw(const SamplerDev &S, uint32_t iter, int64_t n, double *theta, double *lnpw, uint64_t *bins,
+                        uint32_t *key, cudaStream_t st);
+cudaError_t launch_keys(const double *theta, int64_t n, uint32_t *key, cudaStream_t st);
+// Counting sort of keys into perm (scratch: counts[kCells + 1]).
+cudaError_t launch_sort(const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm, cudaStream_t st);
+
+// Reduction of ln w and ln L_tmarg for iteration slot `slot`:
+//   stats[slot*8 + 0..7] = lnZ, sigma, n_eff, n_ess, max lnw, max lnL, N, (unused)
+//   pooled[0..4] = running max lnw, s1, s2 (relative to the max), N, max lnL over all slots.
+constexpr int kRedBlocks = 304;
+cudaError_t launch_reduce(const double *lnw, const double *lnL, int64_t n, double *partial, double *stats, int slot,
+                          double *pooled, int reset_pooled, int *err, cudaStream_t st);
+// Histogram adaptation of the sampler from weights exp(beta (lnw - max lnw)) (max from stats[slot]).
+cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
+                         int slot, double *hist_partial, cudaStream_t st);
+cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st);
+// Final pooled statistics into out[0..7] = lnZ, sigma, n_eff, n_ess, max lnL, N.
+cudaError_t launch_pooled_final(const double *pooled, double *out, cudaStream_t st);
+
+}  // namespace rift

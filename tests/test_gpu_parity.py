@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, on the
+same seeded inputs.
+
+Tolerances:
+  * RIFT_FP64 path: 1e-9 relative on every ln L value and on ln Z.
+  * RIFT_FP32 path: |d ln L| <= 1e-3 and |d ln Z| <= 1e-3 (absolute), at SNR 20.
+  * Integer and index work (sample streams, histogram bins) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ile_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2505_11655_gb300 as G
+    G.load(build_if_missing=True)
+    return G
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_lib):
+    return oracle_lib
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))
+
+
+# ------------------------------------------------------------------------------ FP64 plain path
+
+def test_fp64_coeffs_match_oracle(G, orc):
+    p = S.single_large_problem()
+    th = S.prior_samples(500, 31)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=1000) as s:
+        c, dt, quad = s.coeffs(th)
+    _, _, oc, odt = orc.coeffs(p, th)
+    _, _, oquad = orc.lnL(p, th, want_bins=True)
+    assert np.max(np.abs(c - oc)) < 1e-12 * max(1.0, np.max(np.abs(oc)))
+    assert np.max(np.abs(dt - odt)) < 1e-15
+    assert rel(quad, oquad) < 1e-11
+
+
+def test_fp64_eval_plain_config(G, orc):
+    """Two detectors, modes (2,+-2), 401 bins: every sample and every bin."""
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(10000, 32)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=4096) as s:
+        got = s.eval(th)
+        gb, gbins = s.eval(th[:300], want_bins=True)
+    exp = orc.lnL(p, th)
+    assert rel(got, exp) < 1e-9
+    eb, ebins, _ = orc.lnL(p, th[:300], want_bins=True)
+    assert rel(gbins, ebins) < 1e-9
+    assert np.array_equal(gb, got[:300])
+
+
+def test_fp64_eval_all_modes(G, orc):
+    p = S.single_large_problem()
+    th = S.prior_samples(700, 33)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=256) as s:
+        got, gbins = s.eval(th, want_bins=True)
+    exp, ebins, _ = orc.lnL(p, th, want_bins=True)
+    assert rel(got, exp) < 1e-9
+    assert rel(gbins, ebins) < 1e-9
+
+
+def test_fp64_marginalize_same_stream_as_oracle(G, orc):
+    """The device's Philox stream and inverse-CDF draw equal the oracle's; the
+    histogram bins and ln p - ln p_s agree exactly; ln Z to 1e-9."""
+    p = S.plain_fp64_problem()
+    n = 10000
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=32, seed=1234) as s:
+        r = s.marginalize(n)
+        th, lr, ll, lw = s.last_batch(n)
+    sm = orc.Sampler(n_bins=32, seed=1234)
+    oth, olr, obins = sm.draw(n)
+    assert np.max(np.abs(th - oth)) < 1e-12
+    assert np.array_equal(lr, olr)
+    oll = orc.lnL(p, oth)
+    assert rel(ll, oll) < 1e-9
+    red = orc.reduce(oll + olr)
+    assert abs(r["lnZ"] - red["lnZ"]) < 1e-9 * max(1, abs(red["lnZ"]))
+    assert abs(r["n_eff"] - red["n_eff"]) < 1e-9 * red["n_eff"]
+    assert abs(r["n_ess"] - red["n_ess"]) < 1e-9 * red["n_ess"]
+    assert abs(r["sigma_lnZ"] - red["sigma_lnZ"]) < 1e-9
+
+
+def test_fp64_adapt_matches_oracle_loop(G, orc):
+    """Three adaptive iterations: per-iteration ln Z, pooled ln Z and the
+    adapted histogram masses follow the oracle's loop."""
+    p = S.plain_fp64_problem()
+    n, iters = 20000, 3
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=24, seed=99, adapt_floor=0.1) as s:
+        r = s.adapt(iters, n)
+        P = s.sampler()
+    sm = orc.Sampler(n_bins=24, seed=99, floor=0.1)
+    ref = orc.run_adapt(p, sm, iters, n)
+    for g in range(iters):
+        assert abs(r["lnZ_iter"][g] - ref["iterations"][g]["lnZ"]) < 1e-9 * max(1, abs(ref["iterations"][g]["lnZ"]))
+    assert abs(r["lnZ"] - ref["pooled"]["lnZ"]) < 1e-9 * max(1, abs(ref["pooled"]["lnZ"]))
+    assert abs(r["n_eff"] - ref["pooled"]["n_eff"]) < 1e-8 * ref["pooled"]["n_eff"]
+    assert r["n_total"] == n * iters
+    assert np.max(np.abs(P - sm.P)) < 1e-12
+
+
+# ------------------------------------------------------------------------------ FP32 path
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 3001])
+def test_fp32_eval_sizes_single_large(G, orc, n):
+    """21 modes, 3 detectors, 1001 bins; sizes across tile boundaries and a ragged tail."""
+    p = S.single_large_problem()
+    th = S.prior_samples(n, 40 + n)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
+        got = s.eval(th)
+    exp = orc.lnL(p, th)
+    assert np.max(np.abs(got - exp)) <= 1e-3
+
+
+def test_fp32_bins_match(G, orc):
+    p = S.single_large_problem()
+    th = S.prior_samples(200, 41)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
+        got, gbins = s.eval(th, want_bins=True)
+    exp, ebins, _ = orc.lnL(p, th, want_bins=True)
+    assert np.max(np.abs(gbins - ebins)) <= 1e-3
+    assert np.max(np.abs(got - exp)) <= 1e-3
+
+
+def test_fp32_plain_config_and_batching(G, orc):
+    """Few modes, and n above max_samples (the call processes several batches)."""
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(5000, 42)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=1024) as s:
+        got = s.eval(th)
+    assert np.max(np.abs(got - orc.lnL(p, th))) <= 1e-3
+
+
+def test_fp32_unsorted_sky_and_polar_caps(G, orc):
+    """Samples spread over the whole sky in one batch (tiles straddling cells),
+    plus samples near the poles and at alpha = 0 / 2 pi."""
+    p = S.single_large_problem()
+    th = S.prior_samples(1500, 43)
+    th[:200, 1] = np.sign(th[:200, 1]) * (math.pi / 2 - np.abs(th[:200, 1]) * 1e-3)
+    th[200:300, 0] = np.where(np.arange(100) % 2, 1e-9, 2 * math.pi - 1e-9)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
+        got = s.eval(th)
+    assert np.max(np.abs(got - orc.lnL(p, th))) <= 1e-3
+
+
+def test_fp32_device_memory_inputs(G, orc):
+    import torch
+    p = S.single_large_problem()
+    th = S.prior_samples(777, 44)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=512) as s:
+        tt = torch.from_numpy(th).cuda()
+        got = s.eval(tt).cpu().numpy()
+        got_host = s.eval(th)
+    assert np.max(np.abs(got - orc.lnL(p, th))) <= 1e-3
+    assert np.max(np.abs(got - got_host)) <= 1e-5
+
+
+def test_fp32_marginalize_against_oracle_on_device_stream(G, orc):
+    """ln Z of one batch: the oracle re-evaluates the device's own theta stream."""
+    p = S.single_large_problem()
+    n = 20000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=5) as s:
+        r = s.marginalize(n)
+        th, lr, ll, lw = s.last_batch(n)
+    oll = orc.lnL(p, th)
+    assert np.max(np.abs(ll - oll)) <= 1e-3
+    red = orc.reduce(oll + lr)
+    assert abs(r["lnZ"] - red["lnZ"]) <= 1e-3
+    assert abs(r["n_eff"] - red["n_eff"]) <= 1e-2 * red["n_eff"]
+
+
+def test_fp32_adapt_two_iterations(G, orc):
+    p = S.single_large_problem()
+    n = 30000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=6) as s:
+        r = s.adapt(2, n)
+        th, lr, ll, lw = s.last_batch(n)
+    oll = orc.lnL(p, th)
+    red = orc.reduce(oll + lr)
+    assert abs(r["lnZ_iter"][1] - red["lnZ"]) <= 1e-3
+    assert r["n_total"] == 2 * n
+
+
+# ------------------------------------------------------------------------------ full size
+
+@pytest.mark.slow
+def test_full_size_single_large_sampled(G, orc):
+    """1e6 samples, 3 detectors, 21 modes, 1001 bins, the benchmark's launch
+    configuration: 4000 sampled outputs against the oracle one by one, and
+    ln Z against the reduction of the device's own per-sample values."""
+    p = S.single_large_problem()
+    n = 1_000_000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=7) as s:
+        r = s.marginalize(n)
+        th, lr, ll, lw = s.last_batch(n)
+    idx = np.random.default_rng(0).choice(n, 4000, replace=False)
+    assert np.max(np.abs(ll[idx] - orc.lnL(p, th[idx]))) <= 1e-3
+    red = orc.reduce(lw)
+    assert abs(r["lnZ"] - red["lnZ"]) <= 1e-9 * max(1, abs(red["lnZ"]))
+    assert r["n_total"] == n
+
+
+# ------------------------------------------------------------------------------ edges and state
+
+def test_empty_and_errors(G):
+    p = S.plain_fp64_problem()
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=100) as s:
+        out = s.eval(np.zeros((0, 6)))
+        assert out.shape == (0,)
+        with pytest.raises(G.RiftError) as e:
+            s.marginalize(101)
+        assert e.value.code == G.RIFT_EINVAL
+        with pytest.raises(G.RiftError) as e:
+            s.adapt(0, 10)
+        assert e.value.code == G.RIFT_EINVAL
+        Qbad = p.Q.copy()
+        Qbad[0, 0, 5] = np.nan
+        with pytest.raises(G.RiftError) as e:
+            s.set_overlaps(Qbad, p.U, p.V)
+        assert e.value.code == G.RIFT_ENONFINITE
+        Ubad = p.U.copy()
+        Ubad[0, 0, 1] += 1.0
+        with pytest.raises(G.RiftError) as e:
+            s.set_overlaps(p.Q, Ubad, p.V)
+        assert e.value.code == G.RIFT_EINVAL
+
+
+def test_no_overlaps_is_state_error(G):
+    p = S.plain_fp64_problem()
+    s = G.ILE(p, precision=G.RIFT_FP32, max_samples=100, set_overlaps=False)
+    with pytest.raises(G.RiftError) as e:
+        s.eval(S.prior_samples(3, 1))
+    assert e.value.code == G.RIFT_ESTATE
+    s.close()
+
+
+def test_checkpoint_resume_reproduces_stream(G):
+    """get_state after one adaptation, then: continuing, and restoring the
+    state in a fresh handle, give the same next batch."""
+    p = S.plain_fp64_problem()
+    n = 5000
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=16, seed=11) as a:
+        a.adapt(1, n)
+        blob = a.get_state()
+        ra = a.marginalize(n)
+        tha = a.last_batch(n)[0]
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=16, seed=999) as b:
+        b.set_state(blob)
+        rb = b.marginalize(n)
+        thb = b.last_batch(n)[0]
+        with pytest.raises(G.RiftError):
+            b.set_state(blob[:-8])
+    assert np.array_equal(tha, thb)
+    assert ra["lnZ"] == rb["lnZ"]
+
+
+def test_quad_norm_half_with_half_grams(G):
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(300, 50)
+    import copy
+    h = copy.copy(p)
+    h.quad_norm = 1
+    h.U, h.V = p.U / 2, p.V / 2
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=512) as a, G.ILE(h, precision=G.RIFT_FP64, max_samples=512) as b:
+        assert rel(a.eval(th), b.eval(th)) < 1e-11
