@@ -50,6 +50,9 @@ struct rift_ile {
     double *theta = nullptr, *lnpw = nullptr, *lnL = nullptr, *lnw = nullptr;
     uint64_t *bins = nullptr;
     uint32_t *key = nullptr, *perm = nullptr, *counts = nullptr;
+    int *row_off = nullptr, *tile_counter = nullptr;
+    std::vector<int> row_host;   // sky grid of the current batch size
+    SkyGrid grid{0, 0, nullptr};
     // reductions and sampler
     double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
     double *P = nullptr, *C = nullptr;
@@ -258,6 +261,20 @@ int sync_and_err(rift_ile_t *h, int *flags_out = nullptr)
 
 bool use_fp32(const rift_ile_t *h) { return h->cfg.precision != RIFT_FP64; }
 
+// Sky grid sized for a batch of n samples; uploads the row table when it changes.
+int grid_for_batch(rift_ile_t *h, int64_t n)
+{
+    std::vector<int> off(kMaxRows + 1);
+    const int rows = sky_grid_rows(n, off.data());
+    if (rows != h->grid.rows) {
+        h->row_host.assign(off.begin(), off.begin() + rows + 1);
+        CK(cudaMemcpyAsync(h->row_off, h->row_host.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice,
+                           h->stream));
+        h->grid = SkyGrid{rows, h->row_host[rows], h->row_off};
+    }
+    return RIFT_OK;
+}
+
 // ln L for n device-resident samples (theta [n][6]); perm/key scratch from the handle.
 int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t, const double *lnpw,
                 double *lnw)
@@ -268,10 +285,11 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
         return RIFT_OK;
     }
     h->launches += 5;   // keys, count, scan, scatter, tiled likelihood
-    CK(launch_keys(theta, n, h->key, h->stream));
-    CK(launch_sort(h->key, n, h->counts, h->perm, h->stream));
+    RK(grid_for_batch(h, n));
+    CK(launch_keys(h->grid, theta, n, h->key, h->stream));
+    CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
     CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err,
-                       h->stream));
+                       h->tile_counter, h->stream));
     return RIFT_OK;
 }
 
@@ -279,14 +297,15 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
 int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_pooled)
 {
     SamplerDev S = sampler_of(h);
+    RK(grid_for_batch(h, n));
     CK(cudaEventRecord(h->ev[slot][0], h->stream));
-    CK(launch_draw(S, h->iteration, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    CK(launch_draw(S, h->grid, h->iteration, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
     if (use_fp32(h))
-        CK(launch_sort(h->key, n, h->counts, h->perm, h->stream));
+        CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
     CK(cudaEventRecord(h->ev[slot][1], h->stream));
     if (use_fp32(h))
         CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, h->theta, h->perm, n, h->lnL, nullptr, h->lnpw,
-                           h->lnw, h->err, h->stream));
+                           h->lnw, h->err, h->tile_counter, h->stream));
     else
         CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
     CK(cudaEventRecord(h->ev[slot][2], h->stream));
@@ -435,7 +454,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->theta, (size_t)N * 6)) || (rc = dalloc(h, &h->lnpw, (size_t)N)) ||
         (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
         (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
-        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kCells + 1)) ||
+        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1)) ||
+        (rc = dalloc(h, &h->row_off, (size_t)kMaxRows + 1)) || (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
         (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||
         (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
         (rc = dalloc(h, &h->stats, (size_t)8 * RIFT_MAX_ITER)) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||

@@ -156,22 +156,32 @@ __device__ __forceinline__ double unit53(uint32_t a, uint32_t b)
 }
 
 // ---------------------------------------------------------------- sort key
-// Sky cell of a sample in a 128 x 128 grid over (sin delta, alpha), visited in
-// boustrophedon order so that consecutive cells are neighbours on the sky and
-// samples close in key have close arrival delays at every detector.
-constexpr int kCellSide = 128;
-constexpr int kCells = kCellSide * kCellSide;
+// Sky cell of a sample on a near-equal-area grid: `rows` bands of equal
+// declination width, band r split into row_off[r+1] - row_off[r] cells of equal
+// right-ascension width (about 2 rows cos(delta_r) of them), so cells are
+// roughly square.  Bands are visited in boustrophedon order so that consecutive
+// cells are neighbours on the sky and samples close in key have close arrival
+// delays at every detector.
+constexpr int kMaxCells = 1 << 17;
+constexpr int kMaxRows = 256;
 
-__device__ __forceinline__ uint32_t sky_cell(double alpha, double delta)
+struct SkyGrid {
+    int rows;
+    int n_cells;
+    const int *row_off;   // [rows + 1]
+};
+
+__device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const SkyGrid &G)
 {
-    double z = 0.5 * (sin(delta) + 1.0);
+    int r = (int)((delta * (1.0 / kPi) + 0.5) * G.rows);
+    r = min(G.rows - 1, max(0, r));
+    const int o0 = __ldg(G.row_off + r), na = __ldg(G.row_off + r + 1) - o0;
     double a = alpha * (1.0 / (2.0 * kPi));
     a -= floor(a);
-    int r = min(kCellSide - 1, max(0, (int)(z * kCellSide)));
-    int c = min(kCellSide - 1, max(0, (int)(a * kCellSide)));
+    int c = min(na - 1, max(0, (int)(a * na)));
     if (r & 1)
-        c = kCellSide - 1 - c;
-    return (uint32_t)(r * kCellSide + c);
+        c = na - 1 - c;
+    return (uint32_t)(o0 + c);
 }
 
 }  // namespace rift

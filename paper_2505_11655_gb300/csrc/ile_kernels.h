@@ -20,10 +20,10 @@ cudaError_t launch_lnl_fp64(const Problem &P, const double *theta, int64_t n, do
                             const double *lnpw, double *lnw, int *err, cudaStream_t st);
 
 // Float32 tiled path.  perm[n] lists sample indices in sky-cell order; outputs are
-// written at the original index.
+// written at the original index.  tile_counter: one device int (reset by the launcher).
 cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                             double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
-                            cudaStream_t st);
+                            int *tile_counter, cudaStream_t st);
 size_t lnl_fp32_smem_bytes(const Problem &P);
 
 // Per-sample coefficients: c[n][K][M] (complex), dt[n][K], quad[n]; any may be null.
@@ -40,11 +40,15 @@ struct SamplerDev {
     uint64_t seed;
 };
 
-cudaError_t launch_draw(const SamplerDev &S, uint32_t iter, int64_t n, double *theta, double *lnpw, uint64_t *bins,
-                        uint32_t *key, cudaStream_t st);
-cudaError_t launch_keys(const double *theta, int64_t n, uint32_t *key, cudaStream_t st);
-// Counting sort of keys into perm (scratch: counts[kCells + 1]).
-cudaError_t launch_sort(const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm, cudaStream_t st);
+cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, int64_t n, double *theta, double *lnpw,
+                        uint64_t *bins, uint32_t *key, cudaStream_t st);
+cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32_t *key, cudaStream_t st);
+// Counting sort of keys (< G.n_cells) into perm (scratch: counts[G.n_cells + 1]).
+cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
+                        cudaStream_t st);
+// Rows of the sky grid for a batch of n samples (about 40 samples per cell) and
+// the cumulative cell offsets of those rows (host side).
+int sky_grid_rows(int64_t n, int *row_off /*[kMaxRows + 1]*/);
 
 // Reduction of ln w and ln L_tmarg for iteration slot `slot`:
 //   stats[slot*8 + 0..7] = lnZ, sigma, n_eff, n_ess, max lnw, max lnL, N, (unused)

@@ -8,6 +8,7 @@
 //               n_ESS = (sum w)^2 / sum w^2 (Sec. IV A), all in float64, deterministic
 //               two-level reductions.
 //   adapt     - 1-D weighted histograms of the weights, mixed with a uniform floor.
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -19,7 +20,7 @@ namespace rift {
 
 constexpr int kDrawThreads = 256;
 
-__global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, uint32_t iter, int64_t n,
+__global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGrid G, uint32_t iter, int64_t n,
                                                             double *__restrict__ theta, double *__restrict__ lnpw,
                                                             uint64_t *__restrict__ bins, uint32_t *__restrict__ key)
 {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, uint32
             out[d] = th[d];
         lnpw[i] = lr;
         bins[i] = packed;
-        key[i] = sky_cell(th[0], th[1]);
+        key[i] = sky_cell(th[0], th[1], G);
     }
 }
 
@@ -99,8 +100,8 @@ static int grid_for(int64_t n, int threads, int per_sm)
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-cudaError_t launch_draw(const SamplerDev &S, uint32_t iter, int64_t n, double *theta, double *lnpw, uint64_t *bins,
-                        uint32_t *key, cudaStream_t st)
+cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, int64_t n, double *theta, double *lnpw,
+                        uint64_t *bins, uint32_t *key, cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -110,22 +111,35 @@ cudaError_t launch_draw(const SamplerDev &S, uint32_t iter, int64_t n, double *t
         if (e != cudaSuccess)
             return e;
     }
-    draw_kernel<<<grid_for(n, kDrawThreads, 8), kDrawThreads, smem, st>>>(S, iter, n, theta, lnpw, bins, key);
+    draw_kernel<<<grid_for(n, kDrawThreads, 8), kDrawThreads, smem, st>>>(S, G, iter, n, theta, lnpw, bins, key);
     return cudaGetLastError();
 }
 
-__global__ void keys_kernel(const double *__restrict__ theta, int64_t n, uint32_t *__restrict__ key)
+__global__ void keys_kernel(SkyGrid G, const double *__restrict__ theta, int64_t n, uint32_t *__restrict__ key)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        key[i] = sky_cell(theta[6 * i], theta[6 * i + 1]);
+        key[i] = sky_cell(theta[6 * i], theta[6 * i + 1], G);
 }
 
-cudaError_t launch_keys(const double *theta, int64_t n, uint32_t *key, cudaStream_t st)
+cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32_t *key, cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
-    keys_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(theta, n, key);
+    keys_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(G, theta, n, key);
     return cudaGetLastError();
+}
+
+int sky_grid_rows(int64_t n, int *row_off)
+{
+    int rows = (int)std::lround(std::sqrt((double)n / 40.0));
+    rows = std::max(4, std::min(kMaxRows, rows));
+    row_off[0] = 0;
+    for (int r = 0; r < rows; ++r) {
+        const double dc = -0.5 * kPi + (r + 0.5) * kPi / rows;
+        const int na = std::max(1, (int)std::lround(2.0 * rows * std::cos(dc)));
+        row_off[r + 1] = row_off[r] + na;
+    }
+    return rows;
 }
 
 // ======================================================================== counting sort by sky cell
@@ -136,20 +150,18 @@ __global__ void count_kernel(const uint32_t *__restrict__ key, int64_t n, uint32
         atomicAdd(counts + key[i], 1u);
 }
 
-// Exclusive scan of kCells counts by one block of 1024 threads (16 cells each).
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *counts)
+// Exclusive scan of n_cells counts by one block of 1024 threads, each owning a
+// contiguous segment: segment totals, a block scan of the totals, then a second
+// pass over the segment writing running offsets.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *counts, int n_cells)
 {
-    constexpr int per = kCells / 1024;
     __shared__ uint32_t warp_tot[32];
     const int t = threadIdx.x;
-    uint32_t loc[per];
+    const int per = (n_cells + 1023) / 1024;
+    const int b0 = min(n_cells, t * per), b1 = min(n_cells, b0 + per);
     uint32_t run = 0;
-#pragma unroll
-    for (int i = 0; i < per; ++i) {
-        loc[i] = run;
-        run += counts[t * per + i];
-    }
-    // inclusive scan of `run` across the block
+    for (int i = b0; i < b1; ++i)
+        run += counts[i];
     uint32_t v = run;
     const int lane = t & 31, w = t >> 5;
 #pragma unroll
@@ -172,10 +184,12 @@ __global__ void __launch_bounds__(1024) scan_kernel(uint32_t *counts)
         warp_tot[lane] = x;
     }
     __syncthreads();
-    uint32_t excl = v - run + (w > 0 ? warp_tot[w - 1] : 0u);
-#pragma unroll
-    for (int i = 0; i < per; ++i)
-        counts[t * per + i] = excl + loc[i];
+    uint32_t off = v - run + (w > 0 ? warp_tot[w - 1] : 0u);
+    for (int i = b0; i < b1; ++i) {
+        uint32_t c = counts[i];
+        counts[i] = off;
+        off += c;
+    }
 }
 
 __global__ void scatter_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ offs,
@@ -187,16 +201,17 @@ __global__ void scatter_kernel(const uint32_t *__restrict__ key, int64_t n, uint
     }
 }
 
-cudaError_t launch_sort(const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm, cudaStream_t st)
+cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
+                        cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (kCells + 1), st);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (G.n_cells + 1), st);
     if (e != cudaSuccess)
         return e;
     const int g = grid_for(n, 256, 8);
     count_kernel<<<g, 256, 0, st>>>(key, n, counts);
-    scan_kernel<<<1, 1024, 0, st>>>(counts);
+    scan_kernel<<<1, 1024, 0, st>>>(counts, G.n_cells);
     scatter_kernel<<<g, 256, 0, st>>>(key, n, counts, perm);
     return cudaGetLastError();
 }

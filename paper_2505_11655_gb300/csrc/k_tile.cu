@@ -1,0 +1,460 @@
+// Float32 tiled likelihood kernel of the ILE hot path (arXiv:2505.11655 Sec. II A,
+// Eq. (def:lnL:Decomposed), time-marginalised on a uniform grid).
+//
+// Samples arrive sorted by sky cell, so the kTS = 64 samples of a tile need nearly
+// the same Q window at every detector.  Per tile:
+//   1. prologue (all 256 threads): float64 sky trigonometry and arrival delays,
+//      float32 responses F_k and harmonics Y_lm, coefficients c_k,lm = x F_k Y_lm
+//      as real components C[s, r] (r = 2m: Re, 2m+1: Im), template term.
+//   2. for each chunk of time bins and each detector, on the Q sample grid
+//         R[s, c] = sum_r C[s, r] Qr[r, iw0 + c]     (= Re sum_lm conj(c_lm) Q_lm)
+//      as a register-blocked 64 x 256 x 2M contraction from shared memory, the
+//      next detector's Q window streaming in by cp.async meanwhile; then R is
+//      interpolated linearly at every bin's shifted time (interpolation commutes
+//      with the mode sum) and summed over detectors;
+//   3. the template term is subtracted and each chunk is folded into a per-sample
+//      online log-sum-exp; ln L_tmarg = max + ln(sum) - ln n_t in float64.
+// Tiles are handed out by an atomic counter (persistent CTAs, one per SM).
+#include <cfloat>
+#include <cmath>
+
+#include "ile_kernels.h"
+
+namespace rift {
+
+constexpr int kTS = 64;          // samples per tile
+constexpr int kNCol = 256;       // Q window columns per chunk
+constexpr int kColGroups = kNCol / 32;
+constexpr int kTThreads = 256;   // 8 warps
+constexpr int kBinsPerLane = 5;  // a chunk holds <= 160 bins
+constexpr int kMaxChunkBins = 32 * kBinsPerLane;
+
+struct TileLayout {
+    size_t cs, qb0, qb1, r, bini, binf, sky, par, fx, i0, f0, quad, gid, end;
+};
+
+__host__ __device__ inline size_t al16(size_t o) { return (o + 15) & ~(size_t)15; }
+
+__host__ __device__ inline TileLayout tile_layout(int K, int M, int n_t, bool dbuf)
+{
+    TileLayout L;
+    size_t o = 0;
+    L.cs = o;  o = al16(o + (size_t)K * 2 * M * kTS * 4);
+    L.qb0 = o; o = al16(o + (size_t)2 * M * kNCol * 4);
+    L.qb1 = o; if (dbuf) o = al16(o + (size_t)2 * M * kNCol * 4);
+    L.r = o;   o = al16(o + (size_t)kTS * kNCol * 4);
+    L.bini = o; o = al16(o + (size_t)n_t * 4);
+    L.binf = o; o = al16(o + (size_t)n_t * 4);
+    L.sky = o; o = al16(o + (size_t)kTS * 4 * 8);     // cos d, sin d, cos h, sin h (float64)
+    L.par = o; o = al16(o + (size_t)kTS * 8 * 4);     // c2psi, s2psi, x, phi, cos(i/2), sin(i/2) (float32)
+    L.fx = o;  o = al16(o + (size_t)K * kTS * 8);     // x F_k (float2)
+    L.i0 = o;  o = al16(o + (size_t)K * kTS * 4);
+    L.f0 = o;  o = al16(o + (size_t)K * kTS * 4);
+    L.quad = o; o = al16(o + (size_t)kTS * 4);
+    L.gid = o; o = al16(o + (size_t)kTS * 4);
+    L.end = o;
+    return L;
+}
+
+static bool tile_dbuf(const Problem &P, int max_smem)
+{
+    return tile_layout(P.K, P.M, P.n_t, true).end <= (size_t)max_smem;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ float ipow(float b, int e)
+{
+    float r = 1.f;
+    for (int i = 0; i < e; ++i)
+        r *= b;
+    return r;
+}
+
+template <bool kDbuf>
+__global__ void __launch_bounds__(kTThreads, 1)
+lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const uint32_t *__restrict__ perm, int64_t n,
+                double *__restrict__ lnL_tmarg, double *__restrict__ lnL_t, const double *__restrict__ lnpw,
+                double *__restrict__ lnw, int *err, int *tile_counter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int K = P.K, M = P.M, R2 = 2 * M, NT = P.n_t;
+    const TileLayout L = tile_layout(K, M, NT, kDbuf);
+    float *Cs = reinterpret_cast<float *>(smraw + L.cs);        // [K][2M][kTS]
+    float *Qb[2] = {reinterpret_cast<float *>(smraw + L.qb0), reinterpret_cast<float *>(smraw + (kDbuf ? L.qb1 : L.qb0))};
+    float *Rs = reinterpret_cast<float *>(smraw + L.r);         // [kTS][kNCol]
+    int *bini = reinterpret_cast<int *>(smraw + L.bini);
+    float *binf = reinterpret_cast<float *>(smraw + L.binf);
+    double *sky = reinterpret_cast<double *>(smraw + L.sky);    // [kTS][4]
+    float *par = reinterpret_cast<float *>(smraw + L.par);      // [kTS][8]
+    float2 *fx = reinterpret_cast<float2 *>(smraw + L.fx);      // [K][kTS]
+    int *i0s = reinterpret_cast<int *>(smraw + L.i0);           // [K][kTS]
+    float *f0s = reinterpret_cast<float *>(smraw + L.f0);       // [K][kTS]
+    float *qds = reinterpret_cast<float *>(smraw + L.quad);     // [kTS]
+    uint32_t *gid = reinterpret_cast<uint32_t *>(smraw + L.gid);
+    __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];
+    __shared__ int tile_s;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double beta = P.t_step * P.fs;
+    const int64_t n_tiles = (n + kTS - 1) / kTS;
+
+    for (int j = tid; j < NT; j += kTThreads) {
+        bini[j] = bt.bin_i[j];
+        binf[j] = bt.bin_f[j];
+    }
+
+    for (;;) {
+        if (tid == 0)
+            tile_s = atomicAdd(tile_counter, 1);
+        if (tid < kMaxDet) {
+            lo_s[tid] = INT_MAX;
+            hi_s[tid] = INT_MIN;
+        }
+        __syncthreads();
+        const int64_t tile = tile_s;
+        if (tile >= n_tiles)
+            break;
+
+        // ---------------- phase A: per sample, float64 sky trigonometry and scalars
+        if (tid < kTS) {
+            const int64_t si = tile * kTS + tid;
+            uint32_t g = si < n ? perm[si] : 0xffffffffu;
+            const bool valid = (int64_t)g < n;
+            gid[tid] = valid ? g : 0xffffffffu;
+            double th[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
+            if (valid)
+                for (int d = 0; d < 6; ++d)
+                    th[d] = theta[6 * (int64_t)g + d];
+            Sky sk = sky_of(th[0], th[1], P.gmst);
+            double *sp = sky + 4 * tid;
+            sp[0] = sk.cd;
+            sp[1] = sk.sd;
+            sp[2] = sk.ch;
+            sp[3] = sk.sh;
+            float s2p, c2p, shalf, chalf;
+            sincosf((float)(2.0 * th[2]), &s2p, &c2p);
+            sincosf((float)(0.5 * th[4]), &shalf, &chalf);
+            float *pp = par + 8 * tid;
+            pp[0] = c2p;
+            pp[1] = s2p;
+            pp[2] = valid ? (float)(P.d_ref / th[5]) : 0.f;
+            pp[3] = (float)th[3];
+            pp[4] = chalf;
+            pp[5] = shalf;
+        }
+        __syncthreads();
+        // ---------------- phase B: per (sample, detector), delays and x F_k
+        for (int it = tid; it < kTS * K; it += kTThreads) {
+            const int s = it % kTS, k = it / kTS;
+            const double *sp = sky + 4 * s;
+            Sky sk{sp[0], sp[1], sp[2], sp[3]};
+            const float *pp = par + 8 * s;
+            double dt = arrival_delay(P, k, sk);
+            double u0 = (P.t_lo + dt - P.q_t0[k]) * P.fs;
+            double fl = floor(u0);
+            int i0 = (int)fl;
+            i0s[k * kTS + s] = i0;
+            f0s[k * kTS + s] = (float)(u0 - fl);
+            if (gid[s] != 0xffffffffu) {
+                atomicMin(&lo_s[k], i0);
+                atomicMax(&hi_s[k], i0);
+            }
+            Cx<float> F = response<float>(P, k, sk, pp[0], pp[1]);
+            fx[k * kTS + s] = make_float2(pp[2] * F.re, pp[2] * F.im);
+        }
+        __syncthreads();
+        // ---------------- phase C: per (sample, mode), harmonic and coefficients
+        for (int it = tid; it < kTS * M; it += kTThreads) {
+            const int s = it % kTS, m = it / kTS;
+            const float *pp = par + 8 * s;
+            float d = 0.f;
+            for (int t = 0; t < P.wn[m]; ++t)
+                d += (float)P.wcoef[m][t] * ipow(pp[4], P.wpc[m][t]) * ipow(pp[5], P.wps[m][t]);
+            float sy, cy;
+            sincosf(-(float)P.mode_m[m] * pp[3], &sy, &cy);
+            const float yr = d * cy, yi = d * sy;
+            for (int k = 0; k < K; ++k) {
+                float2 f = fx[k * kTS + s];
+                Cs[(k * R2 + 2 * m) * kTS + s] = f.x * yr - f.y * yi;
+                Cs[(k * R2 + 2 * m + 1) * kTS + s] = f.x * yi + f.y * yr;
+            }
+        }
+        __syncthreads();
+        // ---------------- phase D: template term, 4 threads per sample
+        {
+            const int s = tid >> 2, part = tid & 3;
+            float acc = 0.f;
+            for (int k = 0; k < K; ++k) {
+                const float *Ck = Cs + (size_t)k * R2 * kTS;
+                for (int a = part; a < M; a += 4) {
+                    const float2 *Ur = P.U32 + ((size_t)k * M + a) * M;
+                    const float2 *Vr = P.V32 + ((size_t)k * M + a) * M;
+                    float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f;
+                    for (int b = 0; b < M; ++b) {
+                        float cr = Ck[(2 * b) * kTS + s], ci = Ck[(2 * b + 1) * kTS + s];
+                        float2 u = __ldg(Ur + b), v = __ldg(Vr + b);
+                        ur = fmaf(u.x, cr, fmaf(-u.y, ci, ur));
+                        ui = fmaf(u.x, ci, fmaf(u.y, cr, ui));
+                        vr = fmaf(v.x, cr, fmaf(-v.y, ci, vr));
+                        vi = fmaf(v.x, ci, fmaf(v.y, cr, vi));
+                    }
+                    float ar = Ck[(2 * a) * kTS + s], ai = Ck[(2 * a + 1) * kTS + s];
+                    acc += (ar * ur + ai * ui) + (ar * vr - ai * vi);
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            if (part == 0)
+                qds[s] = (float)P.kappa * acc;
+        }
+        __syncthreads();
+
+        int spread = 0;
+        for (int k = 0; k < K; ++k)
+            spread = max(spread, hi_s[k] - lo_s[k]);
+        const bool direct = spread > kNCol - 16;   // no shared window: evaluate from global memory
+        int jmax = (direct || !(beta > 0.0)) ? kMaxChunkBins : (int)floor((double)(kNCol - 8 - spread - 1) / beta) + 1;
+        jmax = max(1, min(jmax, kMaxChunkBins));
+        const int n_chunks = (NT + jmax - 1) / jmax;
+        const int jnom = (NT + n_chunks - 1) / n_chunks;
+        const int n_steps = n_chunks * K;
+
+        // window of step t: detector t % K, bins [j0, j0 + J) of chunk t / K
+        auto window = [&](int t, int &iw0, int &ncg) {
+            const int k = t % K, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
+            const int base = lo_s[k] + bini[j0];
+            iw0 = max(base, 0) & ~3;
+            const int need = hi_s[k] + bini[j0 + J - 1] + 3 - iw0;
+            ncg = max(1, min(kColGroups, (need + 31) >> 5));
+        };
+        auto stage = [&](int t, float *dst) {
+            int iw0, ncg;
+            window(t, iw0, ncg);
+            const float *Qk = P.Qr32 + (size_t)(t % K) * R2 * P.n_q_pad + iw0;
+            const int per_row = ncg * 8;
+            for (int e = tid; e < R2 * per_row; e += kTThreads) {
+                const int r = e / per_row, c4 = e - r * per_row;
+                cp_async16(dst + r * kNCol + 4 * c4, Qk + (size_t)r * P.n_q_pad + 4 * c4);
+            }
+            cp_async_commit();
+        };
+
+        if (!direct) {
+            if (tid == 0 && lo_s[0] + bini[0] < 0)
+                atomicOr(err, kErrRange);
+            stage(0, Qb[0]);
+        }
+
+        float run_mx[8], run_sum[8];
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            run_mx[p] = -INFINITY;
+            run_sum[p] = 0.f;
+        }
+        float lin[8][kBinsPerLane];
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+            for (int q = 0; q < kBinsPerLane; ++q)
+                lin[p][q] = 0.f;
+
+        for (int t = 0; t < n_steps; ++t) {
+            const int k = t % K, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
+            const int *i0k = i0s + k * kTS;
+            const float *f0k = f0s + k * kTS;
+            if (!direct) {
+                int iw0, ncg;
+                window(t, iw0, ncg);
+                cp_async_wait_all();
+                __syncthreads();   // window t visible; every thread is past step t-1
+                if (kDbuf && t + 1 < n_steps)
+                    stage(t + 1, Qb[(t + 1) & 1]);
+                const float *Q = Qb[kDbuf ? (t & 1) : 0];
+                float acc[8][kColGroups];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int g = 0; g < kColGroups; ++g)
+                        acc[i][g] = 0.f;
+                const float *Ck = Cs + (size_t)k * R2 * kTS + warp * 8;
+#pragma unroll 2
+                for (int r = 0; r < R2; ++r) {
+                    const float4 a0 = *reinterpret_cast<const float4 *>(Ck + r * kTS);
+                    const float4 a1 = *reinterpret_cast<const float4 *>(Ck + r * kTS + 4);
+                    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    float b[kColGroups];
+#pragma unroll
+                    for (int g = 0; g < kColGroups; ++g)
+                        b[g] = (g < ncg) ? Q[r * kNCol + lane + 32 * g] : 0.f;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int g = 0; g < kColGroups; ++g)
+                            acc[i][g] = fmaf(a[i], b[g], acc[i][g]);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int g = 0; g < kColGroups; ++g)
+                        if (g < ncg)
+                            Rs[(warp * 8 + i) * kNCol + lane + 32 * g] = acc[i][g];
+                __syncthreads();   // R complete (and, single-buffered, the Q window consumed)
+                if (!kDbuf && t + 1 < n_steps)
+                    stage(t + 1, Qb[0]);
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int s = warp + 8 * p;
+                    if (gid[s] == 0xffffffffu)
+                        continue;
+                    const float *Rrow = Rs + s * kNCol;
+                    const int ib = i0k[s] - iw0;
+                    const float f0 = f0k[s];
+#pragma unroll
+                    for (int q = 0; q < kBinsPerLane; ++q) {
+                        const int jj = lane + 32 * q;
+                        if (jj < J) {
+                            const float sf = f0 + binf[j0 + jj];
+                            const int carry = sf >= 1.f;
+                            const float fr = sf - (float)carry;
+                            const int c = ib + bini[j0 + jj] + carry;
+                            const float r0 = Rrow[c], r1 = Rrow[c + 1];
+                            lin[p][q] += fmaf(fr, r1 - r0, r0);
+                        }
+                    }
+                }
+            } else {
+                const float *Qk = P.Qr32 + (size_t)k * R2 * P.n_q_pad;
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int s = warp + 8 * p;
+                    if (gid[s] == 0xffffffffu)
+                        continue;
+                    const int i0 = i0k[s];
+                    const float f0 = f0k[s];
+#pragma unroll
+                    for (int q = 0; q < kBinsPerLane; ++q) {
+                        const int jj = lane + 32 * q;
+                        if (jj < J) {
+                            const float sf = f0 + binf[j0 + jj];
+                            const int carry = sf >= 1.f;
+                            const float fr = sf - (float)carry;
+                            const int c = i0 + bini[j0 + jj] + carry;
+                            if (c < 0 || c + 1 >= P.n_q) {
+                                atomicOr(err, kErrRange);
+                                continue;
+                            }
+                            float v = 0.f;
+                            for (int r = 0; r < R2; ++r) {
+                                const float *row = Qk + (size_t)r * P.n_q_pad + c;
+                                const float q0 = __ldg(row), q1 = __ldg(row + 1);
+                                v = fmaf(Cs[(k * R2 + r) * kTS + s], fmaf(fr, q1 - q0, q0), v);
+                            }
+                            lin[p][q] += v;
+                        }
+                    }
+                }
+            }
+            if (k == K - 1) {
+                // fold the chunk's bins into each sample's running log-sum-exp
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    const int s = warp + 8 * p;
+                    const float qd = qds[s];
+                    const uint32_t g = gid[s];
+                    float cmx = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < kBinsPerLane; ++q) {
+                        const int jj = lane + 32 * q;
+                        if (jj < J) {
+                            lin[p][q] -= qd;
+                            cmx = fmaxf(cmx, lin[p][q]);
+                            if (lnL_t && g != 0xffffffffu)
+                                lnL_t[(int64_t)g * NT + j0 + jj] = (double)lin[p][q];
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1)
+                        cmx = fmaxf(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
+                    const float nm = fmaxf(run_mx[p], cmx);
+                    float cs = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kBinsPerLane; ++q) {
+                        if (lane + 32 * q < J)
+                            cs += __expf(lin[p][q] - nm);
+                        lin[p][q] = 0.f;
+                    }
+#pragma unroll
+                    for (int o = 16; o; o >>= 1)
+                        cs += __shfl_xor_sync(0xffffffffu, cs, o);
+                    run_sum[p] = (run_mx[p] == -INFINITY ? 0.f : run_sum[p] * __expf(run_mx[p] - nm)) + cs;
+                    run_mx[p] = nm;
+                }
+            }
+        }
+        // ---------------- epilogue: lane p writes sample warp + 8 p
+        if (lane < 8) {
+            float mxv = run_mx[0], smv = run_sum[0];
+#pragma unroll
+            for (int p = 1; p < 8; ++p)
+                if (lane == p) {
+                    mxv = run_mx[p];
+                    smv = run_sum[p];
+                }
+            const int s = warp + 8 * lane;
+            const uint32_t g = gid[s];
+            if (g != 0xffffffffu) {
+                double r = (double)mxv + log((double)smv) - log((double)NT);
+                if (!isfinite(r))
+                    atomicOr(err, kErrNonFinite);
+                lnL_tmarg[g] = r;
+                if (lnw && lnpw)
+                    lnw[g] = r + lnpw[g];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t lnl_fp32_smem_bytes(const Problem &P)
+{
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return tile_layout(P.K, P.M, P.n_t, tile_dbuf(P, max_smem)).end;
+}
+
+cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
+                            double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
+                            int *tile_counter, cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const bool dbuf = tile_dbuf(P, max_smem);
+    const size_t smem = tile_layout(P.K, P.M, P.n_t, dbuf).end;
+    if (smem > (size_t)max_smem)
+        return cudaErrorInvalidConfiguration;
+    auto kern = dbuf ? lnl_tile_kernel<true> : lnl_tile_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(tile_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+        return e;
+    const int64_t tiles = (n + kTS - 1) / kTS;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    kern<<<grid, kTThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err, tile_counter);
+    return cudaGetLastError();
+}
+
+}  // namespace rift
