@@ -189,6 +189,34 @@ int rift_ile_get_sampler(const rift_ile_t *h, double *P);
  * caller count device launches inside a timed region).  Returns -1 for NULL. */
 int64_t rift_ile_kernel_launches(const rift_ile_t *h);
 
+/* Reduction of log-weights that allocates nothing (no counterpart in the paper; it
+ * exists for callers that cannot allocate device memory at the point of the call:
+ * code running under a fixed memory budget or a caching allocator it must not
+ * bypass, real-time loops where cudaMalloc's implicit synchronisation is not
+ * allowed, or a host that has handed all free device memory to other work).
+ *
+ *   lnw  [n]  float64 log-weights ln w_i, DEVICE memory (read only)
+ *   lnL  [n]  optional float64 values whose maximum is reported in out[5]
+ *             (NULL: the maximum of lnw is reported instead)
+ *   out  [8]  DEVICE memory, written: ln Z = ln((1/n) sum w), sigma_lnZ, n_eff =
+ *             sum w / max w, n_ESS = (sum w)^2 / sum w^2, max ln w, max lnL, n, 0
+ *             (the same definitions and the same kernels as rift_ile_marginalize)
+ *   cuda_stream  cudaStream_t (NULL: legacy default stream); the call waits for
+ *             the stream before returning, to read its status.
+ *
+ * Scratch is a 12 KiB file-scope device array inside the library, held by every
+ * GPU that loads the library until the process exits; nothing is allocated per
+ * call (no cudaMalloc, cudaFree or allocating library routine).  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current) and caches it: make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents; the error
+ * word is cleared by each call.  Calls that overlap on the GPU (different streams
+ * or threads at the same time) race on the array and must be serialised by the
+ * caller.  RIFT_EINVAL if n < 1 or n > RIFT_NOALLOC_MAX_SAMPLES or a pointer is
+ * NULL; RIFT_ENONFINITE if a ln w is NaN or infinite; RIFT_ECUDA on a CUDA error. */
+#define RIFT_NOALLOC_MAX_SAMPLES ((int64_t)1 << 31)
+int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, double *out, void *cuda_stream);
+
 void rift_ile_destroy(rift_ile_t *h);
 const char *rift_ile_strerror(int code);
 

@@ -29,7 +29,8 @@ RIFT_MAX_ITER = 64
 
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
-            "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_destroy", "rift_ile_strerror"]
+            "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_destroy",
+            "rift_ile_strerror"]
 
 
 class RiftError(RuntimeError):
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = False):
     L.rift_ile_get_state.argtypes = [vp, vp, C.POINTER(C.c_size_t)]
     L.rift_ile_set_state.argtypes = [vp, vp, C.c_size_t]
     L.rift_ile_get_sampler.argtypes = [vp, vp]
+    L.rift_ile_reduce_noalloc.argtypes = [vp, vp, i64, vp, vp]
     L.rift_ile_kernel_launches.argtypes = [vp]
     L.rift_ile_kernel_launches.restype = C.c_int64
     L.rift_ile_destroy.argtypes = [vp]
@@ -198,6 +200,12 @@ def rift_ile_get_sampler(h, n_bins):
     P = np.empty((6, n_bins))
     _check(load().rift_ile_get_sampler(h, _ptr(P)), "rift_ile_get_sampler")
     return P
+
+
+def rift_ile_reduce_noalloc(lnw, n, out, lnL=None, stream=None):
+    """Reduction of device log-weights into device out[8] without allocating."""
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(load().rift_ile_reduce_noalloc(_ptr(lnw), _ptr(lnL), int(n), _ptr(out), st), "rift_ile_reduce_noalloc")
 
 
 def rift_ile_kernel_launches(h):

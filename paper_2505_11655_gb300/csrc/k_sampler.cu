@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "ile_kernels.h"
 
@@ -491,3 +492,71 @@ cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st)
 }
 
 }  // namespace rift
+
+// ======================================================================== reduction without allocation
+//
+// rift_ile_reduce_noalloc runs the same two reduction kernels as the library's own
+// marginalisation, but its scratch (block partials, the running record and the
+// error word) lives in the file-scope array below instead of in buffers from
+// cudaMalloc.  Every GPU that loads the library holds this array until the
+// process exits.  Host code must not hand the symbol itself to a kernel (on the
+// host it names a stand-in, not device memory): its device address is taken once
+// per device with cudaGetSymbolAddress, with that device current.
+
+namespace {
+
+constexpr int kNoallocPartials = 5 * rift::kRedBlocks;   // [kRedBlocks][5] block partials
+constexpr int kNoallocPooled = kNoallocPartials;         // 8 doubles: running record
+constexpr int kNoallocErr = kNoallocPooled + 8;          // error word (int in a double slot)
+constexpr int kNoallocDoubles = kNoallocErr + 8;          // 1536 doubles = 12 KiB
+
+static __device__ __align__(256) double g_reduce_scratch[kNoallocDoubles];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+int noalloc_scratch(double **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        cudaGetLastError();
+        return RIFT_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_reduce_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return RIFT_ECUDA;
+        }
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return RIFT_OK;
+}
+
+}  // namespace
+
+extern "C" int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, double *out, void *cuda_stream)
+{
+    if (!lnw || !out || n < 1 || n > RIFT_NOALLOC_MAX_SAMPLES)
+        return RIFT_EINVAL;
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != RIFT_OK)
+        return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int *err = reinterpret_cast<int *>(scratch + kNoallocErr);
+    int flags = 0;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+        rift::launch_reduce(lnw, lnL ? lnL : lnw, n, scratch, out, 0, scratch + kNoallocPooled, 1, err, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&flags, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return RIFT_ECUDA;
+    }
+    return (flags & rift::kErrNonFinite) ? RIFT_ENONFINITE : RIFT_OK;
+}
