@@ -28,9 +28,11 @@ constexpr int kColGroups = kNCol / 32;
 constexpr int kTThreads = 256;   // 8 warps
 constexpr int kBinsPerLane = 5;  // a chunk holds <= 160 bins
 constexpr int kMaxChunkBins = 32 * kBinsPerLane;
+constexpr int kPowStride = 16;   // >= kMaxPow + 1
+static_assert(kPowStride >= kMaxPow + 1, "power table too short");
 
 struct TileLayout {
-    size_t cs, qb0, qb1, r, bini, binf, sky, par, fx, i0, f0, quad, gid, end;
+    size_t cs, qb0, qb1, r, bini, binf, sky, par, pw, fx, i0, f0, quad, qpart, gid, end;
 };
 
 __host__ __device__ inline size_t al16(size_t o) { return (o + 15) & ~(size_t)15; }
@@ -47,10 +49,12 @@ __host__ __device__ inline TileLayout tile_layout(int K, int M, int n_t, bool db
     L.binf = o; o = al16(o + (size_t)n_t * 4);
     L.sky = o; o = al16(o + (size_t)kTS * 4 * 8);     // cos d, sin d, cos h, sin h (float64)
     L.par = o; o = al16(o + (size_t)kTS * 8 * 4);     // c2psi, s2psi, x, phi, cos(i/2), sin(i/2) (float32)
+    L.pw = o;  o = al16(o + (size_t)kTS * 2 * kPowStride * 4);   // cos(i/2)^p, sin(i/2)^p
     L.fx = o;  o = al16(o + (size_t)K * kTS * 8);     // x F_k (float2)
     L.i0 = o;  o = al16(o + (size_t)K * kTS * 4);
     L.f0 = o;  o = al16(o + (size_t)K * kTS * 4);
     L.quad = o; o = al16(o + (size_t)kTS * 4);
+    L.qpart = o; o = al16(o + (size_t)4 * kTS * 4);
     L.gid = o; o = al16(o + (size_t)kTS * 4);
     L.end = o;
     return L;
@@ -68,14 +72,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ float ipow(float b, int e)
-{
-    float r = 1.f;
-    for (int i = 0; i < e; ++i)
-        r *= b;
-    return r;
-}
 
 template <bool kDbuf>
 __global__ void __launch_bounds__(kTThreads, 1)
@@ -97,6 +93,8 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
     int *i0s = reinterpret_cast<int *>(smraw + L.i0);           // [K][kTS]
     float *f0s = reinterpret_cast<float *>(smraw + L.f0);       // [K][kTS]
     float *qds = reinterpret_cast<float *>(smraw + L.quad);     // [kTS]
+    float *qpart = reinterpret_cast<float *>(smraw + L.qpart);  // [4][kTS]
+    float *pw = reinterpret_cast<float *>(smraw + L.pw);        // [kTS][2][kPowStride]
     uint32_t *gid = reinterpret_cast<uint32_t *>(smraw + L.gid);
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];
     __shared__ int tile_s;
@@ -148,6 +146,13 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             pp[3] = (float)th[3];
             pp[4] = chalf;
             pp[5] = shalf;
+            float *pc = pw + tid * 2 * kPowStride, *ps = pc + kPowStride;
+            pc[0] = 1.f;
+            ps[0] = 1.f;
+            for (int q = 1; q <= kMaxPow; ++q) {
+                pc[q] = pc[q - 1] * chalf;
+                ps[q] = ps[q - 1] * shalf;
+            }
         }
         __syncthreads();
         // ---------------- phase B: per (sample, detector), delays and x F_k
@@ -174,9 +179,10 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
         for (int it = tid; it < kTS * M; it += kTThreads) {
             const int s = it % kTS, m = it / kTS;
             const float *pp = par + 8 * s;
+            const float *pc = pw + s * 2 * kPowStride, *ps = pc + kPowStride;
             float d = 0.f;
             for (int t = 0; t < P.wn[m]; ++t)
-                d += (float)P.wcoef[m][t] * ipow(pp[4], P.wpc[m][t]) * ipow(pp[5], P.wps[m][t]);
+                d += (float)P.wcoef[m][t] * pc[P.wpc[m][t]] * ps[P.wps[m][t]];
             float sy, cy;
             sincosf(-(float)P.mode_m[m] * pp[3], &sy, &cy);
             const float yr = d * cy, yi = d * sy;
@@ -187,33 +193,40 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             }
         }
         __syncthreads();
-        // ---------------- phase D: template term, 4 threads per sample
+        // ---------------- phase D: template term.  Thread (s, part): sample s = tid % 64,
+        // rows a = part, part + 4, ... of every detector, using U^H = U and V^T = V:
+        //   c^H U c = sum_a [U_aa |c_a|^2 + 2 Re(conj(c_a) sum_{b>a} U_ab c_b)]
+        //   c^T V c = sum_a [V_aa c_a^2   + 2 c_a sum_{b>a} V_ab c_b]
+        // The Gram loads are uniform across a warp (one broadcast each).
         {
-            const int s = tid >> 2, part = tid & 3;
+            const int s = tid & (kTS - 1), part = tid >> 6;
             float acc = 0.f;
             for (int k = 0; k < K; ++k) {
-                const float *Ck = Cs + (size_t)k * R2 * kTS;
+                const float *Ck = Cs + (size_t)k * R2 * kTS + s;
                 for (int a = part; a < M; a += 4) {
                     const float2 *Ur = P.U32 + ((size_t)k * M + a) * M;
                     const float2 *Vr = P.V32 + ((size_t)k * M + a) * M;
+                    const float ar = Ck[(2 * a) * kTS], ai = Ck[(2 * a + 1) * kTS];
                     float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f;
-                    for (int b = 0; b < M; ++b) {
-                        float cr = Ck[(2 * b) * kTS + s], ci = Ck[(2 * b + 1) * kTS + s];
-                        float2 u = __ldg(Ur + b), v = __ldg(Vr + b);
+                    for (int b = a + 1; b < M; ++b) {
+                        const float cr = Ck[(2 * b) * kTS], ci = Ck[(2 * b + 1) * kTS];
+                        const float2 u = __ldg(Ur + b), v = __ldg(Vr + b);
                         ur = fmaf(u.x, cr, fmaf(-u.y, ci, ur));
                         ui = fmaf(u.x, ci, fmaf(u.y, cr, ui));
                         vr = fmaf(v.x, cr, fmaf(-v.y, ci, vr));
                         vi = fmaf(v.x, ci, fmaf(v.y, cr, vi));
                     }
-                    float ar = Ck[(2 * a) * kTS + s], ai = Ck[(2 * a + 1) * kTS + s];
-                    acc += (ar * ur + ai * ui) + (ar * vr - ai * vi);
+                    const float2 ud = __ldg(Ur + a), vd = __ldg(Vr + a);
+                    const float a2r = ar * ar - ai * ai, a2i = 2.f * ar * ai;
+                    acc += ud.x * (ar * ar + ai * ai) + 2.f * (ar * ur + ai * ui);
+                    acc += (vd.x * a2r - vd.y * a2i) + 2.f * (ar * vr - ai * vi);
                 }
             }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            if (part == 0)
-                qds[s] = (float)P.kappa * acc;
+            qpart[part * kTS + s] = acc;
         }
+        __syncthreads();
+        if (tid < kTS)
+            qds[tid] = (float)P.kappa * ((qpart[tid] + qpart[kTS + tid]) + (qpart[2 * kTS + tid] + qpart[3 * kTS + tid]));
         __syncthreads();
 
         int spread = 0;
@@ -231,8 +244,8 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             const int k = t % K, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
             const int base = lo_s[k] + bini[j0];
             iw0 = max(base, 0) & ~3;
-            const int need = hi_s[k] + bini[j0 + J - 1] + 3 - iw0;
-            ncg = max(1, min(kColGroups, (need + 31) >> 5));
+            (void)J;
+            ncg = kColGroups;   // the contraction always covers the full 256-column window
         };
         auto stage = [&](int t, float *dst) {
             int iw0, ncg;
@@ -277,56 +290,66 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                 if (kDbuf && t + 1 < n_steps)
                     stage(t + 1, Qb[(t + 1) & 1]);
                 const float *Q = Qb[kDbuf ? (t & 1) : 0];
-                float acc[8][kColGroups];
+                // thread (warp, lane): samples warp*8 .. +8, columns 4 lane + 128 g + v
+                float acc[8][8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
 #pragma unroll
-                    for (int g = 0; g < kColGroups; ++g)
-                        acc[i][g] = 0.f;
+                    for (int c = 0; c < 8; ++c)
+                        acc[i][c] = 0.f;
                 const float *Ck = Cs + (size_t)k * R2 * kTS + warp * 8;
-#pragma unroll 2
+                const float *Ql = Q + 4 * lane;
+                // operands of step r + 1 are loaded while step r's 64 FMAs issue
+                float4 na0 = *reinterpret_cast<const float4 *>(Ck);
+                float4 na1 = *reinterpret_cast<const float4 *>(Ck + 4);
+                float4 nb0 = *reinterpret_cast<const float4 *>(Ql);
+                float4 nb1 = *reinterpret_cast<const float4 *>(Ql + 128);
                 for (int r = 0; r < R2; ++r) {
-                    const float4 a0 = *reinterpret_cast<const float4 *>(Ck + r * kTS);
-                    const float4 a1 = *reinterpret_cast<const float4 *>(Ck + r * kTS + 4);
-                    const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                    float b[kColGroups];
-#pragma unroll
-                    for (int g = 0; g < kColGroups; ++g)
-                        b[g] = (g < ncg) ? Q[r * kNCol + lane + 32 * g] : 0.f;
+                    const float a[8] = {na0.x, na0.y, na0.z, na0.w, na1.x, na1.y, na1.z, na1.w};
+                    const float b[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
+                    const int rn = r + 1 < R2 ? r + 1 : r;
+                    na0 = *reinterpret_cast<const float4 *>(Ck + rn * kTS);
+                    na1 = *reinterpret_cast<const float4 *>(Ck + rn * kTS + 4);
+                    nb0 = *reinterpret_cast<const float4 *>(Ql + rn * kNCol);
+                    nb1 = *reinterpret_cast<const float4 *>(Ql + rn * kNCol + 128);
 #pragma unroll
                     for (int i = 0; i < 8; ++i)
 #pragma unroll
-                        for (int g = 0; g < kColGroups; ++g)
-                            acc[i][g] = fmaf(a[i], b[g], acc[i][g]);
+                        for (int c = 0; c < 8; ++c)
+                            acc[i][c] = fmaf(a[i], b[c], acc[i][c]);
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-#pragma unroll
-                    for (int g = 0; g < kColGroups; ++g)
-                        if (g < ncg)
-                            Rs[(warp * 8 + i) * kNCol + lane + 32 * g] = acc[i][g];
+                for (int i = 0; i < 8; ++i) {
+                    float *Rrow = Rs + (warp * 8 + i) * kNCol + 4 * lane;
+                    *reinterpret_cast<float4 *>(Rrow) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                    *reinterpret_cast<float4 *>(Rrow + 128) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+                }
                 __syncthreads();   // R complete (and, single-buffered, the Q window consumed)
                 if (!kDbuf && t + 1 < n_steps)
                     stage(t + 1, Qb[0]);
+                int bi[kBinsPerLane];
+                float bf[kBinsPerLane];
+#pragma unroll
+                for (int q = 0; q < kBinsPerLane; ++q) {
+                    const int jj = min(lane + 32 * q, J - 1);
+                    bi[q] = bini[j0 + jj];
+                    bf[q] = binf[j0 + jj];
+                }
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
                     const int s = warp + 8 * p;
-                    if (gid[s] == 0xffffffffu)
-                        continue;
-                    const float *Rrow = Rs + s * kNCol;
-                    const int ib = i0k[s] - iw0;
-                    const float f0 = f0k[s];
+                    const bool ok = gid[s] != 0xffffffffu;
+                    // padding samples use the tile's lowest offset, which keeps every read in the row
+                    const float *Rrow = Rs + s * kNCol + ((ok ? i0k[s] : lo_s[k]) - iw0);
+                    const float f0 = ok ? f0k[s] : 0.f;
 #pragma unroll
                     for (int q = 0; q < kBinsPerLane; ++q) {
-                        const int jj = lane + 32 * q;
-                        if (jj < J) {
-                            const float sf = f0 + binf[j0 + jj];
-                            const int carry = sf >= 1.f;
-                            const float fr = sf - (float)carry;
-                            const int c = ib + bini[j0 + jj] + carry;
-                            const float r0 = Rrow[c], r1 = Rrow[c + 1];
-                            lin[p][q] += fmaf(fr, r1 - r0, r0);
-                        }
+                        const float sf = f0 + bf[q];
+                        const int carry = sf >= 1.f;
+                        const float fr = sf - (float)carry;
+                        const float *rr = Rrow + bi[q] + carry;
+                        const float r0 = rr[0], r1 = rr[1];
+                        lin[p][q] += fmaf(fr, r1 - r0, r0);
                     }
                 }
             } else {
@@ -362,39 +385,55 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                 }
             }
             if (k == K - 1) {
-                // fold the chunk's bins into each sample's running log-sum-exp
+                // fold the chunk's bins into each sample's running log-sum-exp; the
+                // eight samples' warp reductions are interleaved
+                float cmx[8], cs[8];
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
-                    const int s = warp + 8 * p;
-                    const float qd = qds[s];
-                    const uint32_t g = gid[s];
-                    float cmx = -INFINITY;
+                    const float qd = qds[warp + 8 * p];
+                    cmx[p] = -INFINITY;
 #pragma unroll
                     for (int q = 0; q < kBinsPerLane; ++q) {
-                        const int jj = lane + 32 * q;
-                        if (jj < J) {
-                            lin[p][q] -= qd;
-                            cmx = fmaxf(cmx, lin[p][q]);
-                            if (lnL_t && g != 0xffffffffu)
-                                lnL_t[(int64_t)g * NT + j0 + jj] = (double)lin[p][q];
-                        }
+                        lin[p][q] -= qd;
+                        if (lane + 32 * q < J)
+                            cmx[p] = fmaxf(cmx[p], lin[p][q]);
                     }
+                }
+                if (lnL_t) {
 #pragma unroll
-                    for (int o = 16; o; o >>= 1)
-                        cmx = fmaxf(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
-                    const float nm = fmaxf(run_mx[p], cmx);
-                    float cs = 0.f;
+                    for (int p = 0; p < 8; ++p) {
+                        const uint32_t g = gid[warp + 8 * p];
+#pragma unroll
+                        for (int q = 0; q < kBinsPerLane; ++q)
+                            if (lane + 32 * q < J && g != 0xffffffffu)
+                                lnL_t[(int64_t)g * NT + j0 + lane + 32 * q] = (double)lin[p][q];
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1)
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        cmx[p] = fmaxf(cmx[p], __shfl_xor_sync(0xffffffffu, cmx[p], o));
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    cmx[p] = fmaxf(run_mx[p], cmx[p]);
+                    cs[p] = 0.f;
 #pragma unroll
                     for (int q = 0; q < kBinsPerLane; ++q) {
                         if (lane + 32 * q < J)
-                            cs += __expf(lin[p][q] - nm);
+                            cs[p] += __expf(lin[p][q] - cmx[p]);
                         lin[p][q] = 0.f;
                     }
+                }
 #pragma unroll
-                    for (int o = 16; o; o >>= 1)
-                        cs += __shfl_xor_sync(0xffffffffu, cs, o);
-                    run_sum[p] = (run_mx[p] == -INFINITY ? 0.f : run_sum[p] * __expf(run_mx[p] - nm)) + cs;
-                    run_mx[p] = nm;
+                for (int o = 16; o; o >>= 1)
+#pragma unroll
+                    for (int p = 0; p < 8; ++p)
+                        cs[p] += __shfl_xor_sync(0xffffffffu, cs[p], o);
+#pragma unroll
+                for (int p = 0; p < 8; ++p) {
+                    run_sum[p] = (run_mx[p] == -INFINITY ? 0.f : run_sum[p] * __expf(run_mx[p] - cmx[p])) + cs[p];
+                    run_mx[p] = cmx[p];
                 }
             }
         }
