@@ -51,6 +51,10 @@ struct rift_ile {
     uint64_t *bins = nullptr;
     uint32_t *key = nullptr, *perm = nullptr, *counts = nullptr;
     int *row_off = nullptr, *tile_counter = nullptr;
+    __half *Qtc = nullptr;
+    unsigned int *qmax_bits = nullptr;
+    int tc_mode = 2;              // 0 never, 1 whenever it fits, 2 batches >= kTcMinBatch
+    bool tc_ok = false;
     std::vector<int> row_host;   // sky grid of the current batch size
     SkyGrid grid{0, 0, nullptr};
     // reductions and sampler
@@ -134,6 +138,8 @@ int wigner_table(int l, int m, double *coef, int8_t *pc, int8_t *ps)
 
 int map_err(int flags)
 {
+    if (flags & kErrTimeout)
+        return RIFT_ETIMEOUT;
     if (flags & kErrRange)
         return RIFT_ERANGE;
     if (flags & kErrNonFinite)
@@ -261,6 +267,28 @@ int sync_and_err(rift_ile_t *h, int *flags_out = nullptr)
 
 bool use_fp32(const rift_ile_t *h) { return h->cfg.precision != RIFT_FP64; }
 
+// Tensor-core tiles pay off once a batch fills the sky densely enough that 128
+// samples share a 128-column Q window.
+constexpr int64_t kTcMinBatch = 100000;
+
+bool use_tc(const rift_ile_t *h, int64_t n)
+{
+    if (!h->tc_ok || h->tc_mode == 0)
+        return false;
+    return h->tc_mode == 1 || n >= kTcMinBatch;
+}
+
+cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
+                         const double *lnpw, double *lnw)
+{
+    const BinTable bt{h->bin_i, h->bin_f};
+    if (use_tc(h, n))
+        return launch_lnl_tc(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->tile_counter,
+                             h->stream);
+    return launch_lnl_fp32(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->tile_counter,
+                           h->stream);
+}
+
 // Sky grid sized for a batch of n samples; uploads the row table when it changes.
 int grid_for_batch(rift_ile_t *h, int64_t n)
 {
@@ -288,8 +316,7 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
     RK(grid_for_batch(h, n));
     CK(launch_keys(h->grid, theta, n, h->key, h->stream));
     CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
-    CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err,
-                       h->tile_counter, h->stream));
+    CK(launch_tiled(h, theta, n, lnL_tmarg, lnL_t, lnpw, lnw));
     return RIFT_OK;
 }
 
@@ -304,8 +331,7 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
         CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
     CK(cudaEventRecord(h->ev[slot][1], h->stream));
     if (use_fp32(h))
-        CK(launch_lnl_fp32(h->prob, BinTable{h->bin_i, h->bin_f}, h->theta, h->perm, n, h->lnL, nullptr, h->lnpw,
-                           h->lnw, h->err, h->tile_counter, h->stream));
+        CK(launch_tiled(h, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw));
     else
         CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
     CK(cudaEventRecord(h->ev[slot][2], h->stream));
@@ -456,6 +482,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
         (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1)) ||
         (rc = dalloc(h, &h->row_off, (size_t)kMaxRows + 1)) || (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
+        (rc = dalloc(h, &h->qmax_bits, (size_t)4)) ||
+        (rc = dalloc(h, &h->Qtc, (size_t)K * 2 * ((cfg->n_q + 7) / 8 + 17) * ((2 * M + 15) / 16 * 16) * 8)) ||
         (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||
         (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
         (rc = dalloc(h, &h->stats, (size_t)8 * RIFT_MAX_ITER)) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
@@ -499,6 +527,21 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         cudaGetLastError();
         release(h);
         return RIFT_ECUDA;
+    }
+    P.tc_groups = (cfg->n_q + 7) / 8 + 17;
+    P.Qtc = h->Qtc;
+    P.qmax_bits = h->qmax_bits;
+    {
+        int dev = 0, max_smem = 0, major = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        h->tc_ok = major == 10 && lnl_tc_fits(P, max_smem);
+        const char *env = std::getenv("RIFT_ILE_TC");
+        if (env && env[0] == '0')
+            h->tc_mode = 0;
+        else if (env && env[0] == '1')
+            h->tc_mode = 1;
     }
     P.Q64 = h->Q64;
     P.U64 = h->U64;
@@ -559,6 +602,10 @@ int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const voi
                                                       h->U32, h->V32, h->err);
     CK(cudaGetLastError());
     h->launches += 1;
+    if (h->tc_ok) {
+        CK(launch_prep_tc(h->Q64, K, M, nq, h->prob.tc_groups, h->qmax_bits, h->Qtc, h->stream));
+        h->launches += 2;
+    }
     int rc = sync_and_err(h);
     h->have_overlaps = (rc == RIFT_OK);
     return rc;

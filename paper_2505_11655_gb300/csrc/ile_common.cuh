@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/rift_ile.h"
@@ -25,6 +26,7 @@ constexpr int kMaxPow = 2 * kMaxL + 2;   // largest power of cos(iota/2), sin(io
 // Error flags raised by kernels (OR-ed into a device word).
 constexpr int kErrRange = 1;
 constexpr int kErrNonFinite = 2;
+constexpr int kErrTimeout = 4;
 
 // Everything a kernel needs about one problem, passed by value (< 4 KB).
 struct Problem {
@@ -46,6 +48,11 @@ struct Problem {
     const float *Qr32;      // [K][2M][n_q_pad] split planes, zero padded
     const float2 *U32;
     const float2 *V32;
+    // tensor-core copy of Q: [K][hi, lo][tc_groups][Kp/8][8][8] float16, scaled by 2^e
+    // with e from the float bits of max|Q| (*qmax_bits)
+    const __half *Qtc;
+    int tc_groups;
+    const unsigned int *qmax_bits;
 };
 
 // ---------------------------------------------------------------- complex helpers

@@ -26,6 +26,15 @@ cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, 
                             int *tile_counter, cudaStream_t st);
 size_t lnl_fp32_smem_bytes(const Problem &P);
 
+// Tensor-core variant of the float32 tiled path (tiles of 128 samples, tcgen05 MMA).
+bool lnl_tc_fits(const Problem &P, int max_smem);
+cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
+                          double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
+                          int *tile_counter, cudaStream_t st);
+// Builds the float16 hi/lo copy of Q for the tensor-core path.
+cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups, unsigned int *qmax_bits,
+                           __half *Qtc, cudaStream_t st);
+
 // Per-sample coefficients: c[n][K][M] (complex), dt[n][K], quad[n]; any may be null.
 cudaError_t launch_coeffs(const Problem &P, bool fp64, const double *theta, int64_t n, double2 *c, double *dt,
                           double *quad, cudaStream_t st);

@@ -225,6 +225,56 @@ def test_fp32_adapt_two_iterations(G, orc):
     assert r["n_total"] == 2 * n
 
 
+# ------------------------------------------------------------------------------ tensor-core tiles
+
+def clustered_samples(n, seed, center=(1.0, 0.3), width=0.06):
+    """Prior draws with the sky confined to a small patch, so that 128-sample
+    tiles share narrow Q windows even in a small batch."""
+    th = S.prior_samples(n, seed)
+    rng = np.random.default_rng(seed + 1)
+    th[:, 0] = center[0] + width * rng.random(n)
+    th[:, 1] = center[1] + width * rng.random(n)
+    return th
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 6000])
+def test_tc_path_matches_oracle(G, orc, monkeypatch, n):
+    """The tcgen05 contraction (float16 hi/lo split, 3 MMAs per K step) against
+    the oracle, at sizes across the 128-sample tile and a ragged tail."""
+    monkeypatch.setenv("RIFT_ILE_TC", "1")
+    p = S.single_large_problem()
+    th = clustered_samples(n, 61 + n)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=8192) as s:
+        got = s.eval(th)
+    assert_fp32_close(got, *olnL(orc, p, th))
+
+
+def test_tc_path_bins_and_cuda_core_agree(G, orc, monkeypatch):
+    p = S.single_large_problem()
+    th = clustered_samples(700, 62)
+    monkeypatch.setenv("RIFT_ILE_TC", "1")
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=1024) as s:
+        g_tc, b_tc = s.eval(th, want_bins=True)
+    monkeypatch.setenv("RIFT_ILE_TC", "0")
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=1024) as s:
+        g_cc, b_cc = s.eval(th, want_bins=True)
+    exp, ebins, quad = orc.lnL(p, th, want_bins=True)
+    assert np.all(np.abs(b_tc - ebins) <= fp32_floor(ebins, quad[:, None]))
+    assert_fp32_close(g_tc, exp, quad)
+    assert np.max(np.abs(g_tc - g_cc)) <= 2e-3
+
+
+def test_tc_path_plain_config_and_spread_sky(G, orc, monkeypatch):
+    """Two modes (K padded to 16) and an unclustered sky (wide tiles take the
+    direct fallback inside the tensor kernel)."""
+    monkeypatch.setenv("RIFT_ILE_TC", "1")
+    for p, th in ((S.plain_fp64_problem(), clustered_samples(3000, 63)),
+                  (S.single_large_problem(), S.prior_samples(3000, 64))):
+        with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
+            got = s.eval(th)
+        assert_fp32_close(got, *olnL(orc, p, th))
+
+
 # ------------------------------------------------------------------------------ full size
 
 @pytest.mark.slow
