@@ -50,13 +50,12 @@ struct rift_ile {
     double *theta = nullptr, *lnpw = nullptr, *lnL = nullptr, *lnw = nullptr;
     uint64_t *bins = nullptr;
     uint32_t *key = nullptr, *perm = nullptr, *counts = nullptr;
-    int *row_off = nullptr, *tile_counter = nullptr;
+    int *tile_counter = nullptr;
     __half *Qtc = nullptr;
     unsigned int *qmax_bits = nullptr;
     int tc_mode = 2;              // 0 never, 1 whenever it fits, 2 batches >= kTcMinBatch
     bool tc_ok = false;
-    std::vector<int> row_host;   // sky grid of the current batch size
-    SkyGrid grid{0, 0, nullptr};
+    SkyGrid grid{0, 0};   // sky grid of the current batch size
     // reductions and sampler
     double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
     double *P = nullptr, *C = nullptr;
@@ -289,17 +288,10 @@ cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *
                            h->stream);
 }
 
-// Sky grid sized for a batch of n samples; uploads the row table when it changes.
+// Sky grid sized for a batch of n samples.
 int grid_for_batch(rift_ile_t *h, int64_t n)
 {
-    std::vector<int> off(kMaxRows + 1);
-    const int rows = sky_grid_rows(n, off.data());
-    if (rows != h->grid.rows) {
-        h->row_host.assign(off.begin(), off.begin() + rows + 1);
-        CK(cudaMemcpyAsync(h->row_off, h->row_host.data(), sizeof(int) * (rows + 1), cudaMemcpyHostToDevice,
-                           h->stream));
-        h->grid = SkyGrid{rows, h->row_host[rows], h->row_off};
-    }
+    h->grid = sky_grid_for(n);
     return RIFT_OK;
 }
 
@@ -481,7 +473,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
         (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
         (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1)) ||
-        (rc = dalloc(h, &h->row_off, (size_t)kMaxRows + 1)) || (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
+        (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
         (rc = dalloc(h, &h->qmax_bits, (size_t)4)) ||
         (rc = dalloc(h, &h->Qtc, (size_t)K * 2 * ((cfg->n_q + 7) / 8 + 17) * ((2 * M + 15) / 16 * 16) * 8)) ||
         (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||

@@ -163,32 +163,46 @@ __device__ __forceinline__ double unit53(uint32_t a, uint32_t b)
 }
 
 // ---------------------------------------------------------------- sort key
-// Sky cell of a sample on a near-equal-area grid: `rows` bands of equal
-// declination width, band r split into row_off[r+1] - row_off[r] cells of equal
-// right-ascension width (about 2 rows cos(delta_r) of them), so cells are
-// roughly square.  Bands are visited in boustrophedon order so that consecutive
-// cells are neighbours on the sky and samples close in key have close arrival
-// delays at every detector.
-constexpr int kMaxCells = 1 << 17;
-constexpr int kMaxRows = 256;
+// Position of a sample's sky direction along a Hilbert curve over the
+// (right ascension, sin declination) square, 2^order cells a side.  Consecutive
+// samples in this order stay compact on the sky whatever their density, so a
+// tile of consecutive samples has close arrival delays at every detector.
+constexpr int kMaxOrder = 10;
+constexpr int kMaxCells = 1 << (2 * kMaxOrder);
 
 struct SkyGrid {
-    int rows;
-    int n_cells;
-    const int *row_off;   // [rows + 1]
+    int order;     // cells per side = 2^order
+    int n_cells;   // 4^order
 };
+
+__device__ __forceinline__ uint32_t hilbert_index(uint32_t x, uint32_t y, int order)
+{
+    uint32_t d = 0;
+    for (uint32_t s = 1u << (order - 1); s > 0; s >>= 1) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {   // rotate the quadrant so the curve continues
+            if (rx == 1) {
+                x = s - 1 - (x & (s - 1));
+                y = s - 1 - (y & (s - 1));
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
 
 __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const SkyGrid &G)
 {
-    int r = (int)((delta * (1.0 / kPi) + 0.5) * G.rows);
-    r = min(G.rows - 1, max(0, r));
-    const int o0 = __ldg(G.row_off + r), na = __ldg(G.row_off + r + 1) - o0;
+    const int side = 1 << G.order;
     double a = alpha * (1.0 / (2.0 * kPi));
     a -= floor(a);
-    int c = min(na - 1, max(0, (int)(a * na)));
-    if (r & 1)
-        c = na - 1 - c;
-    return (uint32_t)(o0 + c);
+    const double z = 0.5 * (sin(delta) + 1.0);
+    const uint32_t x = (uint32_t)min(side - 1, max(0, (int)(a * side)));
+    const uint32_t y = (uint32_t)min(side - 1, max(0, (int)(z * side)));
+    return hilbert_index(x, y, G.order);
 }
 
 }  // namespace rift

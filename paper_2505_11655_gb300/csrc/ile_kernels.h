@@ -55,9 +55,9 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
 // Counting sort of keys (< G.n_cells) into perm (scratch: counts[G.n_cells + 1]).
 cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
                         cudaStream_t st);
-// Rows of the sky grid for a batch of n samples (about 40 samples per cell) and
-// the cumulative cell offsets of those rows (host side).
-int sky_grid_rows(int64_t n, int *row_off /*[kMaxRows + 1]*/);
+// Hilbert-curve grid for a batch of n samples: about one sample per cell, at most
+// 2^kMaxOrder cells a side (host side).
+SkyGrid sky_grid_for(int64_t n);
 
 // Reduction of ln w and ln L_tmarg for iteration slot `slot`:
 //   stats[slot*8 + 0..7] = lnZ, sigma, n_eff, n_ess, max lnw, max lnL, N, (unused)

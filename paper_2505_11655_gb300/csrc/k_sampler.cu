@@ -130,17 +130,12 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
     return cudaGetLastError();
 }
 
-int sky_grid_rows(int64_t n, int *row_off)
+SkyGrid sky_grid_for(int64_t n)
 {
-    int rows = (int)std::lround(std::sqrt((double)n / 40.0));
-    rows = std::max(4, std::min(kMaxRows, rows));
-    row_off[0] = 0;
-    for (int r = 0; r < rows; ++r) {
-        const double dc = -0.5 * kPi + (r + 0.5) * kPi / rows;
-        const int na = std::max(1, (int)std::lround(2.0 * rows * std::cos(dc)));
-        row_off[r + 1] = row_off[r] + na;
-    }
-    return rows;
+    int order = 4;
+    while (order < kMaxOrder && ((int64_t)1 << (2 * order)) < n)
+        ++order;
+    return SkyGrid{order, 1 << (2 * order)};
 }
 
 // ======================================================================== counting sort by sky cell

@@ -36,6 +36,9 @@ constexpr int kTcMaxBins = kTcQ * kTcBPT;
 constexpr int kTcRS = kTcW + 1;    // R row stride (floats): lane-per-sample accesses hit distinct banks
 constexpr int kTcPow = 16;
 constexpr uint64_t kWaitNs = 1000000000ull;
+// A tile whose samples span more than this many Q samples at some detector is cut
+// into contiguous sub-groups (compact along the sort order) that are windowed apart.
+constexpr int kTcSpreadLimit = 64;
 
 struct TcLayout {
     size_t a, b, r, bini, binf, i0, f0, inv, quad, gid, lse, bar, tptr, end;
@@ -83,7 +86,8 @@ bool lnl_tc_fits(const Problem &P, int max_smem)
     if (P.Qtc == nullptr || P.tc_groups <= 0)
         return false;
     const TcLayout L = tc_layout(P.K, P.M, P.n_t);
-    return L.kp <= 64 && L.end <= (size_t)max_smem;
+    // plus the kernel's static shared memory (sub-group table, ~5 KB)
+    return L.kp <= 64 && L.end + 8192 <= (size_t)max_smem;
 }
 
 // ---------------------------------------------------------------- Q copy for the tensor path
@@ -186,8 +190,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     float *qpart = reinterpret_cast<float *>(sm + L.qpart);
     float *lse = reinterpret_cast<float *>(sm + L.lse);         // [2][kTcQ][kTcS] running max, sum
     float *Cs = Rs;
-    __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];
-    __shared__ int tile_s, abort_s;
+    __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
+    __shared__ int glo[kTcS][kMaxDet], ghi[kTcS][kMaxDet], gstart[kTcS + 1];
+    __shared__ int tile_s, abort_s, ngroups_s;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double beta = P.t_step * P.fs;
@@ -280,6 +285,58 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             fx[k * kTcS + s] = make_float2(pp[2] * F.re, pp[2] * F.im);
         }
         __syncthreads();
+        // sub-groups: the whole tile when it is compact, else a greedy cut along the sort order
+        if (tid == 0) {
+            int spread = 0;
+            for (int k = 0; k < K; ++k)
+                spread = max(spread, hi_s[k] - lo_s[k]);
+            int ng = 0;
+            if (spread <= kTcSpreadLimit) {
+                for (int k = 0; k < K; ++k) {
+                    glo[0][k] = lo_s[k];
+                    ghi[0][k] = hi_s[k];
+                }
+                gstart[0] = 0;
+                ng = 1;
+            } else {
+                int lo[kMaxDet], hi[kMaxDet];
+                bool open = false;
+                for (int e = 0; e < kTcS; ++e) {
+                    if (gid[e] == 0xffffffffu)
+                        continue;   // padding rides along with the group it falls in
+                    bool fits = open;
+                    for (int k = 0; k < K && fits; ++k) {
+                        const int v = i0s[k * kTcS + e];
+                        fits = max(hi[k], v) - min(lo[k], v) <= kTcSpreadLimit;
+                    }
+                    if (!fits) {
+                        if (open) {
+                            for (int k = 0; k < K; ++k) {
+                                glo[ng][k] = lo[k];
+                                ghi[ng][k] = hi[k];
+                            }
+                            ++ng;
+                        }
+                        gstart[ng] = ng == 0 ? 0 : e;
+                        for (int k = 0; k < K; ++k)
+                            lo[k] = hi[k] = i0s[k * kTcS + e];
+                        open = true;
+                    } else {
+                        for (int k = 0; k < K; ++k) {
+                            lo[k] = min(lo[k], i0s[k * kTcS + e]);
+                            hi[k] = max(hi[k], i0s[k * kTcS + e]);
+                        }
+                    }
+                }
+                for (int k = 0; k < K; ++k) {
+                    glo[ng][k] = open ? lo[k] : 0;
+                    ghi[ng][k] = open ? hi[k] : 0;
+                }
+                ++ng;
+            }
+            gstart[ng] = kTcS;
+            ngroups_s = ng;
+        }
         // ---------------- C: harmonics and coefficients C [K][2M][kTcS] (float32)
         for (int it = tid; it < kTcS * M; it += kTcThreads) {
             const int s = it % kTcS, m = it / kTcS;
@@ -328,12 +385,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         if (tid < kTcS)
             qds[tid] = (float)P.kappa * ((qpart[tid] + qpart[kTcS + tid]) + (qpart[2 * kTcS + tid] + qpart[3 * kTcS + tid]));
 
-        int spread = 0;
-        for (int k = 0; k < K; ++k)
-            spread = max(spread, hi_s[k] - lo_s[k]);
-        const bool direct = spread > kTcW - 24;
         // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector)
-        if (!direct) {
+        {
             for (int it = tid; it < kTcS * K; it += kTcThreads) {
                 const int s = it % kTcS, k = it / kTcS;
                 const float *Ck = Cs + (size_t)k * R2 * kTcS + s;
@@ -362,7 +415,25 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
 
-        int jmax = (direct || !(beta > 0.0)) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
+        // gather / fold ownership: thread -> sample s, bin quarter h of every chunk
+        const int gs = tid & (kTcS - 1), gh = tid >> 7;
+        const bool gok = gid[gs] != 0xffffffffu;
+        const float gqd = qds[gs];
+        float run_mx = -INFINITY, run_sum = 0.f;
+        int failed = 0;
+        const int ngroups = ngroups_s;
+        for (int grp = 0; grp < ngroups && !failed; ++grp) {
+        __syncthreads();   // every thread is past the previous sub-group's reads of lo_s / hi_s
+        if (tid < K) {
+            lo_s[tid] = glo[grp][tid];
+            hi_s[tid] = ghi[grp][tid];
+        }
+        __syncthreads();
+        const bool in_grp = gs >= gstart[grp] && gs < gstart[grp + 1];
+        int spread = 0;
+        for (int k = 0; k < K; ++k)
+            spread = max(spread, hi_s[k] - lo_s[k]);
+        int jmax = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
         jmax = max(1, min(jmax, kTcMaxBins));
         const int n_chunks = (NT + jmax - 1) / jmax;
         const int jnom = (NT + n_chunks - 1) / n_chunks;
@@ -370,7 +441,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 
         auto win0 = [&](int t) {
             const int k = t % K, j0 = (t / K) * jnom;
-            return max(lo_s[k] + bini[j0], 0) & ~7;
+            // clamped so that a window never leaves the allocation of the Q copy
+            return min(max(lo_s[k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
         };
         // thread 0: stage window t into B buffer t & 1
         auto stage = [&](int t) {
@@ -404,17 +476,11 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             return true;
         };
 
-        // gather / fold ownership: thread -> sample s, bin quarter h of every chunk
-        const int gs = tid & (kTcS - 1), gh = tid >> 7;
-        const bool gok = gid[gs] != 0xffffffffu;
-        const float gqd = qds[gs];
-        float run_mx = -INFINITY, run_sum = 0.f;
         float lin[kTcBPT];
 #pragma unroll
         for (int i = 0; i < kTcBPT; ++i)
             lin[i] = 0.f;
-        int failed = 0;
-        if (!direct && tid == 0) {
+        if (tid == 0) {
             stage(0);
             if (n_steps > 1)
                 stage(1);
@@ -428,7 +494,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins [jb, jb + jn)
             const int i0 = i0s[k * kTcS + gs];
             const float f0 = f0s[k * kTcS + gs];
-            if (!direct) {
+            {
                 const int b = t & 1;
                 if (tid == 0 && !failed && t + 1 < n_steps && !issue(t + 1))
                     failed = 1;
@@ -458,9 +524,11 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     break;
                 }
                 const int iw0 = win0(t);
-                // padding samples use the tile's lowest offset, keeping every read in the row
-                const float *Rrow = Rs + gs * kTcRS + ((gok ? i0 : lo_s[k]) - iw0);
-                const float ff = gok ? f0 : 0.f;
+                // padding samples and samples of other sub-groups read at the group's lowest
+                // offset, which keeps every read in the row; their sums are discarded
+                const bool mine = gok && in_grp;
+                const float *Rrow = Rs + gs * kTcRS + ((mine ? i0 : lo_s[k]) - iw0);
+                const float ff = mine ? f0 : 0.f;
 #pragma unroll
                 for (int i = 0; i < kTcBPT; ++i) {
                     const int j = min(jb + i, j0 + J - 1);   // idle slots re-read the chunk's last bin
@@ -472,31 +540,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     lin[i] += fmaf(fr, r1 - r0, r0);
                 }
                 __syncthreads();   // R consumed before the next drain
-            } else {
-                const float *Qk = P.Qr32 + (size_t)k * R2 * P.n_q_pad;
-                if (gok) {
-                    for (int i = 0; i < jn; ++i) {
-                        const int j = jb + i;
-                        const float sf = f0 + binf[j];
-                        const int carry = sf >= 1.f;
-                        const float fr = sf - (float)carry;
-                        const int c = i0 + bini[j] + carry;
-                        if (c < 0 || c + 1 >= P.n_q) {
-                            atomicOr(err, kErrRange);
-                            continue;
-                        }
-                        float v = 0.f;
-                        for (int r = 0; r < R2; ++r) {
-                            const float *row = Qk + (size_t)r * P.n_q_pad + c;
-                            const float q0 = __ldg(row), q1 = __ldg(row + 1);
-                            v = fmaf(Cs[(k * R2 + r) * kTcS + gs], fmaf(fr, q1 - q0, q0), v);
-                        }
-#pragma unroll
-                        for (int u = 0; u < kTcBPT; ++u)
-                            if (u == i)
-                                lin[u] += v;
-                    }
-                }
             }
             if (k == K - 1) {
                 // fold this thread's bins of the chunk into its running log-sum-exp
@@ -507,14 +550,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     if (i < jn)
                         cmx = fmaxf(cmx, lin[i]);
                 }
-                if (lnL_t && gok) {
+                if (lnL_t && gok && in_grp) {
                     for (int i = 0; i < jn; ++i)
 #pragma unroll
                         for (int u = 0; u < kTcBPT; ++u)
                             if (u == i)
                                 lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)lin[u];
                 }
-                if (jn > 0) {
+                if (jn > 0 && in_grp) {
                     const float nm = fmaxf(run_mx, cmx);
                     float cs = 0.f;
 #pragma unroll
@@ -529,6 +572,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     lin[i] = 0.f;
             }
         }
+        }   // sub-groups
         if (failed) {
             if (tid == 0) {
                 atomicOr(err, kErrTimeout);
