@@ -304,7 +304,7 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
         h->launches += 1;
         return RIFT_OK;
     }
-    h->launches += 5;   // keys, count, scan, scatter, tiled likelihood
+    h->launches += 7;   // keys, count, 3 scan passes, scatter, tiled likelihood
     RK(grid_for_batch(h, n));
     CK(launch_keys(h->grid, theta, n, h->key, h->stream));
     CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
@@ -332,7 +332,7 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
     if (adapt)
         CK(launch_adapt(S, h->bins, h->lnw, n, h->stats, slot, h->hist_partial, h->stream));
     CK(cudaEventRecord(h->ev[slot][3], h->stream));
-    h->launches += 1 + (use_fp32(h) ? 3 : 0) + 1 + 2 + (adapt ? 2 : 0);
+    h->launches += 1 + (use_fp32(h) ? 5 : 0) + 1 + 2 + (adapt ? 2 : 0);
     h->iteration += 1;
     h->last_n = n;
     return RIFT_OK;
@@ -472,7 +472,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->theta, (size_t)N * 6)) || (rc = dalloc(h, &h->lnpw, (size_t)N)) ||
         (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
         (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
-        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1)) ||
+        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1 + 256)) ||
         (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
         (rc = dalloc(h, &h->qmax_bits, (size_t)4)) ||
         (rc = dalloc(h, &h->Qtc, (size_t)K * 2 * ((cfg->n_q + 7) / 8 + 17) * ((2 * M + 15) / 16 * 16) * 8)) ||

@@ -52,10 +52,10 @@ struct SamplerDev {
 cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, int64_t n, double *theta, double *lnpw,
                         uint64_t *bins, uint32_t *key, cudaStream_t st);
 cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32_t *key, cudaStream_t st);
-// Counting sort of keys (< G.n_cells) into perm (scratch: counts[G.n_cells + 1]).
+// Counting sort of keys (< G.n_cells) into perm (scratch: counts[kMaxCells + 1 + 256]).
 cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
                         cudaStream_t st);
-// Hilbert-curve grid for a batch of n samples: about one sample per cell, at most
+// Hilbert-curve grid for a batch of n samples: about four samples per cell, at most
 // 2^kMaxOrder cells a side (host side).
 SkyGrid sky_grid_for(int64_t n);
 

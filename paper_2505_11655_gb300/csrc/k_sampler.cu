@@ -132,8 +132,8 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
 
 SkyGrid sky_grid_for(int64_t n)
 {
-    int order = 4;
-    while (order < kMaxOrder && ((int64_t)1 << (2 * order)) < n)
+    int order = 4;   // about four samples per cell
+    while (order < kMaxOrder && ((int64_t)4 << (2 * order)) < n)
         ++order;
     return SkyGrid{order, 1 << (2 * order)};
 }
@@ -146,46 +146,100 @@ __global__ void count_kernel(const uint32_t *__restrict__ key, int64_t n, uint32
         atomicAdd(counts + key[i], 1u);
 }
 
-// Exclusive scan of n_cells counts by one block of 1024 threads, each owning a
-// contiguous segment: segment totals, a block scan of the totals, then a second
-// pass over the segment writing running offsets.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t *counts, int n_cells)
+// Exclusive scan of the n_cells counts in three passes: per-block totals of 4096
+// counts, a scan of those totals by one block, then a block-level scan of each
+// 4096-count slice offset by its total.  Loads and stores are coalesced; each
+// thread owns 16 consecutive counts staged through shared memory.
+constexpr int kScanTile = 4096;
+constexpr int kScanThreads = 256;
+
+__global__ void __launch_bounds__(kScanThreads) scan_totals_kernel(const uint32_t *__restrict__ counts, int n_cells,
+                                                                   uint32_t *__restrict__ totals)
 {
-    __shared__ uint32_t warp_tot[32];
-    const int t = threadIdx.x;
-    const int per = (n_cells + 1023) / 1024;
-    const int b0 = min(n_cells, t * per), b1 = min(n_cells, b0 + per);
-    uint32_t run = 0;
-    for (int i = b0; i < b1; ++i)
-        run += counts[i];
-    uint32_t v = run;
-    const int lane = t & 31, w = t >> 5;
+    __shared__ uint32_t red[kScanThreads / 32];
+    const int base = blockIdx.x * kScanTile;
+    uint32_t v = 0;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+        if (base + i < n_cells)
+            v += counts[base + i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanThreads / 32; ++w)
+            t += red[w];
+        totals[blockIdx.x] = t;
+    }
+}
+
+// Block-wide exclusive scan of one value per thread; returns this thread's offset.
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o)
-            v += y;
+            x += y;
     }
     if (lane == 31)
-        warp_tot[w] = v;
+        warp_tot[w] = x;
     __syncthreads();
     if (w == 0) {
-        uint32_t x = warp_tot[lane];
+        uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o)
-                x += y;
+                t += y;
         }
-        warp_tot[lane] = x;
+        warp_tot[lane] = t;
     }
     __syncthreads();
-    uint32_t off = v - run + (w > 0 ? warp_tot[w - 1] : 0u);
-    for (int i = b0; i < b1; ++i) {
-        uint32_t c = counts[i];
-        counts[i] = off;
-        off += c;
+    return x - v + (w > 0 ? warp_tot[w - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(1024) scan_top_kernel(uint32_t *totals, int nb)
+{
+    __shared__ uint32_t warp_tot[32];
+    const uint32_t v = threadIdx.x < nb ? totals[threadIdx.x] : 0u;
+    const uint32_t e = block_exclusive_scan(v, warp_tot);
+    if (threadIdx.x < nb)
+        totals[threadIdx.x] = e;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(uint32_t *__restrict__ counts, int n_cells,
+                                                                  const uint32_t *__restrict__ totals)
+{
+    constexpr int per = kScanTile / kScanThreads;
+    __shared__ uint32_t tile[kScanTile + kScanTile / 32];   // padded: thread-strided reads avoid conflicts
+    __shared__ uint32_t warp_tot[32];
+    const int base = blockIdx.x * kScanTile;
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+        tile[i + (i >> 5)] = base + i < n_cells ? counts[base + i] : 0u;
+    __syncthreads();
+    uint32_t loc[per], run = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int i = threadIdx.x * per + q;
+        loc[q] = run;
+        run += tile[i + (i >> 5)];
     }
+    const uint32_t off = block_exclusive_scan(run, warp_tot) + totals[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+        const int i = threadIdx.x * per + q;
+        tile[i + (i >> 5)] = off + loc[q];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+        if (base + i < n_cells)
+            counts[base + i] = tile[i + (i >> 5)];
 }
 
 __global__ void scatter_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ offs,
@@ -207,7 +261,11 @@ cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32
         return e;
     const int g = grid_for(n, 256, 8);
     count_kernel<<<g, 256, 0, st>>>(key, n, counts);
-    scan_kernel<<<1, 1024, 0, st>>>(counts, G.n_cells);
+    const int nb = (G.n_cells + kScanTile - 1) / kScanTile;   // <= 256 for 2^20 cells
+    uint32_t *totals = counts + kMaxCells + 1;
+    scan_totals_kernel<<<nb, kScanThreads, 0, st>>>(counts, G.n_cells, totals);
+    scan_top_kernel<<<1, 1024, 0, st>>>(totals, nb);
+    scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(counts, G.n_cells, totals);
     scatter_kernel<<<g, 256, 0, st>>>(key, n, counts, perm);
     return cudaGetLastError();
 }

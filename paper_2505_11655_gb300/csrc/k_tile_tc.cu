@@ -29,8 +29,10 @@ namespace rift {
 
 constexpr int kTcS = 128;          // samples per tile (MMA M)
 constexpr int kTcW = 128;          // window columns per step (MMA N)
-constexpr int kTcThreads = 512;    // 16 warps
-constexpr int kTcQ = kTcThreads / kTcS;   // threads per sample in the gather (bin quarters)
+constexpr int kTcConsumers = 512;  // 16 consumer warps: drain, gather, log-sum-exp
+constexpr int kTcThreads = kTcConsumers + 32;   // plus one producer warp: TMA staging and MMA issue
+constexpr int kTcProducerWarp = kTcConsumers / 32;
+constexpr int kTcQ = kTcConsumers / kTcS;  // threads per sample in the gather (bin quarters)
 constexpr int kTcBPT = 16;         // bins per thread per chunk
 constexpr int kTcMaxBins = kTcQ * kTcBPT;
 constexpr int kTcRS = kTcW + 1;    // R row stride (floats): lane-per-sample accesses hit distinct banks
@@ -75,7 +77,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.quad = o; o = tc_al(o + (size_t)kTcS * 4, 16);
     L.gid = o;  o = tc_al(o + (size_t)kTcS * 4, 16);
     L.lse = o;  o = tc_al(o + (size_t)2 * kTcQ * kTcS * 4, 16);
-    L.bar = o;  o = tc_al(o + 4 * 8, 16);
+    L.bar = o;  o = tc_al(o + 6 * 8, 16);
     L.tptr = o; o = tc_al(o + 16, 16);
     L.end = o;
     return L;
@@ -180,8 +182,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     float *invs = reinterpret_cast<float *>(sm + L.inv);        // [K][kTcS] 2^-(row exponent + Q exponent)
     float *qds = reinterpret_cast<float *>(sm + L.quad);
     uint32_t *gid = reinterpret_cast<uint32_t *>(sm + L.gid);
-    uint64_t *bbar = reinterpret_cast<uint64_t *>(sm + L.bar);  // [0,1] bulk copies, [2,3] MMA commits
-    uint64_t *mbar = bbar + 2;
+    uint64_t *bbar = reinterpret_cast<uint64_t *>(sm + L.bar);  // [0,1] windows staged
+    uint64_t *fullb = bbar + 2;   // [0,1] MMAs of an accumulator complete (tcgen05.commit)
+    uint64_t *emptyb = bbar + 4;  // [0,1] accumulator drained by the 16 consumer warps
     uint32_t *tptr = reinterpret_cast<uint32_t *>(sm + L.tptr);
     double *sky = reinterpret_cast<double *>(sm + L.sky);
     float *par = reinterpret_cast<float *>(sm + L.par);
@@ -203,7 +206,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     const uint32_t part_bytes = (uint32_t)(part_halves * 2);
     const int qexp = q_exponent(*P.qmax_bits);
 
-    for (int j = tid; j < NT; j += kTcThreads) {
+    for (int j = tid; j < NT; j += blockDim.x) {
         bini[j] = bt.bin_i[j];
         binf[j] = bt.bin_f[j];
     }
@@ -212,6 +215,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     if (tid == 0) {
         for (int i = 0; i < 4; ++i)
             tc::mbar_init(bbar + i, 1);
+        for (int i = 4; i < 6; ++i)
+            tc::mbar_init(bbar + i, kTcConsumers / 32);
         tc::fence_mbar_init();
         abort_s = 0;
     }
@@ -219,7 +224,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tptr;
-    uint32_t bpar[2] = {0u, 0u}, mpar[2] = {0u, 0u};   // phase parities (identical in every thread)
+    // completed-phase counters per buffer: windows staged (producer), MMA commits
+    // (producer and consumers keep their own copies), accumulator drains (producer)
+    uint32_t nstage[2] = {0u, 0u}, ncommit[2] = {0u, 0u}, nfull[2] = {0u, 0u}, ndrain[2] = {0u, 0u};
+    const bool producer = warp == kTcProducerWarp;
 
     for (;;) {
         if (tid == 0)
@@ -267,7 +275,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
         // ---------------- B: delays, interpolation node split, x F_k
-        for (int it = tid; it < kTcS * K; it += kTcThreads) {
+        for (int it = tid; tid < kTcConsumers && it < kTcS * K; it += kTcConsumers) {
             const int s = it % kTcS, k = it / kTcS;
             const double *sp = sky + 4 * s;
             Sky sk{sp[0], sp[1], sp[2], sp[3]};
@@ -338,7 +346,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             ngroups_s = ng;
         }
         // ---------------- C: harmonics and coefficients C [K][2M][kTcS] (float32)
-        for (int it = tid; it < kTcS * M; it += kTcThreads) {
+        for (int it = tid; tid < kTcConsumers && it < kTcS * M; it += kTcConsumers) {
             const int s = it % kTcS, m = it / kTcS;
             const float *pc = pw + s * 2 * kTcPow, *ps = pc + kTcPow;
             float d = 0.f;
@@ -355,7 +363,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
         // ---------------- D: template term (Hermitian U, symmetric V halving), kTcQ threads per sample
-        {
+        if (tid < kTcConsumers) {
             const int s = tid & (kTcS - 1), part = tid >> 7;
             float acc = 0.f;
             for (int k = 0; k < K; ++k) {
@@ -387,7 +395,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 
         // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector)
         {
-            for (int it = tid; it < kTcS * K; it += kTcThreads) {
+            for (int it = tid; tid < kTcConsumers && it < kTcS * K; it += kTcConsumers) {
                 const int s = it % kTcS, k = it / kTcS;
                 const float *Ck = Cs + (size_t)k * R2 * kTcS + s;
                 float mx = 0.f;
@@ -416,162 +424,176 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         __syncthreads();
 
         // gather / fold ownership: thread -> sample s, bin quarter h of every chunk
-        const int gs = tid & (kTcS - 1), gh = tid >> 7;
-        const bool gok = gid[gs] != 0xffffffffu;
+        const int gs = tid & (kTcS - 1), gh = (tid >> 7) & (kTcQ - 1);
+        const bool gok = !producer && gid[gs] != 0xffffffffu;
         const float gqd = qds[gs];
         float run_mx = -INFINITY, run_sum = 0.f;
         int failed = 0;
         const int ngroups = ngroups_s;
         for (int grp = 0; grp < ngroups && !failed; ++grp) {
-        __syncthreads();   // every thread is past the previous sub-group's reads of lo_s / hi_s
-        if (tid < K) {
-            lo_s[tid] = glo[grp][tid];
-            hi_s[tid] = ghi[grp][tid];
-        }
-        __syncthreads();
-        const bool in_grp = gs >= gstart[grp] && gs < gstart[grp + 1];
-        int spread = 0;
-        for (int k = 0; k < K; ++k)
-            spread = max(spread, hi_s[k] - lo_s[k]);
-        int jmax = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
-        jmax = max(1, min(jmax, kTcMaxBins));
-        const int n_chunks = (NT + jmax - 1) / jmax;
-        const int jnom = (NT + n_chunks - 1) / n_chunks;
-        const int n_steps = n_chunks * K;
-
-        auto win0 = [&](int t) {
-            const int k = t % K, j0 = (t / K) * jnom;
-            // clamped so that a window never leaves the allocation of the Q copy
-            return min(max(lo_s[k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
-        };
-        // thread 0: stage window t into B buffer t & 1
-        auto stage = [&](int t) {
-            const int k = t % K, b = t & 1;
-            const int g0 = win0(t) >> 3;
-            const __half *src = P.Qtc + ((size_t)k * 2 * P.tc_groups + g0) * (size_t)kp * 8;
-            __half *dst = Bs + (size_t)b * 2 * part_halves;
-            tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
-            tc::bulk_g2s(dst, src, part_bytes, bbar + b);
-            tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
-        };
-        // thread 0: wait for window t, issue its 3 x (kp/16) MMAs into accumulator t & 1, commit
-        auto issue = [&](int t) -> bool {
-            const int k = t % K, b = t & 1;
-            if (!tc::mbar_wait(bbar + b, bpar[b], kWaitNs))
-                return false;
-            bpar[b] ^= 1u;
-            tc::tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(b * kTcW);
-            const uint32_t a_hi = tc::smem_u32(As + (size_t)(k * 2) * kTcS * kp);
-            const uint32_t a_lo = a_hi + (uint32_t)(kTcS * kp * 2);
-            const uint32_t b_hi = tc::smem_u32(Bs + (size_t)b * 2 * part_halves);
-            const uint32_t b_lo = b_hi + part_bytes;
-            for (int kk = 0; kk < kp / 16; ++kk) {
-                const uint32_t o = (uint32_t)kk * 256u;
-                tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc, kk > 0);
-                tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_lo + o, 128, sbo), idesc, 1);
-                tc::mma_f16(d, tc::smem_desc(a_lo + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc, 1);
+            int glo_k[kMaxDet];
+            int spread = 0;
+            for (int k = 0; k < K; ++k) {
+                glo_k[k] = glo[grp][k];
+                spread = max(spread, ghi[grp][k] - glo[grp][k]);
             }
-            tc::mma_commit(mbar + b);
-            return true;
-        };
+            const bool in_grp = gs >= gstart[grp] && gs < gstart[grp + 1];
+            int jmax = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
+            jmax = max(1, min(jmax, kTcMaxBins));
+            const int n_chunks = (NT + jmax - 1) / jmax;
+            const int jnom = (NT + n_chunks - 1) / n_chunks;
+            const int n_steps = n_chunks * K;
+            // window of step t: detector t % K, bins of chunk t / K; clamped so that a
+            // window never leaves the allocation of the Q copy
+            auto win0 = [&](int t) {
+                const int k = t % K, j0 = (t / K) * jnom;
+                return min(max(glo_k[k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
+            };
 
-        float lin[kTcBPT];
-#pragma unroll
-        for (int i = 0; i < kTcBPT; ++i)
-            lin[i] = 0.f;
-        if (tid == 0) {
-            stage(0);
-            if (n_steps > 1)
-                stage(1);
-            if (!issue(0))
-                failed = 1;
-        }
-
-        for (int t = 0; t < n_steps; ++t) {
-            const int k = t % K, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
-            const int jq = (J + kTcQ - 1) / kTcQ;                  // bins per quarter
-            const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins [jb, jb + jn)
-            const int i0 = i0s[k * kTcS + gs];
-            const float f0 = f0s[k * kTcS + gs];
-            {
-                const int b = t & 1;
-                if (tid == 0 && !failed && t + 1 < n_steps && !issue(t + 1))
-                    failed = 1;
-                // wait for the MMAs of step t
-                if (!failed && !tc::mbar_wait(mbar + b, mpar[b], kWaitNs))
-                    failed = 1;
-                mpar[b] ^= 1u;
-                tc::tc_fence_after();
-                if (tid == 0 && !failed && t + 2 < n_steps)
-                    stage(t + 2);   // buffer b is free: the MMAs of step t have completed
-                // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
-                if (!failed) {
-                    const int q = warp & 3, cb = warp >> 2;
-                    const int s = 32 * q + lane;
-                    const float sc = invs[k * kTcS + s];
-                    float *Rrow = Rs + s * kTcRS + 32 * cb;
-                    uint32_t v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcW + 32 * cb), v);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 32; ++i)
-                        Rrow[i] = __uint_as_float(v[i]) * sc;
+            if (producer) {
+                // ============ producer warp, lane 0: stage windows, issue MMAs
+                if (lane == 0) {
+                    auto stage = [&](int t) {
+                        const int k = t % K, b = t & 1;
+                        const int g0 = win0(t) >> 3;
+                        const __half *src = P.Qtc + ((size_t)k * 2 * P.tc_groups + g0) * (size_t)kp * 8;
+                        __half *dst = Bs + (size_t)b * 2 * part_halves;
+                        tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
+                        tc::bulk_g2s(dst, src, part_bytes, bbar + b);
+                        tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
+                        ++nstage[b];
+                    };
+                    stage(0);
+                    if (n_steps > 1)
+                        stage(1);
+                    for (int t = 0; t < n_steps && !failed; ++t) {
+                        const int k = t % K, b = t & 1;
+                        // window t staged; accumulator b drained by the consumers
+                        if (!tc::mbar_wait(bbar + b, (nstage[b] - 1) & 1u, kWaitNs) ||
+                            (ncommit[b] > ndrain[b] && !tc::mbar_wait(emptyb + b, ndrain[b] & 1u, kWaitNs))) {
+                            failed = 1;
+                            break;
+                        }
+                        if (ncommit[b] > ndrain[b])
+                            ++ndrain[b];
+                        tc::tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(b * kTcW);
+                        const uint32_t a_hi = tc::smem_u32(As + (size_t)(k * 2) * kTcS * kp);
+                        const uint32_t a_lo = a_hi + (uint32_t)(kTcS * kp * 2);
+                        const uint32_t b_hi = tc::smem_u32(Bs + (size_t)b * 2 * part_halves);
+                        const uint32_t b_lo = b_hi + part_bytes;
+                        for (int kk = 0; kk < kp / 16; ++kk) {
+                            const uint32_t o = (uint32_t)kk * 256u;
+                            tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc,
+                                        kk > 0);
+                            tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_lo + o, 128, sbo), idesc, 1);
+                            tc::mma_f16(d, tc::smem_desc(a_lo + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc, 1);
+                        }
+                        tc::mma_commit(fullb + b);
+                        ++ncommit[b];
+                        // window t + 1 goes into the other buffer once the MMAs of step t - 1 are done
+                        if (t >= 1 && t + 1 < n_steps) {
+                            const int bo = (t - 1) & 1;
+                            if (!tc::mbar_wait(fullb + bo, (ncommit[bo] - 1) & 1u, kWaitNs)) {
+                                failed = 1;
+                                break;
+                            }
+                            stage(t + 1);
+                        }
+                    }
+                    if (failed)
+                        abort_s = 1;
                 }
-                tc::tc_fence_before();
-                if (__syncthreads_or(failed)) {   // R complete; accumulator b free for step t + 2
-                    failed = 1;
-                    break;
-                }
-                const int iw0 = win0(t);
-                // padding samples and samples of other sub-groups read at the group's lowest
-                // offset, which keeps every read in the row; their sums are discarded
-                const bool mine = gok && in_grp;
-                const float *Rrow = Rs + gs * kTcRS + ((mine ? i0 : lo_s[k]) - iw0);
-                const float ff = mine ? f0 : 0.f;
-#pragma unroll
-                for (int i = 0; i < kTcBPT; ++i) {
-                    const int j = min(jb + i, j0 + J - 1);   // idle slots re-read the chunk's last bin
-                    const float sf = ff + binf[j];
-                    const int carry = sf >= 1.f;
-                    const float fr = sf - (float)carry;
-                    const float *rr = Rrow + bini[j] + carry;
-                    const float r0 = rr[0], r1 = rr[1];
-                    lin[i] += fmaf(fr, r1 - r0, r0);
-                }
-                __syncthreads();   // R consumed before the next drain
-            }
-            if (k == K - 1) {
-                // fold this thread's bins of the chunk into its running log-sum-exp
-                float cmx = -INFINITY;
-#pragma unroll
-                for (int i = 0; i < kTcBPT; ++i) {
-                    lin[i] -= gqd;
-                    if (i < jn)
-                        cmx = fmaxf(cmx, lin[i]);
-                }
-                if (lnL_t && gok && in_grp) {
-                    for (int i = 0; i < jn; ++i)
-#pragma unroll
-                        for (int u = 0; u < kTcBPT; ++u)
-                            if (u == i)
-                                lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)lin[u];
-                }
-                if (jn > 0 && in_grp) {
-                    const float nm = fmaxf(run_mx, cmx);
-                    float cs = 0.f;
-#pragma unroll
-                    for (int i = 0; i < kTcBPT; ++i)
-                        if (i < jn)
-                            cs += __expf(lin[i] - nm);
-                    run_sum = (run_mx == -INFINITY ? 0.f : run_sum * __expf(run_mx - nm)) + cs;
-                    run_mx = nm;
-                }
+                __syncwarp();
+            } else {
+                // ============ consumer warps: drain, gather, fold
+                float lin[kTcBPT];
 #pragma unroll
                 for (int i = 0; i < kTcBPT; ++i)
                     lin[i] = 0.f;
+                for (int t = 0; t < n_steps; ++t) {
+                    const int k = t % K, b = t & 1, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
+                    const int jq = (J + kTcQ - 1) / kTcQ;                 // bins per quarter
+                    const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins
+                    // one lane per warp waits for the MMAs of step t
+                    int ok = 1;
+                    if (lane == 0)
+                        ok = tc::mbar_wait(fullb + b, nfull[b] & 1u, kWaitNs) ? 1 : 0;
+                    ++nfull[b];
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    tc::tc_fence_after();
+                    // every consumer is past the previous gather (R is free); agree on failure
+                    if (tc::named_bar_or(1, kTcConsumers, !ok || abort_s)) {
+                        failed = 1;
+                        break;
+                    }
+                    {
+                        // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
+                        const int q = warp & 3, cb = warp >> 2;
+                        float *Rrow = Rs + (32 * q + lane) * kTcRS + 32 * cb;
+                        uint32_t v[32];
+                        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcW + 32 * cb), v);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            Rrow[i] = __uint_as_float(v[i]);
+                    }
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        tc::mbar_arrive(emptyb + b);
+                    tc::named_bar(1, kTcConsumers);   // R complete
+                    const int iw0 = win0(t);
+                    // padding samples and samples of other sub-groups read at the group's lowest
+                    // offset, which keeps every read in the row; their sums are discarded
+                    const bool mine = gok && in_grp;
+                    const float *Rrow = Rs + gs * kTcRS + ((mine ? i0s[k * kTcS + gs] : glo_k[k]) - iw0);
+                    const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
+                    const float sc = invs[k * kTcS + gs];
+#pragma unroll
+                    for (int i = 0; i < kTcBPT; ++i) {
+                        const int j = min(jb + i, j0 + J - 1);   // idle slots re-read the chunk's last bin
+                        const float sf = ff + binf[j];
+                        const int carry = sf >= 1.f;
+                        const float fr = sf - (float)carry;
+                        const float *rr = Rrow + bini[j] + carry;
+                        const float r0 = rr[0], r1 = rr[1];
+                        lin[i] = fmaf(sc, fmaf(fr, r1 - r0, r0), lin[i]);
+                    }
+                    if (k == K - 1) {
+                        // fold this thread's bins of the chunk into its running log-sum-exp
+                        float cmx = -INFINITY;
+#pragma unroll
+                        for (int i = 0; i < kTcBPT; ++i) {
+                            lin[i] -= gqd;
+                            if (i < jn)
+                                cmx = fmaxf(cmx, lin[i]);
+                        }
+                        if (lnL_t && gok && in_grp) {
+                            for (int i = 0; i < jn; ++i)
+#pragma unroll
+                                for (int u = 0; u < kTcBPT; ++u)
+                                    if (u == i)
+                                        lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)lin[u];
+                        }
+                        if (jn > 0 && in_grp) {
+                            const float nm = fmaxf(run_mx, cmx);
+                            float cs = 0.f;
+#pragma unroll
+                            for (int i = 0; i < kTcBPT; ++i)
+                                if (i < jn)
+                                    cs += __expf(lin[i] - nm);
+                            run_sum = (run_mx == -INFINITY ? 0.f : run_sum * __expf(run_mx - nm)) + cs;
+                            run_mx = nm;
+                        }
+#pragma unroll
+                        for (int i = 0; i < kTcBPT; ++i)
+                            lin[i] = 0.f;
+                    }
+                }
             }
-        }
+            // producer and consumers meet between sub-groups (and learn of a failure)
+            failed = __syncthreads_or(failed || abort_s);
         }   // sub-groups
         if (failed) {
             if (tid == 0) {
@@ -582,8 +604,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             continue;   // the next fetch sees abort_s and leaves the loop
         }
         // epilogue: combine the kTcQ partial log-sum-exps of each sample
-        lse[gh * kTcS + gs] = run_mx;
-        lse[(kTcQ + gh) * kTcS + gs] = run_sum;
+        if (!producer) {
+            lse[gh * kTcS + gs] = run_mx;
+            lse[(kTcQ + gh) * kTcS + gs] = run_sum;
+        }
         __syncthreads();
         if (tid < kTcS && gid[tid] != 0xffffffffu) {
             float mx = -INFINITY;
