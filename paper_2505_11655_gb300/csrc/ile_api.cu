@@ -58,7 +58,7 @@ struct rift_ile {
     SkyGrid grid{0, 0};   // sky grid of the current batch size
     // reductions and sampler
     double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
-    double *P = nullptr, *C = nullptr;
+    double *P = nullptr, *C = nullptr, *Lg = nullptr;
     int *err = nullptr;
     double *host_out = nullptr;   // pinned: stats + final + err
     uint32_t iteration = 0;
@@ -169,6 +169,7 @@ SamplerDev sampler_of(const rift_ile_t *h)
     SamplerDev S;
     S.P = h->P;
     S.C = h->C;
+    S.L = h->Lg;
     S.B = h->cfg.n_bins;
     S.d_min = h->cfg.d_min_mpc;
     S.d_max = h->cfg.d_max_mpc;
@@ -480,7 +481,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
         (rc = dalloc(h, &h->stats, (size_t)8 * RIFT_MAX_ITER)) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
         (rc = dalloc(h, &h->final_out, (size_t)8)) || (rc = dalloc(h, &h->P, (size_t)6 * B)) ||
-        (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->err, (size_t)4))) {
+        (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->Lg, (size_t)6 * B)) || (rc = dalloc(h, &h->err, (size_t)4))) {
         release(h);
         return rc;
     }

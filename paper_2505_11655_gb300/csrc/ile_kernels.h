@@ -43,6 +43,7 @@ cudaError_t launch_coeffs(const Problem &P, bool fp64, const double *theta, int6
 struct SamplerDev {
     double *P;       // [6][B] masses
     double *C;       // [6][B+1] running sums
+    double *L;       // [6][B] log densities ln(B P[b] / C[B]) of the bins
     int B;
     double d_min, d_max;
     double floor_eps, temper;

@@ -25,13 +25,16 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
                                                             double *__restrict__ theta, double *__restrict__ lnpw,
                                                             uint64_t *__restrict__ bins, uint32_t *__restrict__ key)
 {
-    extern __shared__ double sC[];   // [6][B+1] running sums, then [6][B] masses
+    extern __shared__ double sC[];   // [6][B+1] running sums, then [6][B] masses, [6][B] log densities
     const int B = S.B;
     double *sP = sC + 6 * (B + 1);
+    double *sL = sP + 6 * B;
     for (int e = threadIdx.x; e < 6 * (B + 1); e += blockDim.x)
         sC[e] = S.C[e];
-    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x)
+    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x) {
         sP[e] = S.P[e];
+        sL[e] = S.L[e];
+    }
     __syncthreads();
     const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
     const double d3lo = S.d_min * S.d_min * S.d_min, d3hi = S.d_max * S.d_max * S.d_max;
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
             if (t >= 1.0)
                 t = 0x1.fffffffffffffp-1;
             v[d] = (lo + t) / B;
-            lr -= log(B * pb / tot);
+            lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
             packed |= (uint64_t)lo << (10 * d);
         }
         double th[6];
@@ -106,7 +109,7 @@ cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, in
 {
     if (n <= 0)
         return cudaSuccess;
-    size_t smem = sizeof(double) * (6 * (S.B + 1) + 6 * S.B);
+    size_t smem = sizeof(double) * (6 * (S.B + 1) + 12 * S.B);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
@@ -504,6 +507,10 @@ __global__ void adapt_final_kernel(SamplerDev S, const double *__restrict__ part
             S.C[d * (B + 1) + b + 1] = run;
         }
     }
+    __syncwarp();
+    const double ctot = S.C[d * (B + 1) + B];
+    for (int b = lane; b < B; b += 32)
+        S.L[d * B + b] = log(B * S.P[d * B + b] / ctot);
 }
 
 cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
@@ -536,6 +543,8 @@ __global__ void build_cdf_kernel(SamplerDev S)
         run += S.P[d * S.B + b];
         S.C[d * (S.B + 1) + b + 1] = run;
     }
+    for (int b = 0; b < S.B; ++b)
+        S.L[d * S.B + b] = log(S.B * S.P[d * S.B + b] / run);
 }
 
 cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st)
