@@ -35,7 +35,8 @@ constexpr int kTcProducerWarp = kTcConsumers / 32;
 constexpr int kTcQ = kTcConsumers / kTcS;  // threads per sample in the gather (bin quarters)
 constexpr int kTcBPT = 16;         // bins per thread per chunk
 constexpr int kTcMaxBins = kTcQ * kTcBPT;
-constexpr int kTcRS = kTcW + 1;    // R row stride (floats): lane-per-sample accesses hit distinct banks
+// R is kept transposed, Rt[column][sample]: the drain (lane = sample, fixed column) and
+// the gather (lane = sample, per-sample column) both touch bank = sample, conflict-free.
 constexpr int kTcPow = 16;
 constexpr uint64_t kWaitNs = 1000000000ull;
 // A tile whose samples span more than this many Q samples at some detector is cut
@@ -67,7 +68,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.qpart = s; s = tc_al(s + (size_t)kTcQ * kTcS * 4, 16);
     o = tc_al(L.b + (bbytes > s - L.b ? bbytes : s - L.b));
     L.r = o;
-    const size_t rbytes = (size_t)kTcS * kTcRS * 4, cbytes = (size_t)K * 2 * M * kTcS * 4;
+    const size_t rbytes = (size_t)kTcW * kTcS * 4, cbytes = (size_t)K * 2 * M * kTcS * 4;
     o = tc_al(o + (rbytes > cbytes ? rbytes : cbytes), 16);
     L.bini = o; o = tc_al(o + (size_t)n_t * 4, 16);
     L.binf = o; o = tc_al(o + (size_t)n_t * 4, 16);
@@ -174,7 +175,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     const int kp = L.kp, kcores = kp / 8;
     __half *As = reinterpret_cast<__half *>(sm + L.a);          // [K][2][kTcS x kp] canonical K-major
     __half *Bs = reinterpret_cast<__half *>(sm + L.b);          // [2 buf][2 part][kTcW x kp]
-    float *Rs = reinterpret_cast<float *>(sm + L.r);            // R [kTcS][kTcRS] (prologue: C [K][2M][kTcS])
+    float *Rs = reinterpret_cast<float *>(sm + L.r);            // Rt [kTcW][kTcS] (prologue: C [K][2M][kTcS])
     int *bini = reinterpret_cast<int *>(sm + L.bini);
     float *binf = reinterpret_cast<float *>(sm + L.binf);
     int *i0s = reinterpret_cast<int *>(sm + L.i0);              // [K][kTcS]
@@ -507,10 +508,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 __syncwarp();
             } else {
                 // ============ consumer warps: drain, gather, fold
-                float lin[kTcBPT];
+                float lin[kTcBPT], bfj[kTcBPT];
+                int bj[kTcBPT];
 #pragma unroll
-                for (int i = 0; i < kTcBPT; ++i)
+                for (int i = 0; i < kTcBPT; ++i) {
                     lin[i] = 0.f;
+                    bfj[i] = 0.f;
+                    bj[i] = 0;
+                }
                 for (int t = 0; t < n_steps; ++t) {
                     const int k = t % K, b = t & 1, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
                     const int jq = (J + kTcQ - 1) / kTcQ;                 // bins per quarter
@@ -530,13 +535,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     {
                         // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
                         const int q = warp & 3, cb = warp >> 2;
-                        float *Rrow = Rs + (32 * q + lane) * kTcRS + 32 * cb;
+                        float *Rcol = Rs + (32 * cb) * kTcS + 32 * q + lane;
                         uint32_t v[32];
                         tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcW + 32 * cb), v);
                         tc::tmem_ld_wait();
 #pragma unroll
                         for (int i = 0; i < 32; ++i)
-                            Rrow[i] = __uint_as_float(v[i]);
+                            Rcol[i * kTcS] = __uint_as_float(v[i]);
                     }
                     tc::tc_fence_before();
                     __syncwarp();
@@ -547,17 +552,26 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     // padding samples and samples of other sub-groups read at the group's lowest
                     // offset, which keeps every read in the row; their sums are discarded
                     const bool mine = gok && in_grp;
-                    const float *Rrow = Rs + gs * kTcRS + ((mine ? i0s[k * kTcS + gs] : glo_k[k]) - iw0);
+                    const float *Rcol = Rs + ((mine ? i0s[k * kTcS + gs] : glo_k[k]) - iw0) * kTcS + gs;
                     const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
                     const float sc = invs[k * kTcS + gs];
+                    if (k == 0) {
+                        // this thread's bins of the chunk, shared by every detector (idle slots
+                        // re-read the chunk's last bin)
+#pragma unroll
+                        for (int i = 0; i < kTcBPT; ++i) {
+                            const int j = min(jb + i, j0 + J - 1);
+                            bj[i] = bini[j];
+                            bfj[i] = binf[j];
+                        }
+                    }
 #pragma unroll
                     for (int i = 0; i < kTcBPT; ++i) {
-                        const int j = min(jb + i, j0 + J - 1);   // idle slots re-read the chunk's last bin
-                        const float sf = ff + binf[j];
+                        const float sf = ff + bfj[i];
                         const int carry = sf >= 1.f;
                         const float fr = sf - (float)carry;
-                        const float *rr = Rrow + bini[j] + carry;
-                        const float r0 = rr[0], r1 = rr[1];
+                        const float *rr = Rcol + (bj[i] + carry) * kTcS;
+                        const float r0 = rr[0], r1 = rr[kTcS];
                         lin[i] = fmaf(sc, fmaf(fr, r1 - r0, r0), lin[i]);
                     }
                     if (k == K - 1) {
