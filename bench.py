@@ -43,8 +43,8 @@ N_SAMPLES = 1_000_000
 FP32_LANES_PER_SM = 128
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
-PROFILE = os.path.join(ROOT, "profiles", "lnl_fp32_single_large.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", "k_tile.cu")
+PROFILE = os.path.join(ROOT, "profiles", "lnl_tc_single_large.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", "k_tile_tc.cu")
 
 
 def workload_config(prob, n):
@@ -278,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(prob, n),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "lnl_tile_kernel", "kernel_ms": lnl_avg,
+                     "kernel": "lnl_tc_kernel", "kernel_ms": lnl_avg,
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
                      "flops_per_sample": fps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
