@@ -58,6 +58,8 @@ struct rift_ile {
     SkyGrid grid{0, 0};   // sky grid of the current batch size
     // reductions and sampler
     double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
+    double *pooled_scratch = nullptr;
+    uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
     double *P = nullptr, *C = nullptr, *Lg = nullptr;
     int *err = nullptr;
     double *host_out = nullptr;   // pinned: stats + final + err
@@ -289,6 +291,22 @@ cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *
                            h->stream);
 }
 
+// RIFT_MIXED: samples whose log-weight is within kMixedMargin of the batch maximum
+// are re-evaluated in float64 (their weight relative to the largest is >= e^-40).
+constexpr double kMixedMargin = 40.0;
+constexpr int kScratchSlot = RIFT_MAX_ITER;
+
+int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, const double *lnpw, double *lnw)
+{
+    const double *key = lnw ? lnw : lnL_tmarg;
+    CK(launch_reduce(key, lnL_tmarg, n, h->red_partial, h->stats, kScratchSlot, h->pooled_scratch, 1, h->err,
+                     h->stream));
+    CK(launch_select(key, n, h->stats, kScratchSlot, kMixedMargin, h->sel_idx, h->sel_count, h->stream));
+    CK(launch_refine(h->prob, theta, h->sel_idx, h->sel_count, n, lnL_tmarg, lnpw, lnw, h->err, h->stream));
+    h->launches += 4;
+    return RIFT_OK;
+}
+
 // Sky grid sized for a batch of n samples.
 int grid_for_batch(rift_ile_t *h, int64_t n)
 {
@@ -310,6 +328,8 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
     CK(launch_keys(h->grid, theta, n, h->key, h->stream));
     CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
     CK(launch_tiled(h, theta, n, lnL_tmarg, lnL_t, lnpw, lnw));
+    if (h->cfg.precision == RIFT_MIXED)
+        RK(refine_batch(h, theta, n, lnL_tmarg, lnpw, lnw));
     return RIFT_OK;
 }
 
@@ -325,6 +345,8 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
     CK(cudaEventRecord(h->ev[slot][1], h->stream));
     if (use_fp32(h))
         CK(launch_tiled(h, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw));
+    if (h->cfg.precision == RIFT_MIXED)
+        RK(refine_batch(h, h->theta, n, h->lnL, h->lnpw, h->lnw));
     else
         CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
     CK(cudaEventRecord(h->ev[slot][2], h->stream));
@@ -479,7 +501,9 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->Qtc, (size_t)K * 2 * ((cfg->n_q + 7) / 8 + 17) * ((2 * M + 15) / 16 * 16) * 8)) ||
         (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||
         (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
-        (rc = dalloc(h, &h->stats, (size_t)8 * RIFT_MAX_ITER)) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
+        (rc = dalloc(h, &h->stats, (size_t)8 * (RIFT_MAX_ITER + 1))) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
+        (rc = dalloc(h, &h->pooled_scratch, (size_t)8)) || (rc = dalloc(h, &h->sel_idx, (size_t)N)) ||
+        (rc = dalloc(h, &h->sel_count, (size_t)4)) ||
         (rc = dalloc(h, &h->final_out, (size_t)8)) || (rc = dalloc(h, &h->P, (size_t)6 * B)) ||
         (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->Lg, (size_t)6 * B)) || (rc = dalloc(h, &h->err, (size_t)4))) {
         release(h);

@@ -35,6 +35,14 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
 cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups, unsigned int *qmax_bits,
                            __half *Qtc, cudaStream_t st);
 
+// Precision mode RIFT_MIXED: indices of the samples with key[i] >= stats[slot].max - margin
+// (idx[*count]), then their float64 re-evaluation in place (lnL_tmarg, and lnw when given).
+cudaError_t launch_select(const double *key, int64_t n, const double *stats, int slot, double margin, uint32_t *idx,
+                          uint32_t *count, cudaStream_t st);
+cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t *idx, const uint32_t *count,
+                          int64_t max_count, double *lnL_tmarg, const double *lnpw, double *lnw, int *err,
+                          cudaStream_t st);
+
 // Per-sample coefficients: c[n][K][M] (complex), dt[n][K], quad[n]; any may be null.
 cudaError_t launch_coeffs(const Problem &P, bool fp64, const double *theta, int64_t n, double2 *c, double *dt,
                           double *quad, cudaStream_t st);

@@ -275,6 +275,55 @@ def test_tc_path_plain_config_and_spread_sky(G, orc, monkeypatch):
         assert_fp32_close(got, *olnL(orc, p, th))
 
 
+# ------------------------------------------------------------------------------ mixed precision
+
+def high_snr_realisable(orc, snr=150.0, seed=71):
+    """21 modes, 3 detectors, 16384 Hz, q=20-like hierarchy, an injection built
+    from F_k Y_lm at theta_true (so ln L reaches ~snr^2/2 near theta_true)."""
+    th_true = np.array([2.2, -0.5, 1.1, 0.7, 1.4, 300.0])
+    probe = S.high_snr_problem(snr=snr, point=seed)
+    F, Y, _, dt = orc.coeffs(probe, th_true)
+    p = S.high_snr_problem(snr=snr, point=seed, a0=np.outer(F[0], Y[0]), dt_true=dt[0])
+    return p, th_true
+
+
+def test_mixed_precision_high_snr(G, orc):
+    """SNR 150: samples near the injection have ln L ~ 1e4.  The float32 path
+    carries ~1e-3..1e-2 rounding there; RIFT_MIXED re-evaluates every sample
+    within 40 of the batch maximum in float64 and meets 1e-3."""
+    p, th_true = high_snr_realisable(orc)
+    rng = np.random.default_rng(8)
+    near = th_true + rng.normal(0, 1, (600, 6)) * np.array([6e-4, 6e-4, 1.5e-3, 1.5e-3, 1.5e-3, 0.3])
+    th = np.concatenate([near, S.prior_samples(1400, 72)])
+    exp, _, quad = orc.lnL(p, th, want_bins=True)
+    assert exp.max() > 5000
+    with G.ILE(p, precision=G.RIFT_MIXED, max_samples=4096) as s:
+        got = s.eval(th)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
+        got32 = s.eval(th)
+    top = exp >= exp.max() - 40.0
+    assert top.sum() >= 50
+    assert np.max(np.abs(got[top] - exp[top])) <= 1e-3
+    assert np.all(np.abs(got - exp) <= fp32_floor(exp, quad))
+    # the float32 path alone is measurably worse on the same samples
+    assert np.max(np.abs(got32[top] - exp[top])) > np.max(np.abs(got[top] - exp[top]))
+
+
+def test_mixed_precision_adapt_lnZ(G, orc):
+    """Adaptive iterations in RIFT_MIXED at SNR 150: ln Z of the device's own
+    sample stream within 1e-3 of the oracle's."""
+    p, th_true = high_snr_realisable(orc)
+    n = 20000
+    with G.ILE(p, precision=G.RIFT_MIXED, max_samples=n, n_bins=32, seed=9) as s:
+        r = s.adapt(3, n)
+        th, lr, ll, lw = s.last_batch(n)
+    oll, oq = olnL(orc, p, th)
+    red = orc.reduce(oll + lr)
+    assert abs(r["lnZ_iter"][2] - red["lnZ"]) <= 1e-3
+    top = oll + lr >= np.max(oll + lr) - 40.0
+    assert np.max(np.abs(ll[top] - oll[top])) <= 1e-3
+
+
 # ------------------------------------------------------------------------------ full size
 
 @pytest.mark.slow
