@@ -343,12 +343,13 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
     if (use_fp32(h))
         CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
     CK(cudaEventRecord(h->ev[slot][1], h->stream));
-    if (use_fp32(h))
-        CK(launch_tiled(h, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw));
-    if (h->cfg.precision == RIFT_MIXED)
-        RK(refine_batch(h, h->theta, n, h->lnL, h->lnpw, h->lnw));
-    else
+    if (!use_fp32(h)) {
         CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
+    } else {
+        CK(launch_tiled(h, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw));
+        if (h->cfg.precision == RIFT_MIXED)
+            RK(refine_batch(h, h->theta, n, h->lnL, h->lnpw, h->lnw));
+    }
     CK(cudaEventRecord(h->ev[slot][2], h->stream));
     CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, slot, h->pooled, reset_pooled ? 1 : 0, h->err,
                      h->stream));

@@ -213,7 +213,12 @@ def test_fp32_marginalize_against_oracle_on_device_stream(G, orc):
     assert abs(r["n_eff"] - red["n_eff"]) <= 1e-2 * red["n_eff"]
 
 
-def test_fp32_adapt_two_iterations(G, orc):
+@pytest.mark.parametrize("tc", ["0", "1"])
+def test_fp32_adapt_two_iterations(G, orc, monkeypatch, tc):
+    """Adaptive iterations through the CUDA-core and the tensor-core kernels.  The
+    batch's ln L must be the float32 kernel's own output: it differs from the
+    float64 kernel's values in the low bits of (almost) every sample."""
+    monkeypatch.setenv("RIFT_ILE_TC", tc)
     p = S.single_large_problem()
     n = 30000
     with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=6) as s:
@@ -223,6 +228,9 @@ def test_fp32_adapt_two_iterations(G, orc):
     red = orc.reduce(oll + lr)
     assert abs(r["lnZ_iter"][1] - red["lnZ"]) <= 1e-3
     assert r["n_total"] == 2 * n
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n) as s64:
+        ll64 = s64.eval(th)
+    assert np.mean(ll == ll64) < 0.05
 
 
 # ------------------------------------------------------------------------------ tensor-core tiles
