@@ -185,6 +185,10 @@ int rift_ile_set_state(rift_ile_t *h, const void *buf, size_t len);
 /* Histogram masses P [6][n_bins] (host) of the current sampling prior. */
 int rift_ile_get_sampler(const rift_ile_t *h, double *P);
 
+/* Device bytes a handle created from `cfg` allocates (an upper bound, used for
+ * admission control), or -1 if `cfg` is invalid.  Host memory only; no CUDA call. */
+int64_t rift_ile_footprint(const rift_ile_config *cfg);
+
 /* Number of kernels this handle has launched since creation (diagnostics: lets a
  * caller count device launches inside a timed region).  Returns -1 for NULL. */
 int64_t rift_ile_kernel_launches(const rift_ile_t *h);
@@ -219,6 +223,51 @@ int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, dou
 
 void rift_ile_destroy(rift_ile_t *h);
 const char *rift_ile_strerror(int code);
+
+/* ---- serving ---------------------------------------------------------------------------
+ * A request loop that accepts ILE solves (one intrinsic point each: its problem, Q/U/V and
+ * sample budget) as they arrive, admits them while the summed device footprint of the
+ * solves in flight stays within a budget and a slot is free, and runs admitted solves
+ * concurrently, each on its own CUDA stream and host worker, so that requests arriving
+ * while others are on the GPU overlap with them (continuous admission, not a queue that
+ * drains one solve at a time).  Requests are admitted in arrival order.  Each solve is
+ * rift_ile_create -> rift_ile_set_overlaps -> rift_ile_adapt(n_iter, n_per_iter) ->
+ * rift_ile_destroy on its slot; its result does not depend on what else is in flight.
+ * Times are milliseconds since rift_srv_create (steady clock). */
+typedef struct rift_srv rift_srv_t;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* limit on the summed rift_ile_footprint of solves in flight */
+    int32_t max_slots;        /* solves in flight at most (1..64)                            */
+} rift_srv_config;
+
+typedef struct {
+    const rift_ile_config *cfg; /* problem; copied at submit (cfg->max_samples >= n_per_iter) */
+    const void *Q, *U, *V;      /* host complex128 arrays, shapes as rift_ile_set_overlaps; copied */
+    int32_t n_iter;             /* adaptive iterations (1..RIFT_MAX_ITER)                   */
+    int64_t n_per_iter;         /* samples per iteration                                    */
+    uint64_t tag;               /* returned with the completion                             */
+} rift_srv_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;            /* RIFT_OK or the first failing call's status */
+    rift_ile_result result;
+    double t_submit_ms, t_admit_ms, t_done_ms;
+} rift_srv_completion;
+
+/* RIFT_EINVAL for a bad configuration; RIFT_ECUDA if no device or stream can be made. */
+int rift_srv_create(const rift_srv_config *cfg, rift_srv_t **out);
+/* Queue one request (inputs copied before returning).  RIFT_EINVAL for an invalid
+ * request; RIFT_ENOMEM if its footprint alone exceeds the budget. */
+int rift_srv_submit(rift_srv_t *s, const rift_srv_request *req);
+/* Move up to `max` completions into `out` (*n_out of them), waiting up to timeout_ms
+ * for the first one (0: do not wait). */
+int rift_srv_poll(rift_srv_t *s, rift_srv_completion *out, int32_t max, int32_t timeout_ms, int32_t *n_out);
+/* Requests waiting for admission and solves in flight. */
+int rift_srv_pending(rift_srv_t *s, int32_t *queued, int32_t *active);
+/* Finishes the solves in flight, drops queued requests, joins the workers. */
+void rift_srv_destroy(rift_srv_t *s);
 
 #ifdef __cplusplus
 }

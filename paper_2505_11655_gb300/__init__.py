@@ -29,8 +29,9 @@ RIFT_MAX_ITER = 64
 
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
-            "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_destroy",
-            "rift_ile_strerror"]
+            "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
+            "rift_ile_destroy", "rift_ile_strerror", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
+            "rift_srv_pending", "rift_srv_destroy"]
 
 
 class RiftError(RuntimeError):
@@ -68,6 +69,20 @@ class rift_ile_result(C.Structure):
                     time_ms=list(self.time_ms))
 
 
+class rift_srv_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_slots", C.c_int32)]
+
+
+class rift_srv_request(C.Structure):
+    _fields_ = [("cfg", C.POINTER(rift_ile_config)), ("Q", C.c_void_p), ("U", C.c_void_p), ("V", C.c_void_p),
+                ("n_iter", C.c_int32), ("n_per_iter", C.c_int64), ("tag", C.c_uint64)]
+
+
+class rift_srv_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("result", rift_ile_result),
+                ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double), ("t_done_ms", C.c_double)]
+
+
 _lib = None
 
 
@@ -93,6 +108,14 @@ def load(build_if_missing: bool = False):
     L.rift_ile_set_state.argtypes = [vp, vp, C.c_size_t]
     L.rift_ile_get_sampler.argtypes = [vp, vp]
     L.rift_ile_reduce_noalloc.argtypes = [vp, vp, i64, vp, vp]
+    L.rift_ile_footprint.argtypes = [C.POINTER(rift_ile_config)]
+    L.rift_ile_footprint.restype = C.c_int64
+    L.rift_srv_create.argtypes = [C.POINTER(rift_srv_config), C.POINTER(vp)]
+    L.rift_srv_submit.argtypes = [vp, C.POINTER(rift_srv_request)]
+    L.rift_srv_poll.argtypes = [vp, C.POINTER(rift_srv_completion), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+    L.rift_srv_pending.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.rift_srv_destroy.argtypes = [vp]
+    L.rift_srv_destroy.restype = None
     L.rift_ile_kernel_launches.argtypes = [vp]
     L.rift_ile_kernel_launches.restype = C.c_int64
     L.rift_ile_destroy.argtypes = [vp]
@@ -100,7 +123,8 @@ def load(build_if_missing: bool = False):
     L.rift_ile_strerror.argtypes = [C.c_int]
     L.rift_ile_strerror.restype = C.c_char_p
     for name in EXPORTED:
-        if name not in ("rift_ile_destroy", "rift_ile_strerror", "rift_ile_kernel_launches"):
+        if name not in ("rift_ile_destroy", "rift_ile_strerror", "rift_ile_kernel_launches", "rift_ile_footprint",
+                        "rift_srv_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -208,6 +232,40 @@ def rift_ile_reduce_noalloc(lnw, n, out, lnL=None, stream=None):
     _check(load().rift_ile_reduce_noalloc(_ptr(lnw), _ptr(lnL), int(n), _ptr(out), st), "rift_ile_reduce_noalloc")
 
 
+def rift_ile_footprint(cfg):
+    return int(load().rift_ile_footprint(C.byref(cfg)))
+
+
+def rift_srv_create(hbm_budget_bytes, max_slots):
+    h = C.c_void_p()
+    cfg = rift_srv_config(int(hbm_budget_bytes), int(max_slots))
+    _check(load().rift_srv_create(C.byref(cfg), C.byref(h)), "rift_srv_create")
+    return h
+
+
+def rift_srv_submit(srv, cfg, Q, U, V, n_iter, n_per_iter, tag):
+    req = rift_srv_request(C.pointer(cfg), _ptr(Q), _ptr(U), _ptr(V), int(n_iter), int(n_per_iter), int(tag))
+    _check(load().rift_srv_submit(srv, C.byref(req)), "rift_srv_submit")
+
+
+def rift_srv_poll(srv, max_n=256, timeout_ms=0):
+    buf = (rift_srv_completion * max_n)()
+    n = C.c_int32()
+    _check(load().rift_srv_poll(srv, buf, max_n, int(timeout_ms), C.byref(n)), "rift_srv_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def rift_srv_pending(srv):
+    q, a = C.c_int32(), C.c_int32()
+    _check(load().rift_srv_pending(srv, C.byref(q), C.byref(a)), "rift_srv_pending")
+    return q.value, a.value
+
+
+def rift_srv_destroy(srv):
+    if srv:
+        load().rift_srv_destroy(srv)
+
+
 def rift_ile_kernel_launches(h):
     return int(load().rift_ile_kernel_launches(h))
 
@@ -222,6 +280,76 @@ def rift_ile_strerror(code):
 
 
 # ---------------------------------------------------------------------------------- convenience
+
+def make_config(prob, precision=RIFT_FP32, max_samples=1 << 20, n_bins=64, adapt_floor=0.1, adapt_temper=1.0,
+                seed=1):
+    """rift_ile_config for a problem (attributes of ile_synth.Problem) and the host
+    arrays it points at (keep the returned dict alive as long as the config)."""
+    keep = dict(
+        det_tensor=np.ascontiguousarray(prob.det_tensor, np.float64),
+        det_pos=np.ascontiguousarray(prob.det_pos, np.float64),
+        lm=np.ascontiguousarray(prob.lm, np.int32),
+        q_t0=np.ascontiguousarray(prob.q_t0, np.float64),
+    )
+    cfg = rift_ile_config(
+        keep["det_tensor"].shape[0], _ptr(keep["det_tensor"]), _ptr(keep["det_pos"]), float(prob.gmst),
+        keep["lm"].shape[0], _ptr(keep["lm"]), float(prob.fs), int(prob.n_q), _ptr(keep["q_t0"]), float(prob.t_lo),
+        float(prob.t_hi), int(prob.n_t), float(prob.d_ref), float(prob.d_min), float(prob.d_max),
+        int(prob.quad_norm), int(precision), int(n_bins), float(adapt_floor), float(adapt_temper), int(seed),
+        int(max_samples))
+    return cfg, keep
+
+
+class Server:
+    """Request loop for many solves (rift_srv_*): submit problems as they arrive,
+    poll completions with their submit/admit/done times."""
+
+    def __init__(self, hbm_budget_bytes=32 << 30, max_slots=8):
+        self.h = rift_srv_create(hbm_budget_bytes, max_slots)
+        self._keep = []
+
+    def submit(self, prob, n_iter, n_per_iter, tag, precision=RIFT_FP32, n_bins=64, seed=1):
+        cfg, keep = make_config(prob, precision, max_samples=n_per_iter, n_bins=n_bins, seed=seed)
+        arrs = [np.ascontiguousarray(x, np.complex128) for x in (prob.Q, prob.U, prob.V)]
+        rift_srv_submit(self.h, cfg, arrs[0], arrs[1], arrs[2], n_iter, n_per_iter, tag)
+
+    def poll(self, max_n=256, timeout_ms=0):
+        out = []
+        for c in rift_srv_poll(self.h, max_n, timeout_ms):
+            d = c.result.as_dict()
+            d.update(tag=c.tag, status=c.status, t_submit_ms=c.t_submit_ms, t_admit_ms=c.t_admit_ms,
+                     t_done_ms=c.t_done_ms)
+            out.append(d)
+        return out
+
+    def pending(self):
+        return rift_srv_pending(self.h)
+
+    def drain(self, n_expected, timeout_s=600.0):
+        """Poll until n_expected completions arrived (or the timeout)."""
+        import time
+        got, t0 = [], time.time()
+        while len(got) < n_expected and time.time() - t0 < timeout_s:
+            got += self.poll(256, 100)
+        return got
+
+    def close(self):
+        if getattr(self, "h", None):
+            rift_srv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
 
 class ILE:
     """One handle for one intrinsic point.  ``prob`` carries the problem's host

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librift_ile.so")
-SOURCES = ["ile_api.cu", "k_lnl.cu", "k_tile.cu", "k_tile_tc.cu", "k_refine.cu", "k_sampler.cu"]
+SOURCES = ["ile_api.cu", "ile_serve.cu", "k_lnl.cu", "k_tile.cu", "k_tile_tc.cu", "k_refine.cu", "k_sampler.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         for _, err in results:
             sys.stderr.write(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart"]
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart", "-Xcompiler", "-pthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

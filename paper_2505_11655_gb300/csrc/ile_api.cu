@@ -4,6 +4,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
+#include <mutex>
 #include <new>
 #include <set>
 #include <utility>
@@ -62,21 +64,37 @@ struct rift_ile {
     uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
     double *P = nullptr, *C = nullptr, *Lg = nullptr;
     int *err = nullptr;
-    double *host_out = nullptr;   // pinned: stats + final + err
+    std::vector<double> host_out;   // err word, pooled record, per-iteration records
     uint32_t iteration = 0;
     int64_t last_n = 0;
     int64_t launches = 0;
-    cudaEvent_t ev[RIFT_MAX_ITER][4];
-    bool events_made = false;
+    std::vector<std::array<cudaEvent_t, 4>> ev;   // per-iteration stage timers, created on first use
     std::vector<void *> allocs;
 };
 
 namespace {
 
+// Device buffers come from the device's stream-ordered memory pool on the handle's
+// stream: no device-wide synchronisation, and freed blocks stay cached for the next
+// handle (the pool's release threshold is raised once per process).
+void keep_pool_cached()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    });
+}
+
 template <typename T> int dalloc(rift_ile_t *h, T **p, size_t count)
 {
     void *q = nullptr;
-    if (cudaMalloc(&q, count * sizeof(T) + 16) != cudaSuccess) {
+    if (cudaMallocAsync(&q, count * sizeof(T) + 16, h->stream) != cudaSuccess) {
         cudaGetLastError();
         return RIFT_ENOMEM;
     }
@@ -89,20 +107,29 @@ void release(rift_ile_t *h)
 {
     if (!h)
         return;
-    if (h->stream)
-        cudaStreamSynchronize(h->stream);
-    else
-        cudaDeviceSynchronize();
     for (void *p : h->allocs)
-        cudaFree(p);
+        cudaFreeAsync(p, h->stream);
     h->allocs.clear();
-    if (h->host_out)
-        cudaFreeHost(h->host_out);
-    if (h->events_made)
-        for (auto &row : h->ev)
-            for (auto &e : row)
-                cudaEventDestroy(e);
+    cudaStreamSynchronize(h->stream);
+    for (auto &row : h->ev)
+        for (auto &e : row)
+            cudaEventDestroy(e);
+    cudaGetLastError();
     delete h;
+}
+
+int ensure_events(rift_ile_t *h, int n)
+{
+    while ((int)h->ev.size() < n) {
+        std::array<cudaEvent_t, 4> row{};
+        for (auto &e : row)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return RIFT_ECUDA;
+            }
+        h->ev.push_back(row);
+    }
+    return RIFT_OK;
 }
 
 double factorial(int n)
@@ -338,6 +365,7 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
 {
     SamplerDev S = sampler_of(h);
     RK(grid_for_batch(h, n));
+    RK(ensure_events(h, slot + 1));
     CK(cudaEventRecord(h->ev[slot][0], h->stream));
     CK(launch_draw(S, h->grid, h->iteration, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
     if (use_fp32(h))
@@ -436,6 +464,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         cudaGetLastError();
         return RIFT_ECUDA;
     }
+    keep_pool_cached();
     rift_ile_t *h = new (std::nothrow) rift_ile_t();
     if (!h)
         return RIFT_ENOMEM;
@@ -510,20 +539,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         release(h);
         return rc;
     }
-    if (cudaMallocHost(&h->host_out, sizeof(double) * (8 + 8 * RIFT_MAX_ITER + 8)) != cudaSuccess) {
-        cudaGetLastError();
-        h->host_out = nullptr;
-        release(h);
-        return RIFT_ENOMEM;
-    }
-    for (auto &row : h->ev)
-        for (auto &e : row)
-            if (cudaEventCreate(&e) != cudaSuccess) {
-                cudaGetLastError();
-                release(h);
-                return RIFT_ECUDA;
-            }
-    h->events_made = true;
+    h->host_out.assign(8 + 8 * (RIFT_MAX_ITER + 1) + 8, 0.0);
 
     // time-bin split table: j * beta = bin_i + bin_f
     std::vector<int> bi(cfg->n_t);
@@ -574,6 +590,24 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
 void rift_ile_destroy(rift_ile_t *h) { release(h); }
 
 int64_t rift_ile_kernel_launches(const rift_ile_t *h) { return h ? h->launches : -1; }
+
+int64_t rift_ile_footprint(const rift_ile_config *cfg)
+{
+    if (validate(cfg) != RIFT_OK)
+        return -1;
+    const int64_t K = cfg->n_det, M = cfg->n_modes, N = cfg->max_samples, B = cfg->n_bins, nt = cfg->n_t;
+    const int64_t nq = cfg->n_q, nq_pad = ((nq + 3) & ~3) + kQPad;
+    const int64_t groups = (nq + 7) / 8 + 17, kp = (2 * M + 15) / 16 * 16;
+    const int64_t sizes[] = {
+        K * M * nq * 16, 2 * K * M * M * 16, K * 2 * M * nq_pad * 4, 2 * K * M * M * 8, 2 * nt * 4,
+        N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, ((int64_t)kMaxCells + 1 + 256) * 4, 16, 16,
+        K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 6 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
+        N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16};
+    int64_t total = 0;
+    for (int64_t b : sizes)
+        total += b + 16;
+    return total + 64 * 1024;   // event and stream bookkeeping slack
+}
 
 int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const void *V, int mem)
 {
@@ -643,7 +677,7 @@ int rift_ile_eval(rift_ile_t *h, const double *theta, int64_t n, int mem, double
     if (lnL_t && mem == RIFT_MEM_HOST) {
         chunk = std::min<int64_t>(chunk, std::max<int64_t>(1, (int64_t)(64 << 20) / nt));
         void *q = nullptr;
-        if (cudaMalloc(&q, sizeof(double) * (size_t)chunk * nt) != cudaSuccess) {
+        if (cudaMallocAsync(&q, sizeof(double) * (size_t)chunk * nt, h->stream) != cudaSuccess) {
             cudaGetLastError();
             return RIFT_ENOMEM;
         }
@@ -672,9 +706,9 @@ int rift_ile_eval(rift_ile_t *h, const double *theta, int64_t n, int mem, double
             rc = eval_device(h, th, c, o, ot, nullptr, nullptr);
         }
     }
-    int rc2 = sync_and_err(h);
     if (stage_t)
-        cudaFree(stage_t);
+        cudaFreeAsync(stage_t, h->stream);
+    int rc2 = sync_and_err(h);
     return rc != RIFT_OK ? rc : rc2;
 }
 
@@ -698,7 +732,7 @@ int rift_ile_coeffs(rift_ile_t *h, const double *theta, int64_t n, int mem, doub
     std::vector<void *> tmp;
     auto grab = [&](size_t bytes) -> void * {
         void *q = nullptr;
-        if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -720,9 +754,9 @@ int rift_ile_coeffs(rift_ile_t *h, const double *theta, int64_t n, int mem, doub
             (quad && cudaMemcpyAsync(quad + i0, dq, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream)))
             rc = RIFT_ECUDA;
     }
-    cudaStreamSynchronize(h->stream);
     for (void *q : tmp)
-        cudaFree(q);
+        cudaFreeAsync(q, h->stream);
+    cudaStreamSynchronize(h->stream);
     h->last_n = 0;
     cudaGetLastError();
     return rc;

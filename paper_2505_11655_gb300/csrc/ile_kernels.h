@@ -2,11 +2,43 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "ile_common.cuh"
 
 namespace rift {
+
+// Raise a kernel's dynamic shared-memory limit to everything the device allows (less
+// its static shared memory), once per kernel and device: every caller sets the same
+// value, so concurrent launches from several host threads and streams never race on
+// it, and the (slow) attribute calls stay off the launch path.
+template <typename Kernel> inline cudaError_t allow_max_dynamic_smem(Kernel kern)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const std::pair<const void *, int> key((const void *)kern, dev);
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(key))
+        return cudaSuccess;
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        done.insert(key);
+    return e;
+}
 
 // Per-bin split of j * beta (beta = bin spacing x fs): j*beta = bin_i[j] + bin_f[j], 0 <= bin_f < 1.
 struct BinTable {

@@ -205,7 +205,7 @@ cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t 
     const int wpb = kRefThreads / 32;
     const size_t smem = sizeof(double) * ((size_t)wpb * 2 * (P.K * P.M + P.K + P.M) + (size_t)wpb * P.n_t);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(refine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(refine_kernel);
         if (e != cudaSuccess)
             return e;
     }

@@ -111,7 +111,7 @@ cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, in
         return cudaSuccess;
     size_t smem = sizeof(double) * (6 * (S.B + 1) + 12 * S.B);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(draw_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(draw_kernel);
         if (e != cudaSuccess)
             return e;
     }
@@ -523,7 +523,7 @@ cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double
         nb = 1;
     size_t smem = sizeof(double) * 6 * S.B;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(hist_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(hist_partial_kernel);
         if (e != cudaSuccess)
             return e;
     }

@@ -484,7 +484,7 @@ cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, 
     if (smem > (size_t)max_smem)
         return cudaErrorInvalidConfiguration;
     auto kern = dbuf ? lnl_tile_kernel<true> : lnl_tile_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess)
         return e;
     e = cudaMemsetAsync(tile_counter, 0, sizeof(int), st);

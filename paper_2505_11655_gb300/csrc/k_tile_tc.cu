@@ -665,7 +665,7 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     if (!lnl_tc_fits(P, max_smem))
         return cudaErrorInvalidConfiguration;
     const size_t smem = tc_layout(P.K, P.M, P.n_t).end;
-    cudaError_t e = cudaFuncSetAttribute(lnl_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dynamic_smem(lnl_tc_kernel);
     if (e != cudaSuccess)
         return e;
     e = cudaMemsetAsync(tile_counter, 0, sizeof(int), st);

@@ -22,12 +22,12 @@ def lib():
 
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "rift_ile.h")).read()
-    return sorted(set(re.findall(r"\b(rift_ile_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rift_(?:ile|srv)_[a-z_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_symbols()
-    assert len(names) >= 12
+    assert len(names) >= 19
     L = C.CDLL(lib._LIB_PATH)
     for n in names:
         assert hasattr(L, n), n
@@ -85,6 +85,27 @@ def test_window_violation_is_erange(lib):
     assert _create_rc(lib, cfg) == lib.RIFT_ERANGE
     cfg, keep = _cfg(lib, prob, t_hi_s=0.08)
     assert _create_rc(lib, cfg) == lib.RIFT_ERANGE
+
+
+def test_footprint_is_host_only_and_grows_with_samples(lib):
+    """rift_ile_footprint validates and sizes a configuration without any CUDA call."""
+    prob = S.single_large_problem()
+    cfg, keep = _cfg(lib, prob, max_samples=1000)
+    small = lib.rift_ile_footprint(cfg)
+    cfg2, keep2 = _cfg(lib, prob, max_samples=1_000_000)
+    big = lib.rift_ile_footprint(cfg2)
+    assert 0 < small < big
+    assert big - small >= 88 * (1_000_000 - 1000)   # per-sample buffers
+    bad, keep3 = _cfg(lib, prob, n_det=0)
+    assert lib.rift_ile_footprint(bad) == -1
+
+
+def test_server_rejects_bad_config(lib):
+    L = lib.load()
+    h = C.c_void_p()
+    for budget, slots in ((0, 4), (1 << 30, 0), (1 << 30, 65)):
+        cfg = lib.rift_srv_config(budget, slots)
+        assert L.rift_srv_create(C.byref(cfg), C.byref(h)) == lib.RIFT_EINVAL
 
 
 def test_valid_config_without_gpu_is_ecuda(lib):

@@ -1,0 +1,85 @@
+"""Serving loop (rift_srv_*): continuous admission by device footprint, solves in
+flight overlapping on separate streams, and each result independent of the mix."""
+import numpy as np
+import pytest
+
+import ile_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2505_11655_gb300 as G
+    G.load(build_if_missing=True)
+    return G
+
+
+def requests():
+    """Uneven solves: detector counts 1-3, mode counts 2-21, 4096 / 16384 Hz."""
+    out = []
+    for i, (dets, M, fs, nt, n) in enumerate([
+            (("H1", "L1"), 2, 4096.0, 401, 6000), (("H1",), 3, 4096.0, 401, 4000),
+            (("H1", "L1", "V1"), 21, 16384.0, 1001, 9000), (("L1", "V1"), 9, 16384.0, 401, 5000),
+            (("H1", "L1", "V1"), 4, 4096.0, 1001, 7000), (("H1", "V1"), 15, 4096.0, 1001, 3000)]):
+        p = S.make_problem(dets, M, fs, n_t=nt, snr=12.0 + 3 * i, seed=S.config_seed(5, i))
+        out.append((i, p, n))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_result_same_alone_and_in_mix(G, precision):
+    prec = G.RIFT_FP64 if precision == "fp64" else G.RIFT_FP32
+    reqs = requests()
+    alone = {}
+    with G.Server(hbm_budget_bytes=8 << 30, max_slots=1) as srv:
+        for tag, p, n in reqs:
+            srv.submit(p, 2, n, tag, precision=prec, seed=100 + tag)
+            (c,) = srv.drain(1)
+            assert c["status"] == 0
+            alone[tag] = c
+    with G.Server(hbm_budget_bytes=8 << 30, max_slots=4) as srv:
+        # the requests of interest interleaved with filler solves
+        filler = S.plain_fp64_problem()
+        k = 0
+        for tag, p, n in reqs:
+            srv.submit(filler, 1, 20000, 1000 + k, precision=prec, seed=7 + k)
+            srv.submit(p, 2, n, tag, precision=prec, seed=100 + tag)
+            k += 1
+        got = {c["tag"]: c for c in srv.drain(2 * len(reqs))}
+    for tag, _, _ in reqs:
+        a, b = alone[tag], got[tag]
+        assert b["status"] == 0
+        tol = 1e-12 if precision == "fp64" else 1e-5
+        assert abs(a["lnZ"] - b["lnZ"]) <= tol * max(1.0, abs(a["lnZ"]))
+        assert abs(a["n_eff"] - b["n_eff"]) <= 1e-6 * a["n_eff"] + tol
+        assert a["n_total"] == b["n_total"]
+    # solves were in flight together
+    t = sorted((c["t_admit_ms"], c["t_done_ms"]) for c in got.values())
+    assert any(t[i + 1][0] < t[i][1] for i in range(len(t) - 1))
+
+
+def test_admission_respects_budget(G):
+    """With room for one large solve at a time, large solves never overlap."""
+    p = S.single_large_problem()
+    cfg, keep = G.make_config(p, G.RIFT_FP32, max_samples=200000)
+    fp = G.rift_ile_footprint(cfg)
+    with G.Server(hbm_budget_bytes=int(fp * 1.5), max_slots=4) as srv:
+        for tag in range(4):
+            srv.submit(p, 1, 200000, tag, seed=tag + 1)
+        got = sorted(srv.drain(4), key=lambda c: c["t_admit_ms"])
+    assert [c["status"] for c in got] == [0] * 4
+    for a, b in zip(got, got[1:]):
+        assert b["t_admit_ms"] >= a["t_done_ms"] - 1e-3
+
+
+def test_oversize_request_refused(G):
+    p = S.single_large_problem()
+    with G.Server(hbm_budget_bytes=64 << 20, max_slots=2) as srv:
+        with pytest.raises(G.RiftError) as e:
+            srv.submit(p, 1, 1_000_000, 0)
+        assert e.value.code == G.RIFT_ENOMEM
+        assert srv.pending() == (0, 0)
