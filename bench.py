@@ -16,6 +16,16 @@ Under torchrun every rank runs its own independent solve (its own intrinsic
 point); value = samples of all ranks / the slowest rank's time ("weak").
 `--impl reference` times the FP64 CPU oracle (the reference arm of this
 project) on bounded samples of the same workload.
+
+Other workloads (one JSON line each, same keys):
+  --workload batched   512 uneven solves (1-3 detectors, 2-21 modes, 1e4-1e6
+                       samples, 3 adaptive iterations each) as one CUDA graph;
+                       solves/s against sequential FP32 and FP64 solves
+  --workload high_snr  SNR-150 realisable injection, q=20-like mode hierarchy:
+                       10 adaptive iterations x 1e6 samples in RIFT_MIXED, n_eff
+                       per iteration, error of FP32 and MIXED against the FP64 path
+  --workload serving   Poisson stream of solves of four sizes through rift_srv_*:
+                       p50/p99 latency and solves/s against sequential FP64
 """
 from __future__ import annotations
 
@@ -159,8 +169,65 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+def run_reference_other(args):
+    """Reference arm of the batched / high-SNR / serving workloads: the FP64 oracle
+    timed on bounded samples of each representative problem (one draw + lnL +
+    reduce + adapt pass), converted to the workload's unit by the samples each
+    solve evaluates."""
+    import oracle
+    oracle.build()
+    if args.workload == "high_snr":
+        items = [(S.high_snr_problem(snr=args.snr), 10, args.samples)]
+        unit, metric = "sample-evals/s", "ILE lnL sample-evals/s (high-SNR adaptive, MIXED)"
+    elif args.workload == "batched":
+        items = [(p, 3, -(-n // 3)) for p, n in (S.batched_problem(i) for i in range(0, args.points, 64))]
+        unit, metric = "solves/s", "ILE solves/s (batched uneven solves)"
+    else:
+        import paper_2505_11655_gb300 as G
+        items = [(p, it, n) for _, p, it, n in serving_requests(G, 16)]
+        unit, metric = "solves/s", "ILE serving solves/s (p50/p99 latency)"
+    per_step = 100.0 / max(1, args.steps + args.warmup) / len(items)
+    secs, samples, times = [], 0, []
+    for g in range(args.warmup + args.steps):
+        t_step, est = 0.0, []
+        for j, (p, it, n) in enumerate(items):
+            P = oracle.Problem(p)
+            sm = oracle.Sampler(n_bins=64, seed=1 + j)
+            m = 64
+            t0 = time.perf_counter()
+            th, lr, bins = sm.draw(m, it=g)
+            ll = oracle.lnL(P, th)
+            dt0 = time.perf_counter() - t0
+            m = int(max(64, min(n, m * per_step / max(dt0, 1e-6))))
+            t0 = time.perf_counter()
+            th, lr, bins = sm.draw(m, it=g)
+            ll = oracle.lnL(P, th)
+            oracle.reduce(ll + lr)
+            sm.adapt(bins, ll + lr)
+            dt = time.perf_counter() - t0
+            t_step += dt
+            est.append(dt / m * it * n)   # seconds this solve would take
+            samples = m
+        if g >= args.warmup:
+            times.append(t_step)
+            secs.append(float(np.mean(est)))
+    value = (args.samples * 10 / np.mean(secs)) if unit == "sample-evals/s" else 1.0 / np.mean(secs)
+    cores = oracle.num_threads()
+    sample = (f"{len(items)} representative problems, about {samples} samples each per step, "
+              "scaled to each solve's sample count")
+    emit({"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": args.workload, "reference": "FP64 CPU oracle (oracle/ile_oracle.c), OpenMP"},
+          "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+          "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
 def run_reference(args, rank):
     if rank != 0:
+        return
+    if args.workload != "single_large":
+        run_reference_other(args)
         return
     prob = S.single_large_problem(point=0)
     import oracle
@@ -271,14 +338,16 @@ def run_ours(args, rank, world, local_rank):
     lnl_avg = statistics.mean(lnl_ms)
     achieved = fps * n / (lnl_avg / 1e3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = profile_traffic()
+    plan = ile.plan()
+    kernel = _lnl_kernel_name(G, plan)
+    traffic = profile_traffic() if plan[0] == G.RIFT_KERNEL_TENSOR else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(prob, n),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "lnl_tc_kernel", "kernel_ms": lnl_avg,
+                     "kernel": kernel, "samples_per_cell": plan[1], "kernel_ms": lnl_avg,
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
                      "flops_per_sample": fps},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -292,6 +361,348 @@ def run_ours(args, rank, world, local_rank):
         emit(out)
 
 
+# ======================================================================== other workloads
+
+def _setup(local_rank):
+    import torch
+
+    import paper_2505_11655_gb300 as G
+    torch.cuda.set_device(local_rank)
+    G.load(build_if_missing=True)
+    return torch, G
+
+
+def _lnl_kernel_name(G, plan):
+    return {G.RIFT_KERNEL_TENSOR: "lnl_tc_kernel", G.RIFT_KERNEL_CUDA_CORE: "lnl_tile_kernel",
+            G.RIFT_KERNEL_FP64: "lnl_fp64_kernel"}[plan[0]]
+
+
+def _max_over_ranks(torch, world, x):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _clock_monitor(torch, local_rank):
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+        gpu_id = uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"
+    except Exception:
+        gpu_id = None
+    return Clocks(gpu_id)
+
+
+def run_batched(args, rank, world, local_rank):
+    """512 uneven solves as one graph per step; solves/s."""
+    torch, G = _setup(local_rank)
+    npts = args.points
+    pts = [S.batched_problem(i + rank * npts) for i in range(npts)]
+    n_iter = 3
+    nper = [max(1, -(-n // n_iter)) for _, n in pts]
+    solves = [G.ILE(p, precision=G.RIFT_FP32, max_samples=m, n_bins=64, seed=1 + i)
+              for i, ((p, _), m) in enumerate(zip(pts, nper))]
+    stream = torch.cuda.Stream()
+    batch = G.Batch(solves, [n_iter] * npts, nper, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    samples = n_iter * sum(nper)
+    flops = sum(flops_per_sample(p) * n_iter * m for (p, _), m in zip(pts, nper))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        res, rc = batch.run()
+        assert rc == 0, rc
+    barrier()
+    clk = _clock_monitor(torch, local_rank)
+    clk.start()
+    step_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, rc = batch.run()
+        e1.record(stream)
+        e1.synchronize()
+        assert rc == 0, rc
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    clocks = clk.stop()
+    total = _max_over_ranks(torch, world, sum(step_ms))
+    value = npts * args.steps * world / (total / 1e3)
+    launches = batch.kernel_launches() * args.steps
+
+    # end to end: every point's Q, U, V uploaded from pinned host memory, then the run
+    pinned = [{k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), np.complex128)).pin_memory().numpy()
+               for k in ("Q", "U", "V")} for p, _ in pts]
+    h2d = sum(a.nbytes for d in pinned for a in d.values())
+    e2e_t = []
+    for _ in range(0 if args.quick else min(args.steps, 3)):
+        barrier()
+        t0 = time.perf_counter()
+        for sv, d in zip(solves, pinned):
+            sv.set_overlaps(d["Q"], d["U"], d["V"])
+        batch.run()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = _max_over_ranks(torch, world, sum(e2e_t)) if e2e_t else None
+    e2e_value = npts * len(e2e_t) * world / e2e_total if e2e_t else None
+    kinds = {}
+    for sv in solves:
+        k = _lnl_kernel_name(G, sv.plan())
+        kinds[k] = kinds.get(k, 0) + 1
+    batch.close()
+
+    # baselines, one solve at a time through rift_ile_adapt: FP32 for every point,
+    # the plain FP64 path on every 16th point (scaled by algorithmic work)
+    seq = {}
+    if not args.quick:
+        t0 = time.perf_counter()
+        for sv, m in zip(solves, nper):
+            sv.adapt(n_iter, m)
+        seq["fp32_s"] = time.perf_counter() - t0
+        sub = list(range(0, npts, 16))
+        t64 = 0.0
+        for i in sub:
+            p, _ = pts[i]
+            with G.ILE(p, precision=G.RIFT_FP64, max_samples=nper[i], n_bins=64, seed=1 + i) as s64:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s64.adapt(n_iter, nper[i])
+                t64 += time.perf_counter() - t0
+        w_sub = sum(flops_per_sample(pts[i][0]) * nper[i] for i in sub)
+        w_all = sum(flops_per_sample(p) * m for (p, _), m in zip(pts, nper))
+        seq["fp64_s"] = t64 * w_all / w_sub
+        seq["fp64_sample"] = f"{len(sub)} of {npts} points timed, scaled by algorithmic work ({w_all / w_sub:.1f}x)"
+    for sv in solves:
+        sv.close()
+    achieved = flops / (total / args.steps / 1e3) / 1e12 / world
+    peak = fp32_peak_tflops()
+    out = {
+        "metric": "ILE solves/s (batched uneven solves)", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched uneven solves: {npts} points per GPU, detectors 1-3, modes 2-21, "
+                               "samples 1e4-1e6 log-uniform, 3 adaptive iterations of N/3, one CUDA graph per step",
+                   "points": npts, "samples_per_step": samples, "n_iter": n_iter,
+                   "lnl_kernels": kinds, "l2": "flushed between timed steps (256 MiB write)"},
+        "sample_evals_per_s": samples * args.steps * world / (total / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole step (all kernels of all solves)",
+                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+                     "note": "algorithmic FP32 flops of every sample evaluation / whole step time"},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": npts * 8 * (7 + 8 * n_iter)},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    if seq:
+        out["sequential"] = {
+            "fp32_solves_per_s": npts / seq["fp32_s"], "fp64_solves_per_s": npts / seq["fp64_s"],
+            "speedup_vs_fp32_sequential": value / world / (npts / seq["fp32_s"]),
+            "speedup_vs_fp64_sequential": value / world / (npts / seq["fp64_s"]),
+            "fp64_sample": seq["fp64_sample"]}
+    if rank == 0:
+        emit(out)
+
+
+def realisable_high_snr(G, snr=150.0, point=0):
+    """SNR-`snr` injection built from this library's own float64 coefficients
+    F_k Y_lm at a fixed near-edge-on truth, so that the sampler can converge on it."""
+    th_true = np.array([2.2, -0.5, 1.1, 0.7, 1.4, 300.0])
+    probe = S.high_snr_problem(snr=snr, point=point)
+    with G.ILE(probe, precision=G.RIFT_FP64, max_samples=16) as s:
+        c, dt, _ = s.coeffs(th_true[None, :])
+    a0 = c[0] * th_true[5] / probe.d_ref
+    return S.high_snr_problem(snr=snr, point=point, a0=a0, dt_true=dt[0]), th_true
+
+
+def run_high_snr(args, rank, world, local_rank):
+    """10 adaptive iterations x 1e6 samples in RIFT_MIXED per step."""
+    torch, G = _setup(local_rank)
+    n, n_iter = args.samples, 10
+    prob, th_true = realisable_high_snr(G, snr=args.snr, point=rank)
+    stream = torch.cuda.Stream()
+    ile = G.ILE(prob, precision=G.RIFT_MIXED, max_samples=n, n_bins=64, seed=1 + rank, stream=stream)
+    for _ in range(args.warmup):
+        ile.adapt(n_iter, n)
+    torch.cuda.synchronize()
+    clk = _clock_monitor(torch, local_rank)
+    clk.start()
+    step_ms, res = [], []
+    l0 = ile.kernel_launches()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ile.adapt(n_iter, n)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        res.append(r)
+    launches = ile.kernel_launches() - l0
+    clocks = clk.stop()
+    total = _max_over_ranks(torch, world, sum(step_ms))
+    value = n * n_iter * args.steps * world / (total / 1e3)
+    r = res[-1]
+    # error of the last batch against the float64 path (1e-9 parity with the oracle):
+    # every sample within 30 of the largest ln w, plus 4096 others
+    th, lr, ll, lw = ile.last_batch(n)
+    heavy = np.nonzero(lw >= lw.max() - 30.0)[0]
+    rest = np.random.default_rng(5).choice(n, 4096, replace=False)
+    idx = np.unique(np.concatenate([heavy, rest]))
+    with G.ILE(prob, precision=G.RIFT_FP64, max_samples=len(idx)) as s64:
+        l64 = s64.eval(th[idx])
+    with G.ILE(prob, precision=G.RIFT_FP32, max_samples=len(idx)) as s32:
+        l32 = s32.eval(th[idx])
+
+    def lse(x):
+        m = x.max()
+        return m + math.log(np.exp(x - m).sum())
+
+    def lnz_with(vals):
+        lnw = ll + lr
+        lnw = lnw.copy()
+        lnw[idx] = vals + lr[idx]
+        return lse(lnw) - math.log(n)
+
+    ref = lnz_with(l64)
+    err = {"mixed": {"max_abs_dlnL_heavy": float(np.max(np.abs(ll[idx] - l64)[np.isin(idx, heavy)])),
+                     "abs_dlnZ_last_iter": abs(lnz_with(ll[idx]) - ref)},
+           "fp32": {"max_abs_dlnL_heavy": float(np.max(np.abs(l32 - l64)[np.isin(idx, heavy)])),
+                    "abs_dlnZ_last_iter": abs(lnz_with(l32) - ref)},
+           "reference": "float64 GPU path on the same theta (parity 1e-9 with the FP64 oracle)",
+           "samples_compared": int(len(idx)), "heavy_samples": int(len(heavy))}
+    ile.close()
+    out = {
+        "metric": "ILE lnL sample-evals/s (high-SNR adaptive, MIXED)", "value": value, "unit": "sample-evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"high-SNR narrow source: SNR {args.snr:g}, realisable injection (iota 1.4 rad), "
+                               "q=20-like hierarchy, 3 detectors, 21 modes, 16384 Hz, 1001 bins, "
+                               f"{n_iter} adaptive iterations x {n} samples per step, RIFT_MIXED",
+                   "n_iter": n_iter, "samples_per_iter": n, "l2": "inputs (theta 48 MB/iter) exceed L2"},
+        "result": {"lnZ": r["lnZ"], "sigma_lnZ": r["sigma_lnZ"], "n_eff": r["n_eff"], "n_ess": r["n_ess"],
+                   "lnL_max": r["lnL_max"], "n_eff_iter": r["n_eff_iter"], "lnZ_iter": r["lnZ_iter"]},
+        "error_vs_fp64": err,
+        "stage_ms_per_step": {"draw_sort": r["time_ms"][0], "lnl_refine": r["time_ms"][1],
+                              "reduce_adapt": r["time_ms"][2]},
+        "e2e": None, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0:
+        emit(out)
+
+
+def serving_requests(G, count, seed=17):
+    """Request mixture: 40% plain (2 det, 2 modes, 1e4 samples, 1 iteration), 30%
+    batched-workload points (3 iterations of N/3), 20% single large (1e6, 1
+    iteration), 10% high-SNR (2 iterations x 1e6).  Problems come from a pool of
+    distinct seeded points; each request has its own sampler seed."""
+    pool = {"plain": [S.plain_fp64_problem(i) for i in range(8)],
+            "batched": [S.batched_problem(100 + i) for i in range(32)],
+            "large": [S.single_large_problem(i) for i in range(2)],
+            "high_snr": [S.high_snr_problem(snr=120.0, point=i) for i in range(2)]}
+    rng = np.random.default_rng(seed)
+    kinds = rng.choice(["plain", "batched", "large", "high_snr"], size=count, p=[0.4, 0.3, 0.2, 0.1])
+    reqs = []
+    for i, k in enumerate(kinds):
+        j = int(rng.integers(len(pool[k])))
+        if k == "plain":
+            reqs.append((k, pool[k][j], 1, 10000))
+        elif k == "batched":
+            p, n = pool[k][j]
+            reqs.append((k, p, 3, max(1, -(-n // 3))))
+        elif k == "large":
+            reqs.append((k, pool[k][j], 1, 1_000_000))
+        else:
+            reqs.append((k, pool[k][j], 2, 1_000_000))
+    return reqs
+
+
+def _serve(G, reqs, rate, budget, slots):
+    """Submit `reqs` (all at once if rate is None, else Poisson arrivals at `rate`
+    per second); completions with their server-side times."""
+    rng = np.random.default_rng(3)
+    with G.Server(hbm_budget_bytes=budget, max_slots=slots) as srv:
+        t0 = time.perf_counter()
+        t_next = 0.0
+        got = []
+        for i, (k, p, it, n) in enumerate(reqs):
+            if rate is not None:
+                t_next += rng.exponential(1.0 / rate)
+                while True:
+                    dt = t0 + t_next - time.perf_counter()
+                    if dt <= 0:
+                        break
+                    got += srv.poll(256, 0)
+                    time.sleep(min(dt, 0.002))
+            srv.submit(p, it, n, i, precision=G.RIFT_MIXED, seed=1 + i)
+        got += srv.drain(len(reqs) - len(got))
+    return got
+
+
+def _latency_stats(got):
+    lat = np.array([c["t_done_ms"] - c["t_submit_ms"] for c in got])
+    span = (max(c["t_done_ms"] for c in got) - min(c["t_submit_ms"] for c in got)) / 1e3
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "solves_per_s": len(got) / span, "span_s": span,
+            "failed": int(sum(c["status"] != 0 for c in got))}
+
+
+def run_serving(args, rank, world, local_rank):
+    torch, G = _setup(local_rank)
+    reqs = serving_requests(G, args.requests, seed=17 + rank)
+    budget, slots = 96 << 30, 16
+    _serve(G, reqs[:64], None, budget, slots)   # warm-up: kernels, tuner classes, pool
+    clk = _clock_monitor(torch, local_rank)
+    clk.start()
+    sat = _latency_stats(_serve(G, reqs, None, budget, slots))
+    lam = sat["solves_per_s"]
+    at08 = _latency_stats(_serve(G, reqs, 0.8 * lam, budget, slots))
+    at12 = None if args.quick else _latency_stats(_serve(G, reqs, 1.2 * lam, budget, slots))
+    clocks = clk.stop()
+    # one solve at a time through the public API (create, upload, adapt, read back):
+    # the plain FP64 path and the unbatched FP32 path on the first requests
+    seq = {}
+    m = min(len(reqs), 40 if not args.quick else 8)
+    for name, prec in (("fp64", G.RIFT_FP64), ("fp32", G.RIFT_FP32)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, (k, p, it, n) in enumerate(reqs[:m]):
+            with G.ILE(p, precision=prec, max_samples=n, n_bins=64, seed=1 + i) as s:
+                s.adapt(it, n)
+        seq[name] = m / (time.perf_counter() - t0)
+    total_solves = _max_over_ranks(torch, world, sat["span_s"])
+    value = len(reqs) * world / total_solves
+    mix = {k: int(sum(r[0] == k for r in reqs)) for k in ("plain", "batched", "large", "high_snr")}
+    out = {
+        "metric": "ILE serving solves/s (p50/p99 latency)", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": len(reqs), "warmup": 64, "ms_per_step": 1e3 * sat["span_s"] / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"serving stream: {len(reqs)} requests (40% plain 2-det/2-mode 1e4 samples, 30% "
+                               "batched-workload points with 3 iterations, 20% single large 1e6, 10% high-SNR "
+                               "2 x 1e6), RIFT_MIXED, admission by HBM footprint",
+                   "requests": mix, "hbm_budget_bytes": budget, "max_slots": slots,
+                   "problem_pool": "8 plain + 32 batched + 2 large + 2 high-SNR points, per-request seeds"},
+        "saturated": sat, "poisson_0.8x": at08, "poisson_1.2x": at12,
+        "sequential": {"fp64_solves_per_s": seq["fp64"], "fp32_solves_per_s": seq["fp32"],
+                       "sample": f"first {m} requests of the stream, one at a time",
+                       "speedup_vs_fp64_sequential": sat["solves_per_s"] / seq["fp64"],
+                       "speedup_vs_fp32_sequential": sat["solves_per_s"] / seq["fp32"]},
+        "e2e": {"value": value, "unit": "solves/s", "note": "requests carry host Q/U/V; the serving loop uploads "
+                "them and reads each result back (latency = submit to result)"},
+        "gpu_launches": None, "clocks": clocks,
+    }
+    if rank == 0:
+        emit(out)
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +712,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--samples", type=int, default=N_SAMPLES, help="samples per step (profiling cases only)")
     ap.add_argument("--quick", action="store_true", help="skip the end-to-end and CPU-baseline legs (profiling)")
+    ap.add_argument("--workload", default="single_large", choices=["single_large", "batched", "high_snr", "serving"])
+    ap.add_argument("--points", type=int, default=512, help="points of the batched workload")
+    ap.add_argument("--requests", type=int, default=2000, help="requests of the serving workload")
+    ap.add_argument("--snr", type=float, default=150.0, help="SNR of the high-SNR workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -313,8 +728,10 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
+    run = {"single_large": run_ours, "batched": run_batched, "high_snr": run_high_snr,
+           "serving": run_serving}[args.workload]
     try:
-        run_ours(args, rank, world, local_rank)
+        run(args, rank, world, local_rank)
     finally:
         if world > 1:
             import torch.distributed as dist

@@ -167,8 +167,24 @@ int rift_ile_coeffs(rift_ile_t *h, const double *theta, int64_t n, int mem, doub
 int rift_ile_marginalize(rift_ile_t *h, int64_t n_samples, rift_ile_result *out);
 
 /* n_iter iterations of draw -> evaluate -> reduce -> adapt, all on the device;
- * results pooled over the iterations (see rift_ile_result). 1 <= n_iter <= RIFT_MAX_ITER. */
+ * results pooled over the iterations (see rift_ile_result). 1 <= n_iter <= RIFT_MAX_ITER.
+ * When a call repeats the previous call's (n_iter, n_per_iter), the whole sequence is
+ * captured once as a CUDA graph and replayed by later calls of that shape (same
+ * kernels and arguments; the sampler's iteration counter lives in device memory).
+ * RIFT_ILE_GRAPHS=0 in the environment turns the capture off. */
 int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_result *out);
+
+/* Launch plan of the float32 likelihood stage for the most recent batch:
+ * *lnl_kernel = RIFT_KERNEL_FP64 (RIFT_FP64 mode), RIFT_KERNEL_CUDA_CORE (64-sample
+ * CUDA-core tiles) or RIFT_KERNEL_TENSOR (128-sample tcgen05 tiles);
+ * *samples_per_cell = fill of the Hilbert sky-sort grid.  The plan is picked per
+ * problem class by the autotuner (timed candidates on the first batch of a class;
+ * RIFT_ILE_TUNE=0 disables the timing, RIFT_ILE_TUNE_CACHE=<file> persists the
+ * choices) unless RIFT_ILE_TC=0/1 forces the kernel.  Either output may be NULL. */
+#define RIFT_KERNEL_FP64 0
+#define RIFT_KERNEL_CUDA_CORE 1
+#define RIFT_KERNEL_TENSOR 2
+int rift_ile_get_plan(const rift_ile_t *h, int32_t *lnl_kernel, int32_t *samples_per_cell);
 
 /* Samples of the most recent batch (in draw order): theta [n][6], ln p - ln p_s [n],
  * time-marginalised ln L [n], ln w [n]; any output may be NULL; *n_out receives
@@ -223,6 +239,31 @@ int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, dou
 
 void rift_ile_destroy(rift_ile_t *h);
 const char *rift_ile_strerror(int code);
+
+/* ---- batches of solves -------------------------------------------------------------------
+ * Many independent solves (handles with their overlaps set) run as one CUDA graph: each
+ * solve's whole adaptive sequence (rift_ile_adapt with its own n_iter and n_per_iter) is
+ * a branch with no dependence on the others, so uneven solves share the GPU at once and
+ * one graph launch replaces thousands of kernel launches.  The graph is captured on the
+ * first run and replayed by later runs; each run continues every solve's adaptive
+ * sequence exactly as a rift_ile_adapt call on that handle would (same draws, same
+ * results).  The handles must stay alive, and must not be used by other calls while a
+ * run is in progress; a handle belongs to at most one batch at a time. */
+typedef struct rift_batch rift_batch_t;
+
+/* solves [n] distinct handles (1 <= n <= 65536), n_iter [n], n_per_iter [n] as for
+ * rift_ile_adapt; cuda_stream: the stream runs are launched on (NULL: a stream of the
+ * batch's own).  RIFT_EINVAL for a bad argument, RIFT_ESTATE if a handle has no
+ * overlaps, RIFT_ECUDA if streams or buffers cannot be made. */
+int rift_batch_create(rift_ile_t *const *solves, int32_t n, const int32_t *n_iter, const int64_t *n_per_iter,
+                      void *cuda_stream, rift_batch_t **out);
+/* Run every solve once; out [n] receives each solve's result (status per solve in
+ * out[i].status; time_ms[3] of every result is the whole run's device time).  Returns
+ * RIFT_OK, or the first failing solve's status. */
+int rift_batch_run(rift_batch_t *b, rift_ile_result *out);
+/* Kernels one run launches (summed over the solves), or -1 before the first run. */
+int64_t rift_batch_kernel_launches(const rift_batch_t *b);
+void rift_batch_destroy(rift_batch_t *b);
 
 /* ---- serving ---------------------------------------------------------------------------
  * A request loop that accepts ILE solves (one intrinsic point each: its problem, Q/U/V and

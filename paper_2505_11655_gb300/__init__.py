@@ -26,11 +26,13 @@ RIFT_MEM_HOST, RIFT_MEM_DEVICE = 0, 1
 RIFT_QUAD_QUARTER, RIFT_QUAD_HALF = 0, 1
 RIFT_FP64, RIFT_FP32, RIFT_MIXED = 0, 1, 2
 RIFT_MAX_ITER = 64
+RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_destroy", "rift_ile_strerror", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
+            "rift_ile_get_plan", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
 
@@ -116,6 +118,13 @@ def load(build_if_missing: bool = False):
     L.rift_srv_pending.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.rift_srv_destroy.argtypes = [vp]
     L.rift_srv_destroy.restype = None
+    L.rift_ile_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
+    L.rift_batch_run.argtypes = [vp, C.POINTER(rift_ile_result)]
+    L.rift_batch_kernel_launches.argtypes = [vp]
+    L.rift_batch_kernel_launches.restype = C.c_int64
+    L.rift_batch_destroy.argtypes = [vp]
+    L.rift_batch_destroy.restype = None
     L.rift_ile_kernel_launches.argtypes = [vp]
     L.rift_ile_kernel_launches.restype = C.c_int64
     L.rift_ile_destroy.argtypes = [vp]
@@ -270,6 +279,40 @@ def rift_ile_kernel_launches(h):
     return int(load().rift_ile_kernel_launches(h))
 
 
+def rift_ile_get_plan(h):
+    k, c = C.c_int32(), C.c_int32()
+    _check(load().rift_ile_get_plan(h, C.byref(k), C.byref(c)), "rift_ile_get_plan")
+    return k.value, c.value
+
+
+def rift_batch_create(handles, n_iter, n_per_iter, stream=None):
+    n = len(handles)
+    hs = (C.c_void_p * n)(*handles)
+    it = (C.c_int32 * n)(*[int(x) for x in n_iter])
+    ns = (C.c_int64 * n)(*[int(x) for x in n_per_iter])
+    b = C.c_void_p()
+    st = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(load().rift_batch_create(hs, n, it, ns, st, C.byref(b)), "rift_batch_create")
+    return b
+
+
+def rift_batch_run(b, n):
+    out = (rift_ile_result * n)()
+    rc = load().rift_batch_run(b, out)
+    if rc not in (RIFT_OK, RIFT_ERANGE, RIFT_ENONFINITE, RIFT_ETIMEOUT):
+        raise RiftError(rc, "rift_batch_run")
+    return list(out), rc
+
+
+def rift_batch_kernel_launches(b):
+    return int(load().rift_batch_kernel_launches(b))
+
+
+def rift_batch_destroy(b):
+    if b:
+        load().rift_batch_destroy(b)
+
+
 def rift_ile_destroy(h):
     if h:
         load().rift_ile_destroy(h)
@@ -351,6 +394,41 @@ class Server:
         self.close()
 
 
+class Batch:
+    """Many solves as one CUDA graph (rift_batch_*): ``solves`` are ILE objects with
+    their overlaps set, each run continues every solve's adaptive sequence."""
+
+    def __init__(self, solves, n_iter, n_per_iter, stream=None):
+        self.solves = list(solves)   # keep the handles alive
+        self.h = rift_batch_create([s.h for s in self.solves], n_iter, n_per_iter, stream)
+
+    def run(self):
+        """Results (dicts, one per solve, each with its own status) and the first
+        failing status (0 if none)."""
+        res, rc = rift_batch_run(self.h, len(self.solves))
+        return [r.as_dict() for r in res], rc
+
+    def kernel_launches(self):
+        return rift_batch_kernel_launches(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            rift_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
 class ILE:
     """One handle for one intrinsic point.  ``prob`` carries the problem's host
     arrays (the attributes of ``ile_synth.Problem``)."""
@@ -414,6 +492,10 @@ class ILE:
 
     def kernel_launches(self):
         return rift_ile_kernel_launches(self.h)
+
+    def plan(self):
+        """(likelihood kernel: RIFT_KERNEL_*, samples per sky cell) of the last batch."""
+        return rift_ile_get_plan(self.h)
 
     def sampler(self):
         return rift_ile_get_sampler(self.h, self.n_bins)

@@ -11,7 +11,7 @@
 #include <utility>
 #include <vector>
 
-#include "ile_kernels.h"
+#include "ile_handle.h"
 
 using namespace rift;
 
@@ -34,45 +34,9 @@ constexpr int kQPad = 256 + 16;
 
 }  // namespace
 
-struct rift_ile {
-    rift_ile_config cfg{};
-    std::vector<double> det_tensor, det_pos, q_t0;
-    std::vector<int32_t> lm;
-    cudaStream_t stream = nullptr;
-    Problem prob{};
-    bool have_overlaps = false;
-    int64_t cap = 0;           // samples per device batch
-    // overlaps
-    double2 *Q64 = nullptr, *U64 = nullptr, *V64 = nullptr;
-    float *Qr32 = nullptr;
-    float2 *U32 = nullptr, *V32 = nullptr;
-    int *bin_i = nullptr;
-    float *bin_f = nullptr;
-    // per-sample buffers
-    double *theta = nullptr, *lnpw = nullptr, *lnL = nullptr, *lnw = nullptr;
-    uint64_t *bins = nullptr;
-    uint32_t *key = nullptr, *perm = nullptr, *counts = nullptr;
-    int *tile_counter = nullptr;
-    __half *Qtc = nullptr;
-    unsigned int *qmax_bits = nullptr;
-    int tc_mode = 2;              // 0 never, 1 whenever it fits, 2 batches >= kTcMinBatch
-    bool tc_ok = false;
-    SkyGrid grid{0, 0};   // sky grid of the current batch size
-    // reductions and sampler
-    double *red_partial = nullptr, *hist_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
-    double *pooled_scratch = nullptr;
-    uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
-    double *P = nullptr, *C = nullptr, *Lg = nullptr;
-    int *err = nullptr;
-    std::vector<double> host_out;   // err word, pooled record, per-iteration records
-    uint32_t iteration = 0;
-    int64_t last_n = 0;
-    int64_t launches = 0;
-    std::vector<std::array<cudaEvent_t, 4>> ev;   // per-iteration stage timers, created on first use
-    std::vector<void *> allocs;
-};
 
-namespace {
+namespace rift {
+namespace host {
 
 // Device buffers come from the device's stream-ordered memory pool on the handle's
 // stream: no device-wide synchronisation, and freed blocks stay cached for the next
@@ -107,6 +71,8 @@ void release(rift_ile_t *h)
 {
     if (!h)
         return;
+    if (h->graph)
+        cudaGraphExecDestroy(h->graph);
     for (void *p : h->allocs)
         cudaFreeAsync(p, h->stream);
     h->allocs.clear();
@@ -114,6 +80,8 @@ void release(rift_ile_t *h)
     for (auto &row : h->ev)
         for (auto &e : row)
             cudaEventDestroy(e);
+    if (h->own_stream)
+        cudaStreamDestroy(h->stream);
     cudaGetLastError();
     delete h;
 }
@@ -175,23 +143,6 @@ int map_err(int flags)
     return RIFT_OK;
 }
 
-#define CK(call)                                                                                                        \
-    do {                                                                                                                \
-        cudaError_t e_ = (call);                                                                                        \
-        if (e_ != cudaSuccess) {                                                                                        \
-            if (std::getenv("RIFT_ILE_DEBUG"))                                                                          \
-                std::fprintf(stderr, "rift_ile: %s at %s:%d: %s\n", #call, __FILE__, __LINE__, cudaGetErrorString(e_)); \
-            cudaGetLastError();                                                                                         \
-            return RIFT_ECUDA;                                                                                          \
-        }                                                                                                               \
-    } while (0)
-
-#define RK(call)                 \
-    do {                         \
-        int r_ = (call);         \
-        if (r_ != RIFT_OK)       \
-            return r_;           \
-    } while (0)
 
 SamplerDev sampler_of(const rift_ile_t *h)
 {
@@ -296,15 +247,17 @@ int sync_and_err(rift_ile_t *h, int *flags_out = nullptr)
 
 bool use_fp32(const rift_ile_t *h) { return h->cfg.precision != RIFT_FP64; }
 
-// Tensor-core tiles pay off once a batch fills the sky densely enough that 128
-// samples share a 128-column Q window.
+// Without a tuned plan: tensor-core tiles pay off once a batch fills the sky densely
+// enough that 128 samples share a 128-column Q window.
 constexpr int64_t kTcMinBatch = 100000;
 
 bool use_tc(const rift_ile_t *h, int64_t n)
 {
     if (!h->tc_ok || h->tc_mode == 0)
         return false;
-    return h->tc_mode == 1 || n >= kTcMinBatch;
+    if (h->tc_mode == 1)
+        return true;
+    return h->plan.tc >= 0 ? h->plan.tc == 1 : n >= kTcMinBatch;
 }
 
 cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
@@ -337,8 +290,19 @@ int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmar
 // Sky grid sized for a batch of n samples.
 int grid_for_batch(rift_ile_t *h, int64_t n)
 {
-    h->grid = sky_grid_for(n);
+    h->grid = sky_grid_for(n, h->plan.per_cell);
     return RIFT_OK;
+}
+
+// Stage timer: inside a graph capture the record becomes an event node, so replays
+// time themselves.
+cudaError_t mark(rift_ile_t *h, int slot, int stage)
+{
+    if (!h->timed)
+        return cudaSuccess;
+    if (h->capturing)
+        return cudaEventRecordWithFlags(h->ev[slot][stage], h->stream, cudaEventRecordExternal);
+    return cudaEventRecord(h->ev[slot][stage], h->stream);
 }
 
 // ln L for n device-resident samples (theta [n][6]); perm/key scratch from the handle.
@@ -350,27 +314,30 @@ int eval_device(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg
         h->launches += 1;
         return RIFT_OK;
     }
-    h->launches += 7;   // keys, count, 3 scan passes, scatter, tiled likelihood
+    RK(choose_plan(h, n, false));
     RK(grid_for_batch(h, n));
+    int sorted = 0;
     CK(launch_keys(h->grid, theta, n, h->key, h->stream));
-    CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
+    CK(launch_sort(h->grid, h->key, n, h->sort_scratch, h->perm, h->stream, &sorted));
+    h->launches += 2 + sorted;   // keys, sort, tiled likelihood
     CK(launch_tiled(h, theta, n, lnL_tmarg, lnL_t, lnpw, lnw));
     if (h->cfg.precision == RIFT_MIXED)
         RK(refine_batch(h, theta, n, lnL_tmarg, lnpw, lnw));
     return RIFT_OK;
 }
 
-// One draw -> sort -> likelihood -> reduce (-> adapt) iteration into stats slot `slot`.
+// One draw -> sort -> likelihood -> reduce (-> adapt) iteration into stats slot `slot`;
+// the draw uses sampler iteration (device counter + slot).
 int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_pooled)
 {
     SamplerDev S = sampler_of(h);
     RK(grid_for_batch(h, n));
-    RK(ensure_events(h, slot + 1));
-    CK(cudaEventRecord(h->ev[slot][0], h->stream));
-    CK(launch_draw(S, h->grid, h->iteration, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    CK(mark(h, slot, 0));
+    CK(launch_draw(S, h->grid, h->iter_dev, (uint32_t)slot, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    int sorted = 0;
     if (use_fp32(h))
-        CK(launch_sort(h->grid, h->key, n, h->counts, h->perm, h->stream));
-    CK(cudaEventRecord(h->ev[slot][1], h->stream));
+        CK(launch_sort(h->grid, h->key, n, h->sort_scratch, h->perm, h->stream, &sorted));
+    CK(mark(h, slot, 1));
     if (!use_fp32(h)) {
         CK(launch_lnl_fp64(h->prob, h->theta, n, h->lnL, nullptr, h->lnpw, h->lnw, h->err, h->stream));
     } else {
@@ -378,22 +345,28 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
         if (h->cfg.precision == RIFT_MIXED)
             RK(refine_batch(h, h->theta, n, h->lnL, h->lnpw, h->lnw));
     }
-    CK(cudaEventRecord(h->ev[slot][2], h->stream));
+    CK(mark(h, slot, 2));
     CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, slot, h->pooled, reset_pooled ? 1 : 0, h->err,
                      h->stream));
     if (adapt)
         CK(launch_adapt(S, h->bins, h->lnw, n, h->stats, slot, h->hist_partial, h->stream));
-    CK(cudaEventRecord(h->ev[slot][3], h->stream));
-    h->launches += 1 + (use_fp32(h) ? 5 : 0) + 1 + 2 + (adapt ? 2 : 0);
-    h->iteration += 1;
-    h->last_n = n;
+    CK(mark(h, slot, 3));
+    h->launches += 1 + sorted + 1 + 2 + (adapt ? 2 : 0);
     return RIFT_OK;
 }
 
-int finish_result(rift_ile_t *h, int n_iter, rift_ile_result *out)
+int enqueue_adapt(rift_ile_t *h, int32_t n_iter, int64_t n)
 {
-    CK(launch_pooled_final(h->pooled, h->final_out, h->stream));
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    for (int g = 0; g < n_iter; ++g)
+        RK(run_iteration(h, n, g, true, g == 0));
+    CK(launch_pooled_final(h->pooled, h->final_out, h->iter_dev, (uint32_t)n_iter, h->stream));
     h->launches += 1;
+    return RIFT_OK;
+}
+
+int collect_result(rift_ile_t *h, int n_iter, rift_ile_result *out)
+{
     // host_out layout: [0] err word, [1..8) final, [8..) stats
     CK(cudaMemcpyAsync(&h->host_out[1], h->final_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&h->host_out[8], h->stats, sizeof(double) * 8 * n_iter, cudaMemcpyDeviceToHost, h->stream));
@@ -417,6 +390,8 @@ int finish_result(rift_ile_t *h, int n_iter, rift_ile_result *out)
         out->sigma_iter[g] = s[1];
         out->n_eff_iter[g] = s[2];
         out->n_ess_iter[g] = s[3];
+        if (!h->timed)
+            continue;
         float a = 0, b = 0, c = 0, d = 0;
         cudaEventElapsedTime(&a, h->ev[g][0], h->ev[g][1]);
         cudaEventElapsedTime(&b, h->ev[g][1], h->ev[g][2]);
@@ -427,10 +402,62 @@ int finish_result(rift_ile_t *h, int n_iter, rift_ile_result *out)
         out->time_ms[2] += c;
         out->time_ms[3] += d;
     }
+    cudaGetLastError();
     return rc;
 }
 
-}  // namespace
+bool graphs_enabled()
+{
+    const char *env = std::getenv("RIFT_ILE_GRAPHS");
+    return !(env && env[0] == '0');
+}
+
+void drop_graph(rift_ile_t *h)
+{
+    if (h->graph)
+        cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_iter = 0;
+    h->graph_n = 0;
+}
+
+// Capture enqueue_adapt(n_iter, n) on the handle's stream into h->graph.
+int capture_adapt(rift_ile_t *h, int32_t n_iter, int64_t n)
+{
+    drop_graph(h);
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = h->launches;
+    h->capturing = true;
+    int rc = enqueue_adapt(h, n_iter, n);
+    h->capturing = false;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    const int64_t per_run = h->launches - l0;
+    h->launches = l0;
+    if (rc != RIFT_OK || e != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != RIFT_OK ? rc : RIFT_ECUDA;
+    }
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        cudaGetLastError();
+        return RIFT_ECUDA;
+    }
+    h->graph_iter = n_iter;
+    h->graph_n = n;
+    h->graph_plan = h->plan;
+    h->graph_launches = per_run;
+    return RIFT_OK;
+}
+
+}  // namespace host
+}  // namespace rift
+
+using namespace rift::host;
 
 // ============================================================================ ABI
 
@@ -479,6 +506,16 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
     h->cfg.q_t0_s = h->q_t0.data();
     h->cfg.lm = h->lm.data();
     h->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!h->stream) {
+        // a stream of the handle's own (blocking: ordered with the legacy default
+        // stream), so that repeated adaptive sequences can be captured as graphs
+        if (cudaStreamCreate(&h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return RIFT_ECUDA;
+        }
+        h->own_stream = true;
+    }
     h->cap = cfg->max_samples;
 
     Problem &P = h->prob;
@@ -509,7 +546,7 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         P.mode_m[m] = cfg->lm[2 * m + 1];
         int nt = wigner_table(cfg->lm[2 * m], cfg->lm[2 * m + 1], P.wcoef[m], P.wpc[m], P.wps[m]);
         if (nt < 0) {
-            delete h;
+            release(h);
             return RIFT_EINVAL;
         }
         P.wn[m] = (int8_t)nt;
@@ -525,17 +562,18 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->theta, (size_t)N * 6)) || (rc = dalloc(h, &h->lnpw, (size_t)N)) ||
         (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
         (rc = dalloc(h, &h->bins, (size_t)N)) || (rc = dalloc(h, &h->key, (size_t)N)) ||
-        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->counts, (size_t)kMaxCells + 1 + 256)) ||
+        (rc = dalloc(h, &h->perm, (size_t)N)) || (rc = dalloc(h, &h->sort_scratch, sort_scratch_words(N))) ||
         (rc = dalloc(h, &h->tile_counter, (size_t)4)) ||
         (rc = dalloc(h, &h->qmax_bits, (size_t)4)) ||
         (rc = dalloc(h, &h->Qtc, (size_t)K * 2 * ((cfg->n_q + 7) / 8 + 17) * ((2 * M + 15) / 16 * 16) * 8)) ||
         (rc = dalloc(h, &h->red_partial, (size_t)5 * kRedBlocks)) ||
-        (rc = dalloc(h, &h->hist_partial, (size_t)152 * 6 * B)) ||
+        (rc = dalloc(h, &h->hist_partial, (size_t)152 * 12 * B)) ||
         (rc = dalloc(h, &h->stats, (size_t)8 * (RIFT_MAX_ITER + 1))) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
         (rc = dalloc(h, &h->pooled_scratch, (size_t)8)) || (rc = dalloc(h, &h->sel_idx, (size_t)N)) ||
         (rc = dalloc(h, &h->sel_count, (size_t)4)) ||
         (rc = dalloc(h, &h->final_out, (size_t)8)) || (rc = dalloc(h, &h->P, (size_t)6 * B)) ||
-        (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->Lg, (size_t)6 * B)) || (rc = dalloc(h, &h->err, (size_t)4))) {
+        (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->Lg, (size_t)6 * B)) || (rc = dalloc(h, &h->err, (size_t)4)) ||
+        (rc = dalloc(h, &h->iter_dev, (size_t)4))) {
         release(h);
         return rc;
     }
@@ -556,7 +594,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
     if (cudaMemcpyAsync(h->bin_i, bi.data(), sizeof(int) * cfg->n_t, cudaMemcpyHostToDevice, h->stream) ||
         cudaMemcpyAsync(h->bin_f, bf.data(), sizeof(float) * cfg->n_t, cudaMemcpyHostToDevice, h->stream) ||
         cudaMemcpyAsync(h->P, P0.data(), sizeof(double) * 6 * B, cudaMemcpyHostToDevice, h->stream) ||
-        cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream) || launch_build_cdf(sampler_of(h), h->stream) ||
+        cudaMemsetAsync(h->err, 0, sizeof(int) * 4, h->stream) ||
+        cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t) * 4, h->stream) || launch_build_cdf(sampler_of(h), h->stream) ||
         cudaStreamSynchronize(h->stream)) {
         cudaGetLastError();
         release(h);
@@ -576,6 +615,12 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
             h->tc_mode = 0;
         else if (env && env[0] == '1')
             h->tc_mode = 1;
+        if (prepare_sampler_kernels() != cudaSuccess || prepare_refine_kernels() != cudaSuccess ||
+            prepare_tile_kernels() != cudaSuccess || (h->tc_ok && prepare_tc_kernels() != cudaSuccess)) {
+            cudaGetLastError();
+            release(h);
+            return RIFT_ECUDA;
+        }
     }
     P.Q64 = h->Q64;
     P.U64 = h->U64;
@@ -591,6 +636,18 @@ void rift_ile_destroy(rift_ile_t *h) { release(h); }
 
 int64_t rift_ile_kernel_launches(const rift_ile_t *h) { return h ? h->launches : -1; }
 
+int rift_ile_get_plan(const rift_ile_t *h, int32_t *lnl_kernel, int32_t *samples_per_cell)
+{
+    if (!h)
+        return RIFT_EINVAL;
+    const int64_t n = h->last_n > 0 ? h->last_n : h->cap;
+    if (lnl_kernel)
+        *lnl_kernel = !use_fp32(h) ? RIFT_KERNEL_FP64 : use_tc(h, n) ? RIFT_KERNEL_TENSOR : RIFT_KERNEL_CUDA_CORE;
+    if (samples_per_cell)
+        *samples_per_cell = h->plan.per_cell;
+    return RIFT_OK;
+}
+
 int64_t rift_ile_footprint(const rift_ile_config *cfg)
 {
     if (validate(cfg) != RIFT_OK)
@@ -600,8 +657,8 @@ int64_t rift_ile_footprint(const rift_ile_config *cfg)
     const int64_t groups = (nq + 7) / 8 + 17, kp = (2 * M + 15) / 16 * 16;
     const int64_t sizes[] = {
         K * M * nq * 16, 2 * K * M * M * 16, K * 2 * M * nq_pad * 4, 2 * K * M * M * 8, 2 * nt * 4,
-        N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, ((int64_t)kMaxCells + 1 + 256) * 4, 16, 16,
-        K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 6 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
+        N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, (int64_t)sort_scratch_words(N) * 4, 16, 16,
+        K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 12 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
         N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16};
     int64_t total = 0;
     for (int64_t b : sizes)
@@ -768,9 +825,16 @@ int rift_ile_marginalize(rift_ile_t *h, int64_t n_samples, rift_ile_result *out)
         return RIFT_EINVAL;
     if (!h->have_overlaps)
         return RIFT_ESTATE;
+    RK(choose_plan(h, n_samples));
+    RK(ensure_events(h, 1));
+    h->timed = true;
     CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
     RK(run_iteration(h, n_samples, 0, false, true));
-    return finish_result(h, 1, out);
+    CK(launch_pooled_final(h->pooled, h->final_out, h->iter_dev, 1, h->stream));
+    h->launches += 1;
+    h->iteration += 1;
+    h->last_n = n_samples;
+    return collect_result(h, 1, out);
 }
 
 int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_result *out)
@@ -779,10 +843,26 @@ int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_r
         return RIFT_EINVAL;
     if (!h->have_overlaps)
         return RIFT_ESTATE;
-    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
-    for (int g = 0; g < n_iter; ++g)
-        RK(run_iteration(h, n_per_iter, g, true, g == 0));
-    return finish_result(h, n_iter, out);
+    RK(choose_plan(h, n_per_iter));
+    RK(ensure_events(h, n_iter));
+    h->timed = true;
+    const bool same_graph = h->graph && h->graph_iter == n_iter && h->graph_n == n_per_iter &&
+                            h->graph_plan.tc == h->plan.tc && h->graph_plan.per_cell == h->plan.per_cell;
+    const bool repeat = h->last_shape_iter == n_iter && h->last_shape_n == n_per_iter;
+    if (graphs_enabled() && (same_graph || repeat)) {
+        // a repeated shape: capture once, then replay
+        if (!same_graph)
+            RK(capture_adapt(h, n_iter, n_per_iter));
+        CK(cudaGraphLaunch(h->graph, h->stream));
+        h->launches += h->graph_launches;
+    } else {
+        RK(enqueue_adapt(h, n_iter, n_per_iter));
+    }
+    h->last_shape_iter = n_iter;
+    h->last_shape_n = n_per_iter;
+    h->iteration += (uint32_t)n_iter;
+    h->last_n = n_per_iter;
+    return collect_result(h, n_iter, out);
 }
 
 int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus_lnps, double *lnL_tmarg, double *lnw,
@@ -852,8 +932,10 @@ int rift_ile_set_state(rift_ile_t *h, const void *buf, size_t len)
     for (int e = 0; e < 6 * h->cfg.n_bins; ++e)
         if (!(P[e] >= 0.0) || !std::isfinite(P[e]))
             return RIFT_ESTATE;
+    drop_graph(h);   // the seed is a kernel argument of the captured draws
     h->cfg.seed = hd.seed;
     h->iteration = hd.iteration;
+    CK(cudaMemcpyAsync(h->iter_dev, &h->iteration, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(h->P, P, sizeof(double) * 6 * h->cfg.n_bins, cudaMemcpyHostToDevice, h->stream));
     CK(launch_build_cdf(sampler_of(h), h->stream));
     CK(cudaStreamSynchronize(h->stream));

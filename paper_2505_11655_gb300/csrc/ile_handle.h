@@ -1,0 +1,117 @@
+// The ILE handle and the host-side steps shared by the single-solve entry points
+// (ile_api.cu), the batch executor (ile_batch.cu) and the launch autotuner
+// (ile_tune.cu).  Internal: nothing here crosses the C ABI.
+#pragma once
+
+#include <array>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "ile_kernels.h"
+
+// Launch plan of the float32 likelihood stage: which kernel, and how densely the
+// sky-sort grid is filled.  Chosen by the autotuner per problem class, or forced by
+// RIFT_ILE_TC.
+struct LaunchPlan {
+    int tc = -1;         // 1 tensor-core tiles, 0 CUDA-core tiles, -1 not chosen yet
+    int per_cell = 4;    // samples per Hilbert sky cell
+};
+
+struct rift_ile {
+    rift_ile_config cfg{};
+    std::vector<double> det_tensor, det_pos, q_t0;
+    std::vector<int32_t> lm;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    rift::Problem prob{};
+    bool have_overlaps = false;
+    int64_t cap = 0;           // samples per device batch
+    // overlaps
+    double2 *Q64 = nullptr, *U64 = nullptr, *V64 = nullptr;
+    float *Qr32 = nullptr;
+    float2 *U32 = nullptr, *V32 = nullptr;
+    int *bin_i = nullptr;
+    float *bin_f = nullptr;
+    // per-sample buffers
+    double *theta = nullptr, *lnpw = nullptr, *lnL = nullptr, *lnw = nullptr;
+    uint64_t *bins = nullptr;
+    uint32_t *key = nullptr, *perm = nullptr;
+    uint32_t *sort_scratch = nullptr;   // radix-sort digit counts, scan totals, ping-pong buffers
+    int *tile_counter = nullptr;
+    __half *Qtc = nullptr;
+    unsigned int *qmax_bits = nullptr;
+    int tc_mode = 2;              // 0 never, 1 whenever it fits, 2 autotuned
+    bool tc_ok = false;
+    LaunchPlan plan;
+    rift::SkyGrid grid{0, 0};   // sky grid of the current batch size
+    // reductions and sampler
+    double *red_partial = nullptr, *stats = nullptr, *pooled = nullptr, *final_out = nullptr;
+    uint64_t *hist_partial = nullptr;   // [152][6][B][2] exact fixed-point block histograms
+    double *pooled_scratch = nullptr;
+    uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
+    double *P = nullptr, *C = nullptr, *Lg = nullptr;
+    int *err = nullptr;
+    uint32_t *iter_dev = nullptr;   // sampler iteration counter read by the draw kernel
+    std::vector<double> host_out;   // err word, pooled record, per-iteration records
+    uint32_t iteration = 0;
+    int64_t last_n = 0;
+    int64_t launches = 0;
+    std::vector<std::array<cudaEvent_t, 4>> ev;   // per-iteration stage timers, created on first use
+    bool timed = true;        // record the stage timers
+    bool capturing = false;   // work is being captured into a graph
+    // captured adapt sequence, replayed while its shape repeats
+    cudaGraphExec_t graph = nullptr;
+    int32_t graph_iter = 0;
+    int64_t graph_n = 0;
+    LaunchPlan graph_plan;
+    int64_t graph_launches = 0;
+    int32_t last_shape_iter = 0;   // shape of the previous direct adapt call
+    int64_t last_shape_n = 0;
+    std::vector<void *> allocs;
+};
+
+#define CK(call)                                                                                                        \
+    do {                                                                                                                \
+        cudaError_t e_ = (call);                                                                                        \
+        if (e_ != cudaSuccess) {                                                                                        \
+            if (std::getenv("RIFT_ILE_DEBUG"))                                                                          \
+                std::fprintf(stderr, "rift_ile: %s at %s:%d: %s\n", #call, __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            cudaGetLastError();                                                                                         \
+            return RIFT_ECUDA;                                                                                          \
+        }                                                                                                               \
+    } while (0)
+
+#define RK(call)                 \
+    do {                         \
+        int r_ = (call);         \
+        if (r_ != RIFT_OK)       \
+            return r_;           \
+    } while (0)
+
+namespace rift {
+namespace host {
+
+SamplerDev sampler_of(const rift_ile_t *h);
+int map_err(int flags);
+bool use_fp32(const rift_ile_t *h);
+// Create the stage timers of iteration slots [0, n).
+int ensure_events(rift_ile_t *h, int n);
+// Enqueue a whole adaptive sequence on h->stream: error reset, n_iter iterations of
+// n samples, pooled result (device side only; nothing is read back).
+int enqueue_adapt(rift_ile_t *h, int32_t n_iter, int64_t n);
+// Read back the error word and the pooled and per-iteration records after the
+// enqueued work; synchronises h->stream.
+int collect_result(rift_ile_t *h, int n_iter, rift_ile_result *out);
+// Fill in h->plan for a batch of n samples: the cached plan of the problem class,
+// else (measure) the fastest candidate timed on a batch drawn from the sampler's
+// current iteration, else the untuned default.
+int choose_plan(rift_ile_t *h, int64_t n, bool measure = true);
+bool use_tc(const rift_ile_t *h, int64_t n);
+int grid_for_batch(rift_ile_t *h, int64_t n);
+cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
+                         const double *lnpw, double *lnw);
+void drop_graph(rift_ile_t *h);
+
+}  // namespace host
+}  // namespace rift

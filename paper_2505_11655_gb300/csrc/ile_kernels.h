@@ -40,6 +40,13 @@ template <typename Kernel> inline cudaError_t allow_max_dynamic_smem(Kernel kern
     return e;
 }
 
+// Raise the dynamic shared-memory limits of every kernel that needs more than the
+// default; called before any launch can be captured into a graph.
+cudaError_t prepare_sampler_kernels();
+cudaError_t prepare_refine_kernels();
+cudaError_t prepare_tile_kernels();
+cudaError_t prepare_tc_kernels();
+
 // Per-bin split of j * beta (beta = bin spacing x fs): j*beta = bin_i[j] + bin_f[j], 0 <= bin_f < 1.
 struct BinTable {
     const int *bin_i;
@@ -90,15 +97,22 @@ struct SamplerDev {
     uint64_t seed;
 };
 
-cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, int64_t n, double *theta, double *lnpw,
-                        uint64_t *bins, uint32_t *key, cudaStream_t st);
+// Draw n samples of sampler iteration *iter_base + iter_off (the iteration counter is
+// read on the device, so a captured graph replays later iterations unchanged).
+cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, const uint32_t *iter_base, uint32_t iter_off, int64_t n,
+                        double *theta, double *lnpw, uint64_t *bins, uint32_t *key, cudaStream_t st);
 cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32_t *key, cudaStream_t st);
-// Counting sort of keys (< G.n_cells) into perm (scratch: counts[kMaxCells + 1 + 256]).
-cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
-                        cudaStream_t st);
-// Hilbert-curve grid for a batch of n samples: about four samples per cell, at most
-// 2^kMaxOrder cells a side (host side).
-SkyGrid sky_grid_for(int64_t n);
+// Stable sort of sample indices by sky-cell key (< G.n_cells <= 2^20) into perm: LSD
+// radix, 10-bit digits; ties keep index order.  scratch holds sort_scratch_words(n)
+// words; *launched (optional) receives the number of kernels enqueued.
+constexpr int kRadixBits = 10;
+constexpr int kRadixBuckets = 1 << kRadixBits;
+size_t sort_scratch_words(int64_t n_max);
+cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *scratch, uint32_t *perm,
+                        cudaStream_t st, int *launched = nullptr);
+// Hilbert-curve grid for a batch of n samples: about `per_cell` samples per cell, at
+// least 2^4 and at most 2^kMaxOrder cells a side (host side).
+SkyGrid sky_grid_for(int64_t n, int per_cell = 4);
 
 // Reduction of ln w and ln L_tmarg for iteration slot `slot`:
 //   stats[slot*8 + 0..7] = lnZ, sigma, n_eff, n_ess, max lnw, max lnL, N, (unused)
@@ -108,9 +122,11 @@ cudaError_t launch_reduce(const double *lnw, const double *lnL, int64_t n, doubl
                           double *pooled, int reset_pooled, int *err, cudaStream_t st);
 // Histogram adaptation of the sampler from weights exp(beta (lnw - max lnw)) (max from stats[slot]).
 cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
-                         int slot, double *hist_partial, cudaStream_t st);
+                         int slot, uint64_t *hist_partial, cudaStream_t st);
 cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st);
-// Final pooled statistics into out[0..7] = lnZ, sigma, n_eff, n_ess, max lnL, N.
-cudaError_t launch_pooled_final(const double *pooled, double *out, cudaStream_t st);
+// Final pooled statistics into out[0..7] = lnZ, sigma, n_eff, n_ess, max lnL, N; the
+// device iteration counter moves on by `advance`.
+cudaError_t launch_pooled_final(const double *pooled, double *out, uint32_t *iter_base, uint32_t advance,
+                                cudaStream_t st);
 
 }  // namespace rift

@@ -1,0 +1,178 @@
+// Launch autotuner of the float32 likelihood stage.
+//
+// Which tile kernel wins (128-sample tensor-core tiles or 64-sample CUDA-core tiles)
+// and how densely the sky sort fills its Hilbert cells depend on the problem class:
+// the detector count, the mode count (padded to the 16-wide MMA K step), the time
+// grid, the Q length and the batch size.  The first batch of a class times every
+// candidate plan on samples drawn from the sampler (keys + sort + likelihood, best of
+// two runs) and the winner is cached for the process; with RIFT_ILE_TUNE_CACHE set
+// to a file path the cache is also read from and appended to that file.
+#include <cmath>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+
+#include "ile_handle.h"
+
+namespace rift {
+namespace host {
+namespace {
+
+constexpr int64_t kTuneMinBatch = 4096;   // smaller batches take the untuned default
+
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::string, LaunchPlan> plans;
+    bool loaded = false;
+};
+
+TuneCache &cache()
+{
+    static TuneCache c;
+    return c;
+}
+
+const char *cache_path()
+{
+    const char *p = std::getenv("RIFT_ILE_TUNE_CACHE");
+    return p && p[0] ? p : nullptr;
+}
+
+// caller holds the lock
+void load_file(TuneCache &c)
+{
+    if (c.loaded)
+        return;
+    c.loaded = true;
+    const char *path = cache_path();
+    if (!path)
+        return;
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        LaunchPlan p;
+        if ((is >> key >> p.tc >> p.per_cell) && (p.tc == 0 || p.tc == 1) && p.per_cell >= 1 && p.per_cell <= 64)
+            c.plans[key] = p;
+    }
+}
+
+void append_file(const std::string &key, const LaunchPlan &p)
+{
+    const char *path = cache_path();
+    if (!path)
+        return;
+    std::ofstream f(path, std::ios::app);
+    f << key << ' ' << p.tc << ' ' << p.per_cell << '\n';
+}
+
+std::string class_key(const rift_ile_t *h, int64_t n)
+{
+    const int kp = (2 * h->prob.M + 15) / 16;
+    const int nb = (int)std::floor(std::log2((double)n) / 2.0);   // batch size in factors of 4
+    std::ostringstream s;
+    s << "K" << h->prob.K << "_kp" << kp << "_nt" << h->prob.n_t << "_nq" << h->prob.n_q << "_n4^" << nb;
+    return s.str();
+}
+
+// Time keys + sort + likelihood for one plan on the drawn batch (best of two).
+int time_plan(rift_ile_t *h, int64_t n, const LaunchPlan &p, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    h->plan = p;
+    RK(grid_for_batch(h, n));
+    float best = INFINITY;
+    for (int rep = 0; rep < 2; ++rep) {
+        CK(cudaEventRecord(e0, h->stream));
+        CK(launch_keys(h->grid, h->theta, n, h->key, h->stream));
+        CK(launch_sort(h->grid, h->key, n, h->sort_scratch, h->perm, h->stream));
+        CK(launch_tiled(h, h->theta, n, h->lnL, nullptr, nullptr, nullptr));
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        best = t < best ? t : best;
+    }
+    *ms = best;
+    return RIFT_OK;
+}
+
+int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
+{
+    static const LaunchPlan candidates[] = {{0, 4}, {1, 2}, {1, 4}, {1, 8}};
+    const SkyGrid g = sky_grid_for(n, 4);
+    CK(launch_draw(sampler_of(h), g, h->iter_dev, 0, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaGetLastError();
+        return RIFT_ECUDA;
+    }
+    float best = INFINITY;
+    int rc = RIFT_OK;
+    for (const LaunchPlan &p : candidates) {
+        float t = 0;
+        rc = time_plan(h, n, p, e0, e1, &t);
+        if (rc != RIFT_OK)
+            break;
+        if (t < best) {
+            best = t;
+            *out = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing runs may have flagged samples of the scratch batch; the real
+    // iteration redraws the same batch and resets the flags
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return rc;
+}
+
+}  // namespace
+
+int choose_plan(rift_ile_t *h, int64_t n, bool measure_allowed)
+{
+    if (!use_fp32(h))
+        return RIFT_OK;
+    if (!h->tc_ok || h->tc_mode == 0) {
+        h->plan = LaunchPlan{0, 4};
+        return RIFT_OK;
+    }
+    if (h->tc_mode == 1) {
+        h->plan = LaunchPlan{1, 4};
+        return RIFT_OK;
+    }
+    const std::string key = class_key(h, n);
+    TuneCache &c = cache();
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        load_file(c);
+        auto it = c.plans.find(key);
+        if (it != c.plans.end()) {
+            h->plan = it->second;
+            return RIFT_OK;
+        }
+    }
+    const char *env = std::getenv("RIFT_ILE_TUNE");
+    if (!measure_allowed || n < kTuneMinBatch || (env && env[0] == '0')) {
+        h->plan = LaunchPlan{};   // untuned default (kernel by batch size)
+        return RIFT_OK;
+    }
+    LaunchPlan best{};
+    RK(measure(h, n, &best));
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        if (c.plans.emplace(key, best).second)
+            append_file(key, best);
+        h->plan = c.plans[key];
+    }
+    return RIFT_OK;
+}
+
+}  // namespace host
+}  // namespace rift

@@ -218,4 +218,9 @@ cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t 
     return cudaGetLastError();
 }
 
+cudaError_t prepare_refine_kernels()
+{
+    return allow_max_dynamic_smem(refine_kernel);
+}
+
 }  // namespace rift

@@ -21,10 +21,13 @@ namespace rift {
 
 constexpr int kDrawThreads = 256;
 
-__global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGrid G, uint32_t iter, int64_t n,
-                                                            double *__restrict__ theta, double *__restrict__ lnpw,
-                                                            uint64_t *__restrict__ bins, uint32_t *__restrict__ key)
+__global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGrid G,
+                                                            const uint32_t *__restrict__ iter_base, uint32_t iter_off,
+                                                            int64_t n, double *__restrict__ theta,
+                                                            double *__restrict__ lnpw, uint64_t *__restrict__ bins,
+                                                            uint32_t *__restrict__ key)
 {
+    const uint32_t iter = *iter_base + iter_off;
     extern __shared__ double sC[];   // [6][B+1] running sums, then [6][B] masses, [6][B] log densities
     const int B = S.B;
     double *sP = sC + 6 * (B + 1);
@@ -104,8 +107,8 @@ static int grid_for(int64_t n, int threads, int per_sm)
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, int64_t n, double *theta, double *lnpw,
-                        uint64_t *bins, uint32_t *key, cudaStream_t st)
+cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, const uint32_t *iter_base, uint32_t iter_off, int64_t n,
+                        double *theta, double *lnpw, uint64_t *bins, uint32_t *key, cudaStream_t st)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -115,7 +118,7 @@ cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, uint32_t iter, in
         if (e != cudaSuccess)
             return e;
     }
-    draw_kernel<<<grid_for(n, kDrawThreads, 8), kDrawThreads, smem, st>>>(S, G, iter, n, theta, lnpw, bins, key);
+    draw_kernel<<<grid_for(n, kDrawThreads, 8), kDrawThreads, smem, st>>>(S, G, iter_base, iter_off, n, theta, lnpw, bins, key);
     return cudaGetLastError();
 }
 
@@ -133,26 +136,100 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
     return cudaGetLastError();
 }
 
-SkyGrid sky_grid_for(int64_t n)
+SkyGrid sky_grid_for(int64_t n, int per_cell)
 {
-    int order = 4;   // about four samples per cell
-    while (order < kMaxOrder && ((int64_t)4 << (2 * order)) < n)
+    int order = 4;
+    while (order < kMaxOrder && ((int64_t)per_cell << (2 * order)) < n)
         ++order;
     return SkyGrid{order, 1 << (2 * order)};
 }
 
-// ======================================================================== counting sort by sky cell
+// ======================================================================== stable sort by sky cell
+//
+// Least-significant-digit radix sort of the cell keys (10-bit digits: one pass for
+// grids of up to 1024 cells, two for up to 2^20), stable in the sample index: samples
+// of one cell keep their draw order, so the tiles the likelihood kernels form, and
+// with them every float32 result, are the same from run to run.  Each pass: per-tile
+// digit counts (8192 samples per tile), an exclusive scan of the counts in
+// digit-major order, and a scatter in which each warp walks its contiguous quarter of
+// the tile in order and ranks equal digits with a warp match.
 
-__global__ void count_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ counts)
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixPerWarp = 1024;
+constexpr int kRadixTile = kRadixWarps * kRadixPerWarp;
+
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n,
+                                                                   int shift, int nblk, uint32_t *__restrict__ hist)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(counts + key[i], 1u);
+    __shared__ uint32_t h[kRadixBuckets];
+    for (int d = threadIdx.x; d < kRadixBuckets; d += kRadixThreads)
+        h[d] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int j = threadIdx.x; j < kRadixTile; j += kRadixThreads) {
+        const int64_t i = base + j;
+        if (i < n)
+            atomicAdd(&h[(keys[i] >> shift) & (kRadixBuckets - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBuckets; d += kRadixThreads)
+        hist[(size_t)d * nblk + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of the n_cells counts in three passes: per-block totals of 4096
-// counts, a scan of those totals by one block, then a block-level scan of each
-// 4096-count slice offset by its total.  Loads and stores are coalesced; each
-// thread owns 16 consecutive counts staged through shared memory.
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint32_t *__restrict__ keys_in,
+                                                                      const uint32_t *__restrict__ vals_in, int64_t n,
+                                                                      int shift, int nblk,
+                                                                      const uint32_t *__restrict__ offsets,
+                                                                      uint32_t *__restrict__ keys_out,
+                                                                      uint32_t *__restrict__ vals_out)
+{
+    __shared__ uint32_t wpos[kRadixWarps][kRadixBuckets];   // per-warp digit counts, then positions
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = threadIdx.x; e < kRadixWarps * kRadixBuckets; e += kRadixThreads)
+        (&wpos[0][0])[e] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * kRadixPerWarp;
+    for (int j = lane; j < kRadixPerWarp; j += 32) {
+        const int64_t i = base + j;
+        if (i < n)
+            atomicAdd(&wpos[w][(keys_in[i] >> shift) & (kRadixBuckets - 1)], 1u);
+    }
+    __syncthreads();
+    // first position of each digit for each warp: the tile's offset, then warps in order
+    for (int d = threadIdx.x; d < kRadixBuckets; d += kRadixThreads) {
+        uint32_t run = offsets[(size_t)d * nblk + blockIdx.x];
+#pragma unroll
+        for (int v = 0; v < kRadixWarps; ++v) {
+            const uint32_t c = wpos[v][d];
+            wpos[v][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < kRadixPerWarp && base + j0 < n; j0 += 32) {
+        const int64_t i = base + j0 + lane;
+        const bool ok = i < n;
+        const uint32_t k = ok ? keys_in[i] : 0u;
+        const uint32_t d = ok ? (k >> shift) & (kRadixBuckets - 1) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (ok) {
+            const uint32_t pos = wpos[w][d] + __popc(peers & ((1u << lane) - 1u));
+            vals_out[pos] = vals_in ? vals_in[i] : (uint32_t)i;
+            if (keys_out)
+                keys_out[pos] = k;
+        }
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1)
+            wpos[w][d] += (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+}
+
+// Exclusive scan of L counts in place: per-tile totals of 4096 counts, a scan of the
+// totals (recursively when there are more than 1024 tiles), then a block-level scan
+// of each tile offset by its total.  Coalesced loads and stores; each thread owns 16
+// consecutive counts staged through shared memory.
 constexpr int kScanTile = 4096;
 constexpr int kScanThreads = 256;
 
@@ -245,31 +322,60 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(uint32_t *__re
             counts[base + i] = tile[i + (i >> 5)];
 }
 
-__global__ void scatter_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ offs,
-                               uint32_t *__restrict__ perm)
+// Exclusive scan of data[0, L) in place; scratch holds the totals of every level.
+static int launch_scan(uint32_t *data, int L, uint32_t *scratch, cudaStream_t st)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t pos = atomicAdd(offs + key[i], 1u);
-        perm[pos] = (uint32_t)i;
+    const int nb = (L + kScanTile - 1) / kScanTile;
+    scan_totals_kernel<<<nb, kScanThreads, 0, st>>>(data, L, scratch);
+    int launched = 1;
+    if (nb <= 1024) {
+        scan_top_kernel<<<1, 1024, 0, st>>>(scratch, nb);
+        ++launched;
+    } else {
+        launched += launch_scan(scratch, nb, scratch + nb, st);
     }
+    scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(data, L, scratch);
+    return launched + 1;
 }
 
-cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *counts, uint32_t *perm,
-                        cudaStream_t st)
+size_t sort_scratch_words(int64_t n_max)
 {
+    const int64_t nblk = (n_max + kRadixTile - 1) / kRadixTile;
+    int64_t L = (int64_t)kRadixBuckets * (nblk > 0 ? nblk : 1), words = L;
+    while (L > 1) {   // totals of every scan level
+        L = (L + kScanTile - 1) / kScanTile;
+        words += L;
+    }
+    return (size_t)(words + 2 * n_max + 64);
+}
+
+cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *scratch, uint32_t *perm,
+                        cudaStream_t st, int *launched)
+{
+    if (launched)
+        *launched = 0;
     if (n <= 0)
         return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (G.n_cells + 1), st);
-    if (e != cudaSuccess)
-        return e;
-    const int g = grid_for(n, 256, 8);
-    count_kernel<<<g, 256, 0, st>>>(key, n, counts);
-    const int nb = (G.n_cells + kScanTile - 1) / kScanTile;   // <= 256 for 2^20 cells
-    uint32_t *totals = counts + kMaxCells + 1;
-    scan_totals_kernel<<<nb, kScanThreads, 0, st>>>(counts, G.n_cells, totals);
-    scan_top_kernel<<<1, 1024, 0, st>>>(totals, nb);
-    scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(counts, G.n_cells, totals);
-    scatter_kernel<<<g, 256, 0, st>>>(key, n, counts, perm);
+    const int nblk = (int)((n + kRadixTile - 1) / kRadixTile);
+    const int L = kRadixBuckets * nblk;
+    uint32_t *hist = scratch;
+    uint32_t *key_tmp = hist + L, *val_tmp = key_tmp + n;
+    uint32_t *scan_scratch = val_tmp + n;
+    const int passes = G.n_cells <= kRadixBuckets ? 1 : 2;
+    int count = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * kRadixBits;
+        const bool last = pass == passes - 1;
+        const uint32_t *kin = pass == 0 ? key : key_tmp;
+        const uint32_t *vin = pass == 0 ? nullptr : val_tmp;
+        radix_hist_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, nblk, hist);
+        count += 1 + launch_scan(hist, L, scan_scratch, st);
+        radix_scatter_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, nblk, hist,
+                                                             last ? nullptr : key_tmp, last ? perm : val_tmp);
+        count += 1;
+    }
+    if (launched)
+        *launched = count;
     return cudaGetLastError();
 }
 
@@ -425,8 +531,10 @@ cudaError_t launch_reduce(const double *lnw, const double *lnL, int64_t n, doubl
     return cudaGetLastError();
 }
 
-__global__ void pooled_final_kernel(const double *__restrict__ pooled, double *__restrict__ out)
+__global__ void pooled_final_kernel(const double *__restrict__ pooled, double *__restrict__ out, uint32_t *iter_base,
+                                    uint32_t advance)
 {
+    *iter_base += advance;
     double N = pooled[3];
     double var = pooled[2] / (pooled[1] * pooled[1]) - 1.0 / N;
     out[0] = pooled[0] + log(pooled[1]) - log(N);
@@ -437,9 +545,10 @@ __global__ void pooled_final_kernel(const double *__restrict__ pooled, double *_
     out[5] = N;
 }
 
-cudaError_t launch_pooled_final(const double *pooled, double *out, cudaStream_t st)
+cudaError_t launch_pooled_final(const double *pooled, double *out, uint32_t *iter_base, uint32_t advance,
+                                cudaStream_t st)
 {
-    pooled_final_kernel<<<1, 1, 0, st>>>(pooled, out);
+    pooled_final_kernel<<<1, 1, 0, st>>>(pooled, out, iter_base, advance);
     return cudaGetLastError();
 }
 
@@ -447,15 +556,56 @@ cudaError_t launch_pooled_final(const double *pooled, double *out, cudaStream_t 
 
 constexpr int kHistBlocks = 152;
 
+// Histogram weights are summed exactly, in 128-bit fixed point with 2^-90 resolution
+// (lo, hi words): integer addition does not depend on the order in which samples
+// arrive, so the adapted sampler is bitwise reproducible however the blocks and
+// atomics interleave (and a solve's result does not depend on what else runs).
+// Weights are w = exp(beta (ln w_i - max ln w)) <= 1; at most 2^31 samples keep the
+// sum below 2^121.
+constexpr int kFixShift = 90;
+
+__device__ __forceinline__ void to_fixed(double w, uint64_t &lo, uint64_t &hi)
+{
+    lo = hi = 0;
+    if (!(w > 0.0))
+        return;
+    w = fmin(w, 1.0);
+    const uint64_t bits = (uint64_t)__double_as_longlong(w);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    if (e < -kFixShift - 1)
+        return;
+    const uint64_t m = (bits & ((1ull << 52) - 1)) | (1ull << 52);   // w = m 2^(e-52)
+    const int s = e - 52 + kFixShift;                                  // W = m 2^s
+    if (s >= 64) {
+        hi = m << (s - 64);
+    } else if (s > 0) {
+        lo = m << s;
+        hi = m >> (64 - s);
+    } else if (s > -64) {
+        lo = m >> (-s);
+    }
+}
+
+__device__ __forceinline__ void add_fixed(unsigned long long *lo, unsigned long long *hi, uint64_t a_lo, uint64_t a_hi)
+{
+    if (a_lo) {
+        const unsigned long long old = atomicAdd(lo, (unsigned long long)a_lo);
+        if (old + a_lo < old)
+            ++a_hi;   // this addition wrapped the low word
+    }
+    if (a_hi)
+        atomicAdd(hi, (unsigned long long)a_hi);
+}
+
 __global__ void __launch_bounds__(256) hist_partial_kernel(SamplerDev S, const uint64_t *__restrict__ bins,
                                                            const double *__restrict__ lnw, int64_t n,
                                                            const double *__restrict__ stats, int slot,
-                                                           double *__restrict__ partial)
+                                                           uint64_t *__restrict__ partial)
 {
-    extern __shared__ double sH[];   // [6][B]
+    extern __shared__ unsigned long long sF[];   // [6][B][2] = (lo, hi) per bin
     const int B = S.B;
-    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x)
-        sH[e] = 0.0;
+    for (int e = threadIdx.x; e < 12 * B; e += blockDim.x)
+        sF[e] = 0ull;
     __syncthreads();
     const double mx = stats[8 * slot + 4];
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -464,19 +614,24 @@ __global__ void __launch_bounds__(256) hist_partial_kernel(SamplerDev S, const u
         double x = lnw[i];
         if (!isfinite(x))
             continue;
-        double w = exp(S.temper * (x - mx));
+        uint64_t lo, hi;
+        to_fixed(exp(S.temper * (x - mx)), lo, hi);
+        if (!(lo | hi))
+            continue;
         uint64_t pk = bins[i];
 #pragma unroll
-        for (int d = 0; d < 6; ++d)
-            atomicAdd(&sH[d * B + (int)((pk >> (10 * d)) & 1023u)], w);
+        for (int d = 0; d < 6; ++d) {
+            const int e = d * B + (int)((pk >> (10 * d)) & 1023u);
+            add_fixed(&sF[2 * e], &sF[2 * e + 1], lo, hi);
+        }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x)
-        partial[(size_t)blockIdx.x * 6 * B + e] = sH[e];
+    for (int e = threadIdx.x; e < 12 * B; e += blockDim.x)
+        partial[(size_t)blockIdx.x * 12 * B + e] = sF[e];
 }
 
-// Sum partial histograms in block order; P <- (1-eps) H / sum H + eps / B; rebuild C.
-__global__ void adapt_final_kernel(SamplerDev S, const double *__restrict__ partial, int nb)
+// Sum the partial histograms exactly (128-bit); P <- (1-eps) H / sum H + eps / B; rebuild C.
+__global__ void adapt_final_kernel(SamplerDev S, const uint64_t *__restrict__ partial, int nb)
 {
     const int B = S.B;
     const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;   // one warp per dimension
@@ -484,9 +639,14 @@ __global__ void adapt_final_kernel(SamplerDev S, const double *__restrict__ part
         return;
     double tot = 0.0;
     for (int b = lane; b < B; b += 32) {
-        double h = 0.0;
-        for (int k = 0; k < nb; ++k)
-            h += partial[(size_t)k * 6 * B + d * B + b];
+        uint64_t lo = 0, hi = 0;
+        for (int k = 0; k < nb; ++k) {
+            const uint64_t *q = partial + (size_t)k * 12 * B + 2 * (d * B + b);
+            const uint64_t l = lo + q[0];
+            hi += q[1] + (l < lo ? 1u : 0u);
+            lo = l;
+        }
+        const double h = ldexp((double)hi, 64 - kFixShift) + ldexp((double)lo, -kFixShift);
         S.C[d * (B + 1) + b + 1] = h;   // stash H in the C slots while reducing
         tot += h;
     }
@@ -514,14 +674,14 @@ __global__ void adapt_final_kernel(SamplerDev S, const double *__restrict__ part
 }
 
 cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
-                         int slot, double *hist_partial, cudaStream_t st)
+                         int slot, uint64_t *hist_partial, cudaStream_t st)
 {
     int nb = kHistBlocks;
     if ((int64_t)nb * 256 > n)
         nb = (int)((n + 255) / 256);
     if (nb < 1)
         nb = 1;
-    size_t smem = sizeof(double) * 6 * S.B;
+    size_t smem = sizeof(uint64_t) * 12 * S.B;
     if (smem > 48 * 1024) {
         cudaError_t e = allow_max_dynamic_smem(hist_partial_kernel);
         if (e != cudaSuccess)
@@ -551,6 +711,12 @@ cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st)
 {
     build_cdf_kernel<<<1, 32, 0, st>>>(S);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_sampler_kernels()
+{
+    cudaError_t e = allow_max_dynamic_smem(draw_kernel);
+    return e != cudaSuccess ? e : allow_max_dynamic_smem(hist_partial_kernel);
 }
 
 }  // namespace rift

@@ -496,4 +496,10 @@ cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, 
     return cudaGetLastError();
 }
 
+cudaError_t prepare_tile_kernels()
+{
+    cudaError_t e = allow_max_dynamic_smem(lnl_tile_kernel<true>);
+    return e != cudaSuccess ? e : allow_max_dynamic_smem(lnl_tile_kernel<false>);
+}
+
 }  // namespace rift

@@ -678,4 +678,9 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     return cudaGetLastError();
 }
 
+cudaError_t prepare_tc_kernels()
+{
+    return allow_max_dynamic_smem(lnl_tc_kernel);
+}
+
 }  // namespace rift

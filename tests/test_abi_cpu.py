@@ -22,7 +22,7 @@ def lib():
 
 def declared_symbols():
     text = open(os.path.join(ROOT, "include", "rift_ile.h")).read()
-    return sorted(set(re.findall(r"\b(rift_(?:ile|srv)_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(rift_(?:ile|srv|batch)_[a-z_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -126,3 +126,18 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     monkeypatch.setattr(G, "_LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         G.load()
+
+
+def test_batch_rejects_bad_arguments(lib):
+    """rift_batch_create validates its arguments before any CUDA call."""
+    L = lib.load()
+    b = C.c_void_p()
+    it = (C.c_int32 * 2)(1, 1)
+    ns = (C.c_int64 * 2)(100, 100)
+    hs = (C.c_void_p * 2)(None, None)
+    assert L.rift_batch_create(hs, 2, it, ns, None, C.byref(b)) == lib.RIFT_EINVAL
+    assert L.rift_batch_create(hs, 0, it, ns, None, C.byref(b)) == lib.RIFT_EINVAL
+    assert L.rift_batch_create(None, 2, it, ns, None, C.byref(b)) == lib.RIFT_EINVAL
+    assert L.rift_batch_run(None, None) == lib.RIFT_EINVAL
+    assert L.rift_batch_kernel_launches(None) == -1
+    assert L.rift_ile_get_plan(None, None, None) == lib.RIFT_EINVAL

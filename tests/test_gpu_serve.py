@@ -53,10 +53,11 @@ def test_result_same_alone_and_in_mix(G, precision):
     for tag, _, _ in reqs:
         a, b = alone[tag], got[tag]
         assert b["status"] == 0
-        tol = 1e-12 if precision == "fp64" else 1e-5
-        assert abs(a["lnZ"] - b["lnZ"]) <= tol * max(1.0, abs(a["lnZ"]))
-        assert abs(a["n_eff"] - b["n_eff"]) <= 1e-6 * a["n_eff"] + tol
-        assert a["n_total"] == b["n_total"]
+        # bitwise: the sampler histogram is summed exactly and the sky sort is stable,
+        # so nothing in a solve depends on what else is in flight
+        for k in ("lnZ", "sigma_lnZ", "n_eff", "n_ess", "lnL_max", "n_total"):
+            assert a[k] == b[k], (precision, tag, k, a[k], b[k])
+        assert a["lnZ_iter"] == b["lnZ_iter"]
     # solves were in flight together
     t = sorted((c["t_admit_ms"], c["t_done_ms"]) for c in got.values())
     assert any(t[i + 1][0] < t[i][1] for i in range(len(t) - 1))
