@@ -290,7 +290,21 @@ int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmar
 // Sky grid sized for a batch of n samples.
 int grid_for_batch(rift_ile_t *h, int64_t n)
 {
-    h->grid = sky_grid_for(n, h->plan.per_cell);
+    SkyGrid g = sky_grid_for(n, h->plan.per_cell);
+    const Problem &P = h->prob;
+    if (P.K <= 2) {
+        g.mode = P.K == 1 ? kSortDelay1 : kSortDelay2;
+        g.gmst = P.gmst;
+        for (int k = 0; k < P.K; ++k) {
+            double r2 = 0.0;
+            for (int i = 0; i < 3; ++i) {
+                g.x[k][i] = P.xpos[k][i];
+                r2 += P.xpos[k][i] * P.xpos[k][i];
+            }
+            g.span[k] = std::sqrt(r2);
+        }
+    }
+    h->grid = g;
     return RIFT_OK;
 }
 

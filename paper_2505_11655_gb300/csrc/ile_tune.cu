@@ -103,8 +103,9 @@ int time_plan(rift_ile_t *h, int64_t n, const LaunchPlan &p, cudaEvent_t e0, cud
 int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
 {
     static const LaunchPlan candidates[] = {{0, 4}, {1, 2}, {1, 4}, {1, 8}};
-    const SkyGrid g = sky_grid_for(n, 4);
-    CK(launch_draw(sampler_of(h), g, h->iter_dev, 0, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
+    h->plan = LaunchPlan{};
+    RK(grid_for_batch(h, n));
+    CK(launch_draw(sampler_of(h), h->grid, h->iter_dev, 0, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {

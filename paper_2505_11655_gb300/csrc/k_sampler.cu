@@ -639,14 +639,20 @@ __global__ void adapt_final_kernel(SamplerDev S, const uint64_t *__restrict__ pa
         return;
     double tot = 0.0;
     for (int b = lane; b < B; b += 32) {
-        uint64_t lo = 0, hi = 0;
+        // the low words are summed as two 32-bit halves (no carry chain between the
+        // loads), then recombined exactly
+        uint64_t l0 = 0, l1 = 0, hi = 0;
+#pragma unroll 8
         for (int k = 0; k < nb; ++k) {
             const uint64_t *q = partial + (size_t)k * 12 * B + 2 * (d * B + b);
-            const uint64_t l = lo + q[0];
-            hi += q[1] + (l < lo ? 1u : 0u);
-            lo = l;
+            const uint64_t lo = q[0];
+            l0 += lo & 0xffffffffull;
+            l1 += lo >> 32;
+            hi += q[1];
         }
-        const double h = ldexp((double)hi, 64 - kFixShift) + ldexp((double)lo, -kFixShift);
+        const uint64_t a = l0 + (l1 << 32);
+        hi += (l1 >> 32) + (a < l0 ? 1u : 0u);
+        const double h = ldexp((double)hi, 64 - kFixShift) + ldexp((double)a, -kFixShift);
         S.C[d * (B + 1) + b + 1] = h;   // stash H in the C slots while reducing
         tot += h;
     }
