@@ -82,6 +82,16 @@ def lib():
             L.orc_antenna.restype = None
             L.orc_delay.argtypes = [vp, dbl, dbl, dbl]
             L.orc_delay.restype = dbl
+            L.orc_fair_words.argtypes = [C.c_uint64, i64, vp]
+            L.orc_fair_words.restype = None
+            L.orc_fix_cumulative.argtypes = [vp, i64, vp]
+            L.orc_fix_cumulative.restype = C.c_int
+            L.orc_fix_choose.argtypes = [vp, i64, C.c_uint64]
+            L.orc_fix_choose.restype = i64
+            L.orc_fair_draws.argtypes = [vp, i64, C.c_uint64, i64, vp, vp]
+            L.orc_fair_draws.restype = C.c_int
+            L.orc_fair_time_bin.argtypes = [vp, i64, C.c_uint64]
+            L.orc_fair_time_bin.restype = i64
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = C.c_int
             _lib = L
@@ -242,6 +252,50 @@ def run_adapt(prob, sampler: Sampler, n_iter: int, n_per_iter: int, adapt_last=T
     pooled = reduce(np.concatenate(lnws))
     pooled["lnL_max"] = float(max(np.max(x) for x in lnLs))
     return dict(iterations=its, pooled=pooled, lnw=lnws, theta=thetas, lnL=lnLs)
+
+
+def fair_words(seed, d):
+    """53-bit integers (sample choice, time choice) of fair draw d."""
+    out = np.empty(2, np.uint64)
+    lib().orc_fair_words(int(seed), int(d), _p(out))
+    return int(out[0]), int(out[1])
+
+
+def fix_cumulative(x):
+    """Running sums of the exact fixed-point weights of log-weights x, and the shift S."""
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    cum = np.empty(max(1, a.size), np.uint64)
+    S = lib().orc_fix_cumulative(_p(a), a.size, _p(cum))
+    if S < 0:
+        raise ValueError("no finite log-weight")
+    return cum[:a.size], S
+
+
+def fix_choose(cum, U):
+    c = np.ascontiguousarray(cum, dtype=np.uint64)
+    return int(lib().orc_fix_choose(_p(c), c.size, int(U)))
+
+
+def fair_draws(prob, theta, lnw, n_draws, seed):
+    """Fair draws from the weighted samples (theta [n][6], lnw [n]): sample indices,
+    their theta, and each draw's time bin and time from the sample's per-bin ln L
+    (evaluated here in float64).  Returns (idx, theta, j, t)."""
+    P = _as_problem(prob)
+    w = np.ascontiguousarray(lnw, dtype=np.float64)
+    idx = np.empty(int(n_draws), np.int64)
+    Ut = np.empty(int(n_draws), np.uint64)
+    if lib().orc_fair_draws(_p(w), w.size, int(seed), int(n_draws), _p(idx), _p(Ut)) != 0:
+        raise ValueError("no finite log-weight")
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).reshape(-1, 6)[idx])
+    _, bins, _ = lnL(P, th, want_bins=True)
+    j = np.empty(int(n_draws), np.int64)
+    for d in range(int(n_draws)):
+        row = np.ascontiguousarray(bins[d])
+        j[d] = lib().orc_fair_time_bin(_p(row), row.size, int(Ut[d]))
+    t_lo, t_hi = P.s.t_lo, P.s.t_hi
+    step = (t_hi - t_lo) / (P.n_t - 1) if P.n_t > 1 else 0.0
+    t = t_lo + j * step
+    return idx, th, j, t
 
 
 def num_threads() -> int:

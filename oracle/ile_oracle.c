@@ -471,6 +471,112 @@ void orc_adapt(double *P, int B, const int32_t *bins, const double *lnw, int64_t
     free(H);
 }
 
+/* ---------------------------------------------------------------- fair draws */
+
+/* The final ILE pass (Sec. II, the closing paragraph of the method overview, and the
+ * two-step posterior construction of Sec. II D): extrinsic samples are drawn fairly,
+ * with replacement, from the Monte Carlo integral's weighted samples, and each draw's
+ * time from the per-bin likelihood of that sample (the time prior is uniform on the grid).
+ *
+ * Readings where the paper is silent:
+ *  - every discrete choice is made exactly in integer arithmetic.  Item i of a list of
+ *    log-weights x gets W_i = floor(exp(x_i - max x) 2^S) with S = 62 - ceil(log2 n)
+ *    (0 for non-finite x_i), so the total stays below 2^62;
+ *  - draw d uses Philox4x32-10 with key = seed and counter = (d low, d high,
+ *    0xFFFFFFFF, 0); words (0,1) give the 53-bit integer U of the sample choice, words
+ *    (2,3) that of the time choice (the same 27 + 26 bit split as orc_u53);
+ *  - the chosen item is the first whose running sum of W exceeds floor(U Total / 2^53). */
+static int orc_fix_shift(int64_t n)
+{
+    int c = 0;
+    while (((int64_t)1 << c) < n)
+        ++c;
+    return 62 - c;
+}
+
+static uint64_t orc_fix_weight(double x, double mx, int S)
+{
+    if (!isfinite(x))
+        return 0;
+    return (uint64_t)ldexp(exp(x - mx), S);
+}
+
+/* 53-bit integers (sample choice, time choice) of draw d. */
+void orc_fair_words(uint64_t seed, int64_t d, uint64_t U[2])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)(uint64_t)d, (uint32_t)((uint64_t)d >> 32), 0xFFFFFFFFu, 0u};
+    uint32_t r[4];
+    orc_philox4x32_10(ctr, key, r);
+    U[0] = ((uint64_t)(r[0] >> 5) << 26) | (uint64_t)(r[1] >> 6);
+    U[1] = ((uint64_t)(r[2] >> 5) << 26) | (uint64_t)(r[3] >> 6);
+}
+
+/* Running sums of the fixed-point weights of x[0..n); returns the shift S, or -1 if no
+ * x is finite.  cum has n entries. */
+int orc_fix_cumulative(const double *x, int64_t n, uint64_t *cum)
+{
+    double mx = -INFINITY;
+    for (int64_t i = 0; i < n; ++i)
+        if (isfinite(x[i]) && x[i] > mx)
+            mx = x[i];
+    if (!isfinite(mx))
+        return -1;
+    const int S = orc_fix_shift(n);
+    uint64_t run = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        run += orc_fix_weight(x[i], mx, S);
+        cum[i] = run;
+    }
+    return S;
+}
+
+/* First i with cum[i] > floor(U cum[n-1] / 2^53) (binary search over the running sums). */
+int64_t orc_fix_choose(const uint64_t *cum, int64_t n, uint64_t U)
+{
+    const uint64_t T = (uint64_t)(((unsigned __int128)U * cum[n - 1]) >> 53);
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (cum[mid] > T)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+/* n_draws fair draws from the weighted samples lnw[0..n): sample indices idx[] and the
+ * time-choice integers U_time[] (for the second step).  Returns 0, or -1 if no weight is
+ * finite. */
+int orc_fair_draws(const double *lnw, int64_t n, uint64_t seed, int64_t n_draws, int64_t *idx, uint64_t *U_time)
+{
+    uint64_t *cum = malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    if (n < 1 || orc_fix_cumulative(lnw, n, cum) < 0) {
+        free(cum);
+        return -1;
+    }
+    for (int64_t d = 0; d < n_draws; ++d) {
+        uint64_t U[2];
+        orc_fair_words(seed, d, U);
+        idx[d] = orc_fix_choose(cum, n, U[0]);
+        U_time[d] = U[1];
+    }
+    free(cum);
+    return 0;
+}
+
+/* Time bin of one draw from its per-bin ln L[0..n_t) and its time-choice integer. */
+int64_t orc_fair_time_bin(const double *lnL_bins, int64_t n_t, uint64_t U)
+{
+    uint64_t *cum = malloc(sizeof(uint64_t) * (size_t)n_t);
+    int64_t j = -1;
+    if (orc_fix_cumulative(lnL_bins, n_t, cum) >= 0)
+        j = orc_fix_choose(cum, n_t, U);
+    free(cum);
+    return j;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

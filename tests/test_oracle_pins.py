@@ -465,3 +465,94 @@ def test_p10_mc_matches_quadrature(orc):
     res = orc.run_adapt(p, sm, 2, 200000)
     for it in res["iterations"]:
         assert abs(it["lnZ"] - lnZ_q) < 4 * it["sigma_lnZ"] + 2e-3
+
+
+# ------------------------------------------------------------------------------ fair draws
+
+def test_fair_fixed_point_weights_and_choice_definition(orc):
+    """Exact integer weights W_i = floor(exp(x_i - max) 2^S), S = 62 - ceil(log2 n),
+    and the choice 'first running sum above floor(U Total / 2^53)' at the ends and
+    at exact interior fractions."""
+    x = np.log(np.array([1.0, 2.0, 0.0, 5.0, 2.0]))   # ln 0 = -inf: never chosen
+    cum, S = orc.fix_cumulative(x)
+    assert S == 62 - 3
+    mx = math.log(5.0)
+    w = [int(math.ldexp(math.exp(v - mx), S)) if np.isfinite(v) else 0 for v in x]
+    assert w[3] == 1 << S and w[2] == 0 and abs(w[0] - (1 << S) // 5) <= 64
+    assert [int(c) for c in cum] == list(np.cumsum(np.array(w, dtype=object)))
+    tot = int(cum[-1])
+    assert orc.fix_choose(cum, 0) == 0
+    assert orc.fix_choose(cum, (1 << 53) - 1) == 4
+    # at each running-sum boundary c: the smallest U whose threshold floor(U tot / 2^53)
+    # reaches c chooses the next item with weight; the U just below chooses the item
+    # that ends at c
+    for c, before, after in ((int(cum[0]), 0, 1), (int(cum[1]), 1, 3), (int(cum[3]), 3, 4)):
+        U = -(-(c << 53) // tot)
+        assert (U * tot) >> 53 >= c and ((U - 1) * tot) >> 53 < c
+        assert orc.fix_choose(cum, U) == after
+        assert orc.fix_choose(cum, U - 1) == before
+    with pytest.raises(ValueError):
+        orc.fix_cumulative(np.full(3, -np.inf))
+
+
+def test_fair_draw_words_are_philox(orc):
+    """The draw integers are Philox4x32-10 words under the reserved counter word."""
+    seed, d = 0x0123456789ABCDEF, 77
+    r = orc.philox4x32_10([d, 0, 0xFFFFFFFF, 0], [seed & 0xFFFFFFFF, seed >> 32])
+    U = orc.fair_words(seed, d)
+    assert U[0] == (int(r[0]) >> 5 << 26) | (int(r[1]) >> 6)
+    assert U[1] == (int(r[2]) >> 5 << 26) | (int(r[3]) >> 6)
+
+
+def test_fair_draw_frequencies_are_multinomial(orc):
+    """200k draws from five weighted items: chi-square against the exact
+    probabilities w_i / sum w (the p-value floor is fixed for the fixed seed)."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    w = np.array([0.1, 3.0, 0.0, 1.5, 0.4])
+    lnw = np.log(w)
+    n_draws = 200000
+    idx = np.empty(n_draws, np.int64)
+    cum, _ = orc.fix_cumulative(lnw)
+    for d in range(n_draws):
+        idx[d] = orc.fix_choose(cum, orc.fair_words(5, d)[0])
+    counts = np.bincount(idx, minlength=5)
+    assert counts[2] == 0
+    keep = w > 0
+    p = scipy_stats.chisquare(counts[keep], n_draws * w[keep] / w.sum()).pvalue
+    assert p > 1e-3
+
+
+def test_fair_draws_brute_force_joint_distribution(orc):
+    """Tiny problem: the joint frequency of (sample, time bin) over 60000 draws
+    matches w_i / sum w x exp(ln L_ij) / sum_j exp(ln L_ij) computed directly."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    p = S.make_problem(("H1",), 2, 4096.0, n_t=5, snr=3.0, t_lo=-0.002, t_hi=0.002, seed=31)
+    th = S.prior_samples(4, 9)
+    ll, bins, _ = orc.lnL(p, th, want_bins=True)
+    lnw = ll + np.array([0.0, -0.5, 0.3, -1.0])
+    n_draws = 60000
+    idx, th_d, j, t = orc.fair_draws(p, th, lnw, n_draws, seed=12)
+    assert np.array_equal(th_d, th[idx])
+    assert np.allclose(t, p.t_lo + j * (p.t_hi - p.t_lo) / (p.n_t - 1), rtol=0, atol=1e-15)
+    pw = np.exp(lnw - lnw.max())
+    pw /= pw.sum()
+    pt = np.exp(bins - bins.max(1, keepdims=True))
+    pt /= pt.sum(1, keepdims=True)
+    expected = (pw[:, None] * pt).ravel() * n_draws
+    counts = np.bincount(idx * p.n_t + j, minlength=4 * p.n_t)
+    keep = expected > 5
+    assert counts[~keep].sum() < 50
+    pval = scipy_stats.chisquare(counts[keep], expected[keep] * counts[keep].sum() / expected[keep].sum()).pvalue
+    assert pval > 1e-3
+
+
+def test_fair_time_bin_follows_a_dominant_bin(orc):
+    """A bin 50 above every other is always the one drawn; equal bins are drawn
+    uniformly."""
+    row = np.zeros(9)
+    row[6] = 50.0
+    cum, _ = orc.fix_cumulative(row)
+    assert all(orc.fix_choose(cum, orc.fair_words(3, d)[1]) == 6 for d in range(500))
+    cum, _ = orc.fix_cumulative(np.zeros(4))
+    got = np.bincount([orc.fix_choose(cum, orc.fair_words(3, d)[1]) for d in range(4000)], minlength=4)
+    assert np.all(np.abs(got - 1000) < 150)
