@@ -550,6 +550,11 @@ def run_high_snr(args, rank, world, local_rank):
     total = _max_over_ranks(torch, world, sum(step_ms))
     value = n * n_iter * args.steps * world / (total / 1e3)
     r = res[-1]
+    # fair draws from the last batch (sample by weight, then time bin by per-bin ln L)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fth, ft, fidx = ile.fair_draws(10000, seed=17)
+    fair_ms = 1e3 * (time.perf_counter() - t0)
     # error of the last batch against the float64 path (1e-9 parity with the oracle):
     # every sample within 30 of the largest ln w, plus 4096 others
     th, lr, ll, lw = ile.last_batch(n)
@@ -590,6 +595,8 @@ def run_high_snr(args, rank, world, local_rank):
         "result": {"lnZ": r["lnZ"], "sigma_lnZ": r["sigma_lnZ"], "n_eff": r["n_eff"], "n_ess": r["n_ess"],
                    "lnL_max": r["lnL_max"], "n_eff_iter": r["n_eff_iter"], "lnZ_iter": r["lnZ_iter"]},
         "error_vs_fp64": err,
+        "fair_draws": {"draws": 10000, "ms": fair_ms, "distinct_samples": int(len(np.unique(fidx))),
+                       "t_spread_ms": float(1e3 * np.std(ft))},
         "stage_ms_per_step": {"draw_sort": r["time_ms"][0], "lnl_refine": r["time_ms"][1],
                               "reduce_adapt": r["time_ms"][2]},
         "e2e": None, "gpu_launches": launches, "clocks": clocks,

@@ -192,6 +192,27 @@ int rift_ile_get_plan(const rift_ile_t *h, int32_t *lnl_kernel, int32_t *samples
 int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus_lnps, double *lnL_tmarg,
                         double *lnw, int64_t *n_out);
 
+/* Fair draws from the most recent batch (the final ILE pass: extrinsic samples drawn
+ * fairly from the Monte Carlo integral's weighted samples, arXiv:2505.11655 Sec. II;
+ * the two-step fair draw of Sec. II D).  Draw d takes sample i, with replacement, with
+ * probability w_i / sum w (w = exp(ln w) of that batch), then a time bin j with
+ * probability exp(ln L(theta_i, t_j)) / sum_j exp(ln L(theta_i, t_j)), the per-bin
+ * ln L evaluated in float64 (the time prior is uniform on the grid).
+ *   n_draws            number of draws (0 is a no-op)
+ *   seed               key of the draws' random numbers (independent of the sampler)
+ *   theta [n_draws][6] drawn samples, t [n_draws] their times (s, relative to the
+ *                      reference epoch), index [n_draws] their positions in the batch;
+ *                      any output may be NULL (not all), all in `mem`.
+ * Every choice is exact in integer arithmetic: weights floor(exp(x - max x) 2^S),
+ * S = 62 - ceil(log2 count), and the first item whose running sum exceeds
+ * floor(U Total / 2^53) for the 53-bit integer U of Philox4x32-10 (key = seed, counter =
+ * (d low, d high, 0xFFFFFFFF, 0); words 0,1 for the sample, 2,3 for the time bin).
+ * RIFT_ESTATE if there is no batch yet; RIFT_ENONFINITE if a ln w of the batch is not
+ * finite; RIFT_ENOMEM if the scratch (about 16 n + 70 n_draws + 16 MiB bytes) cannot be
+ * allocated. */
+int rift_ile_fair_draws(rift_ile_t *h, int64_t n_draws, uint64_t seed, int mem, double *theta, double *t,
+                        int64_t *index);
+
 /* Sampler state (histogram masses, counter, seed) as an opaque versioned blob.
  * get: if buf is NULL, *len receives the size; otherwise *len must be >= it.
  * set: restores a blob from get (RIFT_ESTATE if malformed or of another shape). */

@@ -31,7 +31,7 @@ RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_get_plan", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_ile_get_plan", "rift_ile_fair_draws", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
             "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
@@ -119,6 +119,7 @@ def load(build_if_missing: bool = False):
     L.rift_srv_destroy.argtypes = [vp]
     L.rift_srv_destroy.restype = None
     L.rift_ile_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.rift_ile_fair_draws.argtypes = [vp, i64, C.c_uint64, C.c_int, vp, vp, vp]
     L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
     L.rift_batch_run.argtypes = [vp, C.POINTER(rift_ile_result)]
     L.rift_batch_kernel_launches.argtypes = [vp]
@@ -283,6 +284,13 @@ def rift_ile_get_plan(h):
     k, c = C.c_int32(), C.c_int32()
     _check(load().rift_ile_get_plan(h, C.byref(k), C.byref(c)), "rift_ile_get_plan")
     return k.value, c.value
+
+
+def rift_ile_fair_draws(h, n_draws, seed, theta=None, t=None, index=None):
+    bufs = [b for b in (theta, t, index) if b is not None]
+    mem = _mem(bufs[0]) if bufs else RIFT_MEM_HOST
+    _check(load().rift_ile_fair_draws(h, int(n_draws), int(seed), mem, _ptr(theta), _ptr(t), _ptr(index)),
+           "rift_ile_fair_draws")
 
 
 def rift_batch_create(handles, n_iter, n_per_iter, stream=None):
@@ -492,6 +500,12 @@ class ILE:
 
     def kernel_launches(self):
         return rift_ile_kernel_launches(self.h)
+
+    def fair_draws(self, n_draws, seed=1):
+        """Fair draws from the most recent batch: (theta [n][6], t [n], index [n])."""
+        th, t, idx = np.empty((n_draws, 6)), np.empty(n_draws), np.empty(n_draws, np.int64)
+        rift_ile_fair_draws(self.h, n_draws, seed, th, t, idx)
+        return th, t, idx
 
     def plan(self):
         """(likelihood kernel: RIFT_KERNEL_*, samples per sky cell) of the last batch."""

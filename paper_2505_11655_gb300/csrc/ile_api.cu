@@ -902,6 +902,74 @@ int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus
     return RIFT_OK;
 }
 
+int rift_ile_fair_draws(rift_ile_t *h, int64_t n_draws, uint64_t seed, int mem, double *theta, double *t,
+                        int64_t *index)
+{
+    if (!h || n_draws < 0 || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    if (n_draws == 0)
+        return RIFT_OK;
+    if (!theta && !t && !index)
+        return RIFT_EINVAL;
+    const int64_t n = h->last_n;
+    if (n == 0)
+        return RIFT_ESTATE;
+    const int nt = h->prob.n_t;
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_draws, (int64_t)(16 << 20) / nt));
+    std::vector<void *> tmp;
+    auto grab = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        tmp.push_back(q);
+        return q;
+    };
+    auto W = static_cast<uint64_t *>(grab(sizeof(uint64_t) * n));
+    auto E = static_cast<uint64_t *>(grab(sizeof(uint64_t) * n));
+    auto scan = static_cast<uint64_t *>(grab(sizeof(uint64_t) * scan_scratch_words(n)));
+    auto idx = static_cast<int64_t *>(grab(sizeof(int64_t) * n_draws));
+    auto th = static_cast<double *>(grab(sizeof(double) * 6 * n_draws));
+    auto Ut = static_cast<uint64_t *>(grab(sizeof(uint64_t) * n_draws));
+    auto tt = static_cast<double *>(grab(sizeof(double) * n_draws));
+    auto jj = static_cast<int32_t *>(grab(sizeof(int32_t) * n_draws));
+    auto bins = static_cast<double *>(grab(sizeof(double) * chunk * nt));
+    auto lt = static_cast<double *>(grab(sizeof(double) * chunk));
+    int rc = (W && E && scan && idx && th && Ut && tt && jj && bins && lt) ? RIFT_OK : RIFT_ENOMEM;
+    const cudaMemcpyKind kind = mem == RIFT_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    auto run = [&]() -> int {
+        CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+        // the batch's largest ln w (checks every ln w is finite)
+        CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, kScratchSlot, h->pooled_scratch, 1, h->err,
+                         h->stream));
+        int k = 0;
+        CK(launch_fair_select(h->lnw, n, h->stats, kScratchSlot, W, E, scan, seed, n_draws, h->theta, idx, th, Ut,
+                              h->stream, &k));
+        h->launches += 2 + k;
+        // time bins from each drawn sample's per-bin ln L, in float64 (the draws are few)
+        for (int64_t c0 = 0; c0 < n_draws; c0 += chunk) {
+            const int64_t m = std::min(chunk, n_draws - c0);
+            CK(launch_lnl_fp64(h->prob, th + 6 * c0, m, lt, bins, nullptr, nullptr, h->err, h->stream));
+            CK(launch_fair_time(bins, m, nt, Ut + c0, h->prob.t_lo, h->prob.t_step, jj + c0, tt + c0, h->stream));
+            h->launches += 2;
+        }
+        if (theta)
+            CK(cudaMemcpyAsync(theta, th, sizeof(double) * 6 * n_draws, kind, h->stream));
+        if (t)
+            CK(cudaMemcpyAsync(t, tt, sizeof(double) * n_draws, kind, h->stream));
+        if (index)
+            CK(cudaMemcpyAsync(index, idx, sizeof(int64_t) * n_draws, kind, h->stream));
+        return RIFT_OK;
+    };
+    if (rc == RIFT_OK)
+        rc = run();
+    for (void *q : tmp)
+        cudaFreeAsync(q, h->stream);
+    const int rc2 = sync_and_err(h);
+    return rc != RIFT_OK ? rc : rc2;
+}
+
 int rift_ile_get_sampler(const rift_ile_t *h, double *P)
 {
     if (!h || !P)

@@ -40,6 +40,16 @@ template <typename Kernel> inline cudaError_t allow_max_dynamic_smem(Kernel kern
     return e;
 }
 
+// Fair draws (k_fair.cu): fixed-point weights of lnw (max from stats[slot]), their
+// running sums, and n_draws sample choices with their time-choice integers.
+cudaError_t launch_fair_select(const double *lnw, int64_t n, const double *stats, int slot, uint64_t *W,
+                               uint64_t *E, uint64_t *scan_scratch, uint64_t seed, int64_t n_draws,
+                               const double *theta, int64_t *idx, double *theta_sel, uint64_t *U_time,
+                               cudaStream_t st, int *launched);
+// Time bins of m draws from their per-bin ln L rows [m][n_t].
+cudaError_t launch_fair_time(const double *lnL_t, int64_t m, int n_t, const uint64_t *U_time, double t_lo,
+                             double t_step, int32_t *j_out, double *t_out, cudaStream_t st);
+
 // Raise the dynamic shared-memory limits of every kernel that needs more than the
 // default; called before any launch can be captured into a graph.
 cudaError_t prepare_sampler_kernels();
@@ -108,6 +118,9 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
 constexpr int kRadixBits = 10;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 size_t sort_scratch_words(int64_t n_max);
+// Exclusive scan of 64-bit counts in place (L < 2^31); scratch holds scan_scratch_words(L).
+size_t scan_scratch_words(int64_t L);
+cudaError_t launch_scan_u64(uint64_t *data, int64_t L, uint64_t *scratch, cudaStream_t st, int *launched = nullptr);
 cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32_t *scratch, uint32_t *perm,
                         cudaStream_t st, int *launched = nullptr);
 // Hilbert-curve grid for a batch of n samples: about `per_cell` samples per cell, at

@@ -229,16 +229,18 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint
 // Exclusive scan of L counts in place: per-tile totals of 4096 counts, a scan of the
 // totals (recursively when there are more than 1024 tiles), then a block-level scan
 // of each tile offset by its total.  Coalesced loads and stores; each thread owns 16
-// consecutive counts staged through shared memory.
+// consecutive counts staged through shared memory.  32-bit for the sort, 64-bit for
+// the fair draws' fixed-point weights.
 constexpr int kScanTile = 4096;
 constexpr int kScanThreads = 256;
 
-__global__ void __launch_bounds__(kScanThreads) scan_totals_kernel(const uint32_t *__restrict__ counts, int n_cells,
-                                                                   uint32_t *__restrict__ totals)
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) scan_totals_kernel(const T *__restrict__ counts, int n_cells,
+                                                                   T *__restrict__ totals)
 {
-    __shared__ uint32_t red[kScanThreads / 32];
+    __shared__ T red[kScanThreads / 32];
     const int base = blockIdx.x * kScanTile;
-    uint32_t v = 0;
+    T v = 0;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
         if (base + i < n_cells)
             v += counts[base + i];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_totals_kernel(const uint32_
         red[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        uint32_t t = 0;
+        T t = 0;
         for (int w = 0; w < kScanThreads / 32; ++w)
             t += red[w];
         totals[blockIdx.x] = t;
@@ -257,13 +259,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_totals_kernel(const uint32_
 }
 
 // Block-wide exclusive scan of one value per thread; returns this thread's offset.
-__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot)
+template <typename T> __device__ T block_exclusive_scan(T v, T *warp_tot)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        T y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o)
             x += y;
     }
@@ -271,46 +273,47 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_tot)
         warp_tot[w] = x;
     __syncthreads();
     if (w == 0) {
-        uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+        T t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : (T)0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            T y = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o)
                 t += y;
         }
         warp_tot[lane] = t;
     }
     __syncthreads();
-    return x - v + (w > 0 ? warp_tot[w - 1] : 0u);
+    return x - v + (w > 0 ? warp_tot[w - 1] : (T)0);
 }
 
-__global__ void __launch_bounds__(1024) scan_top_kernel(uint32_t *totals, int nb)
+template <typename T> __global__ void __launch_bounds__(1024) scan_top_kernel(T *totals, int nb)
 {
-    __shared__ uint32_t warp_tot[32];
-    const uint32_t v = threadIdx.x < nb ? totals[threadIdx.x] : 0u;
-    const uint32_t e = block_exclusive_scan(v, warp_tot);
+    __shared__ T warp_tot[32];
+    const T v = threadIdx.x < nb ? totals[threadIdx.x] : (T)0;
+    const T e = block_exclusive_scan(v, warp_tot);
     if (threadIdx.x < nb)
         totals[threadIdx.x] = e;
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(uint32_t *__restrict__ counts, int n_cells,
-                                                                  const uint32_t *__restrict__ totals)
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(T *__restrict__ counts, int n_cells,
+                                                                  const T *__restrict__ totals)
 {
     constexpr int per = kScanTile / kScanThreads;
-    __shared__ uint32_t tile[kScanTile + kScanTile / 32];   // padded: thread-strided reads avoid conflicts
-    __shared__ uint32_t warp_tot[32];
+    __shared__ T tile[kScanTile + kScanTile / 32];   // padded: thread-strided reads avoid conflicts
+    __shared__ T warp_tot[32];
     const int base = blockIdx.x * kScanTile;
     for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
-        tile[i + (i >> 5)] = base + i < n_cells ? counts[base + i] : 0u;
+        tile[i + (i >> 5)] = base + i < n_cells ? counts[base + i] : (T)0;
     __syncthreads();
-    uint32_t loc[per], run = 0;
+    T loc[per], run = 0;
 #pragma unroll
     for (int q = 0; q < per; ++q) {
         const int i = threadIdx.x * per + q;
         loc[q] = run;
         run += tile[i + (i >> 5)];
     }
-    const uint32_t off = block_exclusive_scan(run, warp_tot) + totals[blockIdx.x];
+    const T off = block_exclusive_scan(run, warp_tot) + totals[blockIdx.x];
 #pragma unroll
     for (int q = 0; q < per; ++q) {
         const int i = threadIdx.x * per + q;
@@ -323,19 +326,37 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(uint32_t *__re
 }
 
 // Exclusive scan of data[0, L) in place; scratch holds the totals of every level.
-static int launch_scan(uint32_t *data, int L, uint32_t *scratch, cudaStream_t st)
+template <typename T> static int launch_scan(T *data, int L, T *scratch, cudaStream_t st)
 {
     const int nb = (L + kScanTile - 1) / kScanTile;
-    scan_totals_kernel<<<nb, kScanThreads, 0, st>>>(data, L, scratch);
+    scan_totals_kernel<T><<<nb, kScanThreads, 0, st>>>(data, L, scratch);
     int launched = 1;
     if (nb <= 1024) {
-        scan_top_kernel<<<1, 1024, 0, st>>>(scratch, nb);
+        scan_top_kernel<T><<<1, 1024, 0, st>>>(scratch, nb);
         ++launched;
     } else {
-        launched += launch_scan(scratch, nb, scratch + nb, st);
+        launched += launch_scan<T>(scratch, nb, scratch + nb, st);
     }
-    scan_apply_kernel<<<nb, kScanThreads, 0, st>>>(data, L, scratch);
+    scan_apply_kernel<T><<<nb, kScanThreads, 0, st>>>(data, L, scratch);
     return launched + 1;
+}
+
+size_t scan_scratch_words(int64_t L)
+{
+    size_t words = 0;
+    while (L > 1) {
+        L = (L + kScanTile - 1) / kScanTile;
+        words += (size_t)L;
+    }
+    return words + 1;
+}
+
+cudaError_t launch_scan_u64(uint64_t *data, int64_t L, uint64_t *scratch, cudaStream_t st, int *launched)
+{
+    const int k = L > 0 ? launch_scan<uint64_t>(data, (int)L, scratch, st) : 0;
+    if (launched)
+        *launched = k;
+    return cudaGetLastError();
 }
 
 size_t sort_scratch_words(int64_t n_max)
@@ -369,7 +390,7 @@ cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32
         const uint32_t *kin = pass == 0 ? key : key_tmp;
         const uint32_t *vin = pass == 0 ? nullptr : val_tmp;
         radix_hist_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, nblk, hist);
-        count += 1 + launch_scan(hist, L, scan_scratch, st);
+        count += 1 + launch_scan<uint32_t>(hist, L, scan_scratch, st);
         radix_scatter_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, nblk, hist,
                                                              last ? nullptr : key_tmp, last ? perm : val_tmp);
         count += 1;
