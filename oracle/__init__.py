@@ -82,6 +82,8 @@ def lib():
             L.orc_antenna.restype = None
             L.orc_delay.argtypes = [vp, dbl, dbl, dbl]
             L.orc_delay.restype = dbl
+            L.orc_av_draw.argtypes = [vp, i64, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, vp, vp]
+            L.orc_av_draw.restype = None
             L.orc_fair_words.argtypes = [C.c_uint64, i64, vp]
             L.orc_fair_words.restype = None
             L.orc_fix_cumulative.argtypes = [vp, i64, vp]

@@ -471,6 +471,50 @@ void orc_adapt(double *P, int B, const int32_t *bins, const double *lnw, int64_t
     free(H);
 }
 
+/* ---------------------------------------------------------------- adaptive-volume draws */
+
+/* Draws of the adaptive-volume integrator (Sec. IV A): uniform over the union of the
+ * active cells of a grid with 2^level cells per side of the unit cube of prior-CDF
+ * coordinates.  A cell's key packs its six integer coordinates, coordinate d in bits
+ * [level d, level (d+1)); cells[] holds the active keys in increasing order.
+ * Random words of draw i in iteration `iter`: Philox4x32-10 with key = seed and counter
+ * (i low, i high, iter, p), p = 0..3; p = 0 words (0,1) give the 53-bit integer U of the
+ * cell choice, the cell being cells[floor(U n_cells / 2^53)]; the remaining word pairs in
+ * order give the six in-cell uniforms.  v_d = (coordinate_d + u_d) / 2^level, and theta
+ * follows from v as for the histogram sampler. */
+void orc_av_draw(const uint64_t *cells, int64_t n_cells, int level, uint64_t seed, uint32_t iter, int64_t i0,
+                 int64_t n, double d_min, double d_max, double *theta, double *v_out)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const double side = ldexp(1.0, level);
+    const uint64_t mask = level > 0 ? ((uint64_t)1 << level) - 1 : 0;
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n; ++s) {
+        const int64_t i = i0 + s;
+        uint32_t w[16];
+        for (uint32_t p = 0; p < 4; ++p) {
+            const uint32_t ctr[4] = {(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p};
+            orc_philox4x32_10(ctr, key, w + 4 * p);
+        }
+        const uint64_t U = ((uint64_t)(w[0] >> 5) << 26) | (uint64_t)(w[1] >> 6);
+        const int64_t c = (int64_t)(((unsigned __int128)U * (uint64_t)n_cells) >> 53);
+        const uint64_t cell = cells[c];
+        double *v = v_out + 6 * s;
+        for (int d = 0; d < 6; ++d) {
+            const double u = orc_u53(w[2 + 2 * d], w[3 + 2 * d]);
+            const double coord = (double)((cell >> (level * d)) & mask);
+            v[d] = (coord + u) / side;
+        }
+        double *th = theta + 6 * s;
+        th[0] = 2.0 * ORC_PI * v[0];
+        th[1] = asin(2.0 * v[1] - 1.0);
+        th[2] = ORC_PI * v[2];
+        th[3] = 2.0 * ORC_PI * v[3];
+        th[4] = acos(1.0 - 2.0 * v[4]);
+        th[5] = cbrt(d_min * d_min * d_min + v[5] * (d_max * d_max * d_max - d_min * d_min * d_min));
+    }
+}
+
 /* ---------------------------------------------------------------- fair draws */
 
 /* The final ILE pass (Sec. II, the closing paragraph of the method overview, and the

@@ -556,3 +556,126 @@ def test_fair_time_bin_follows_a_dominant_bin(orc):
     cum, _ = orc.fix_cumulative(np.zeros(4))
     got = np.bincount([orc.fix_choose(cum, orc.fair_words(3, d)[1]) for d in range(4000)], minlength=4)
     assert np.all(np.abs(got - 1000) < 150)
+
+
+# ------------------------------------------------------------------------------ adaptive volume
+
+def _v_of_theta(th, d_min=100.0, d_max=1000.0):
+    """Prior-CDF coordinates of theta (the inverse of the draw's mapping)."""
+    v = np.empty_like(th)
+    v[:, 0] = th[:, 0] / (2 * np.pi)
+    v[:, 1] = (np.sin(th[:, 1]) + 1) / 2
+    v[:, 2] = th[:, 2] / np.pi
+    v[:, 3] = th[:, 3] / (2 * np.pi)
+    v[:, 4] = (1 - np.cos(th[:, 4])) / 2
+    v[:, 5] = (th[:, 5] ** 3 - d_min ** 3) / (d_max ** 3 - d_min ** 3)
+    return v
+
+
+def test_av_draws_are_uniform_in_the_active_cells(orc):
+    """Draws land only in active cells, equally often in each, and their theta is the
+    prior mapping of v."""
+    from oracle import av as A
+    a = A.AV(seed=4)
+    a.level = 2
+    a.cells = np.array(sorted({int(k) for k in A.cell_keys(np.random.default_rng(0).random((5, 6)), 2)}), np.uint64)
+    th, v = a.draw(40000)
+    keys = A.cell_keys(v, 2)
+    assert set(np.unique(keys)) <= set(a.cells.tolist())
+    counts = np.array([np.sum(keys == c) for c in a.cells])
+    assert np.all(np.abs(counts - 40000 / a.cells.size) < 5 * np.sqrt(40000 / a.cells.size))
+    assert np.allclose(_v_of_theta(th), v, atol=1e-9)
+
+
+def test_av_threshold_rule_against_sorted_definition(orc):
+    """The histogram threshold keeps every point of the exact sort-based rule (the
+    fewest top points holding P_thr of the mass, or N_min* points) and at most the
+    rest of the 1/64-wide bin where that rule stops."""
+    from oracle import av as A
+    rng = np.random.default_rng(2)
+    for p_thr, nstar in ((0.999, 1000), (0.9, 50), (0.99999, 10)):
+        lnL = rng.normal(0, 4, 5000)
+        m, b_thr, kept = A.threshold(lnL, p_thr, nstar)
+        order = np.argsort(-lnL)
+        w = np.exp(lnL[order] - m)
+        frac = np.cumsum(w) / w.sum()
+        k_mass = int(np.searchsorted(frac, np.floor(p_thr * 2 ** 20) / 2 ** 20 * (1 - 1e-12))) + 1
+        k = min(k_mass, nstar)
+        exact = np.zeros(lnL.size, bool)
+        exact[order[:k]] = True
+        assert np.all(kept[exact])
+        last = lnL[order[k - 1]]
+        assert np.all(lnL[kept] >= last - 1.0 / 64)
+
+
+def test_av_uniform_target_is_exact(orc):
+    """ln L = 0: every iteration keeps all points, every cell of the chosen level stays
+    active, V = 1 and ln Z = 0 exactly."""
+    from oracle import av as A
+    res = A.run(lambda th: np.zeros(th.shape[0]), 4, 50000, seed=5)
+    for r in res["iterations"]:
+        assert r["V"] == 1.0 and r["reduce"]["lnZ"] == 0.0
+    assert res["iterations"][-1]["level"] >= 1
+
+
+def test_av_box_target_is_exact(orc):
+    """L = 1 on a box that is one cell of the level-2 grid, negligible elsewhere:
+    after one refinement the active region is exactly that box (one level-2 cell, or
+    all its sub-cells once the grid refines further) and ln Z = ln(4^-6) exactly."""
+    from oracle import av as A
+    lo = np.array([1, 2, 1, 3, 0, 2]) / 4.0
+
+    def lnL(th):
+        v = _v_of_theta(th)
+        inside = np.all((v >= lo) & (v < lo + 0.25), 1)
+        return np.where(inside, 0.0, -200.0)
+
+    res = A.run(lnL, 3, 200000, seed=6)
+    its = res["iterations"]
+    for r in its[1:]:
+        assert r["level"] >= 2 and r["n_cells"] == 64 ** (r["level"] - 2)
+        assert r["V"] == 4.0 ** -6
+        assert r["reduce"]["lnZ"] == pytest.approx(-6 * math.log(4.0), abs=1e-12)
+
+
+def test_av_refinement_formula_and_nesting(orc):
+    """n_bins = (1/dV)^(1/6) rounded down to a power of two, never coarser; refined
+    cells lie inside cells that were active."""
+    from oracle import av as A
+    assert A.next_level(0, 1.0, 100, 10000) == int(math.floor(math.log2((1 / (0.01 / 10)) ** (1 / 6))))
+    assert A.next_level(3, 1.0, 100, 10000) == 3
+    assert A.next_level(0, 1e-30, 100, 100) == A.MAX_LEVEL
+    mu, sig = np.array([0.3, 0.6, 0.45, 0.55, 0.4, 0.7]), 0.05
+
+    def lnL(th):
+        return -np.sum((_v_of_theta(th) - mu) ** 2, 1) / (2 * sig ** 2)
+
+    a = A.AV(seed=7, n_min_star=200)
+    for _ in range(4):
+        old_level, old_cells = a.level, set(a.cells.tolist())
+        a.step(lnL, 50000)
+        if a.level >= old_level:
+            shift = a.level - old_level
+            c = a.cells.astype(np.uint64)
+            parent = np.zeros_like(c)
+            for d in range(6):
+                coord = (c >> np.uint64(a.level * d)) & np.uint64((1 << a.level) - 1)
+                parent |= (coord >> np.uint64(shift)) << np.uint64(old_level * d)
+            assert set(parent.tolist()) <= old_cells
+
+
+def test_av_gaussian_target(orc):
+    """A 6-D Gaussian well inside one level-3 cell on every axis (sigma = 0.01):
+    each refined iteration's ln Z is within 4 sigma + 1e-3 of the analytic integral."""
+    from oracle import av as A
+    mu, sig = np.array([0.3125, 0.5625, 0.4375, 0.6875, 0.1875, 0.8125]), 0.01
+
+    def lnL(th):
+        return -np.sum((_v_of_theta(th) - mu) ** 2, 1) / (2 * sig ** 2)
+
+    truth = 3 * math.log(2 * math.pi * sig ** 2)
+    res = A.run(lnL, 6, 100000, seed=8, n_min_star=300)
+    late = res["iterations"][3:]
+    assert all(r["level"] >= 2 for r in late)
+    for r in late:
+        assert abs(r["reduce"]["lnZ"] - truth) < 4 * r["reduce"]["sigma_lnZ"] + 1e-3, (r["reduce"], truth)
