@@ -555,6 +555,21 @@ def run_high_snr(args, rank, world, local_rank):
     t0 = time.perf_counter()
     fth, ft, fidx = ile.fair_draws(10000, seed=17)
     fair_ms = 1e3 * (time.perf_counter() - t0)
+    # the adaptive-volume integrator on the same problem and budget (10 x n, MIXED)
+    av_res = None
+    if not args.quick:
+        with G.ILE(prob, precision=G.RIFT_MIXED, max_samples=n, n_bins=64, seed=1 + rank, stream=stream) as sav:
+            sav.av(2, n, restart=True)   # warm-up (allocation, kernels)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ra = sav.av(n_iter, n, restart=True)
+            torch.cuda.synchronize()
+            av_ms = 1e3 * (time.perf_counter() - t0)
+            info = sav.av_info()
+        av_res = {"ms_per_step": av_ms, "sample_evals_per_s": n * n_iter / (av_ms / 1e3), "lnZ": ra["lnZ"],
+                  "sigma_lnZ": ra["sigma_lnZ"], "n_eff": ra["n_eff"], "n_eff_iter": ra["n_eff_iter"],
+                  "lnZ_iter": ra["lnZ_iter"], "final_level": info["level"], "final_cells": info["n_cells"],
+                  "final_volume": info["V"], "p_thr": 0.9999, "n_min_star": 1000}
     # error of the last batch against the float64 path (1e-9 parity with the oracle):
     # every sample within 30 of the largest ln w, plus 4096 others
     th, lr, ll, lw = ile.last_batch(n)
@@ -595,6 +610,7 @@ def run_high_snr(args, rank, world, local_rank):
         "result": {"lnZ": r["lnZ"], "sigma_lnZ": r["sigma_lnZ"], "n_eff": r["n_eff"], "n_ess": r["n_ess"],
                    "lnL_max": r["lnL_max"], "n_eff_iter": r["n_eff_iter"], "lnZ_iter": r["lnZ_iter"]},
         "error_vs_fp64": err,
+        "adaptive_volume": av_res,
         "fair_draws": {"draws": 10000, "ms": fair_ms, "distinct_samples": int(len(np.unique(fidx))),
                        "t_spread_ms": float(1e3 * np.std(ft))},
         "stage_ms_per_step": {"draw_sort": r["time_ms"][0], "lnl_refine": r["time_ms"][1],

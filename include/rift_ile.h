@@ -192,6 +192,36 @@ int rift_ile_get_plan(const rift_ile_t *h, int32_t *lnl_kernel, int32_t *samples
 int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus_lnps, double *lnL_tmarg,
                         double *lnw, int64_t *n_out);
 
+/* Adaptive-volume integrator (arXiv:2505.11655 Sec. IV A, the paper's recommended ILE
+ * integrator), an alternative to rift_ile_adapt's histogram sampler.  It works on the unit
+ * cube of prior-CDF coordinates (the same coordinates the histogram sampler draws through)
+ * with nested grids of 2^level cells per side (level <= 10):
+ *   1. n_per_iter draws uniform over the active cells (ln p - ln p_s = ln V, V their volume);
+ *   2. time-marginalised ln L in the handle's precision;
+ *   3. the draws passing the current threshold join the live set (draw order, at most
+ *      `capacity` live points);
+ *   4. the threshold keeps the fewest top 1/64-wide ln L bins (below the live maximum)
+ *      holding the fraction p_thr of the live mass or n_min_star points, whichever comes
+ *      first; masses are exact fixed-point integers;
+ *   5. refinement: V' = V N_min / N_live, dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6)
+ *      (Eq. nbins_V) rounded down to a power of two and never coarser; the new active
+ *      cells are the cells holding a kept live point.
+ * Draw i of AV iteration g uses Philox4x32-10 with key = seed and counter
+ * (i low, i high, g, p), p = 0..3: the first word pair chooses the cell (first of the
+ * sorted active cells at floor(U n_cells / 2^53)), the next six the in-cell uniforms.
+ * Results pool every iteration's draws (ln w = ln L + ln V) like rift_ile_adapt; the last
+ * iteration's draws are the handle's most recent batch (rift_ile_last_batch,
+ * rift_ile_fair_draws).  restart = 1 (or the first call) starts from the whole cube; the
+ * live set's device memory (about 130 B per point of `capacity`) is allocated by the
+ * first call and `capacity` cannot change afterwards (RIFT_EINVAL).
+ * RIFT_EINVAL for n_iter outside 1..RIFT_MAX_ITER, n_per_iter outside 1..max_samples,
+ * p_thr outside (0, 1], n_min_star < 1, capacity < n_per_iter or >= 2^31 - 2. */
+int rift_ile_av(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, double p_thr, int64_t n_min_star,
+                int64_t capacity, int32_t restart, rift_ile_result *out);
+/* State of the adaptive-volume integrator after the last call: grid level, active cells,
+ * live points, active volume.  Any output may be NULL. */
+int rift_ile_av_info(const rift_ile_t *h, int32_t *level, int64_t *n_cells, int64_t *n_live, double *volume);
+
 /* Fair draws from the most recent batch (the final ILE pass: extrinsic samples drawn
  * fairly from the Monte Carlo integral's weighted samples, arXiv:2505.11655 Sec. II;
  * the two-step fair draw of Sec. II D).  Draw d takes sample i, with replacement, with

@@ -31,7 +31,7 @@ RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_get_plan", "rift_ile_fair_draws", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_ile_get_plan", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
             "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = False):
     L.rift_srv_destroy.restype = None
     L.rift_ile_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     L.rift_ile_fair_draws.argtypes = [vp, i64, C.c_uint64, C.c_int, vp, vp, vp]
+    L.rift_ile_av.argtypes = [vp, i32, i64, C.c_double, i64, i64, i32, C.POINTER(rift_ile_result)]
+    L.rift_ile_av_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]
     L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
     L.rift_batch_run.argtypes = [vp, C.POINTER(rift_ile_result)]
     L.rift_batch_kernel_launches.argtypes = [vp]
@@ -291,6 +293,19 @@ def rift_ile_fair_draws(h, n_draws, seed, theta=None, t=None, index=None):
     mem = _mem(bufs[0]) if bufs else RIFT_MEM_HOST
     _check(load().rift_ile_fair_draws(h, int(n_draws), int(seed), mem, _ptr(theta), _ptr(t), _ptr(index)),
            "rift_ile_fair_draws")
+
+
+def rift_ile_av(h, n_iter, n_per_iter, p_thr, n_min_star, capacity, restart):
+    r = rift_ile_result()
+    _check(load().rift_ile_av(h, int(n_iter), int(n_per_iter), float(p_thr), int(n_min_star), int(capacity),
+                              int(restart), C.byref(r)), "rift_ile_av")
+    return r
+
+
+def rift_ile_av_info(h):
+    lv, nc, nl, V = C.c_int32(), C.c_int64(), C.c_int64(), C.c_double()
+    _check(load().rift_ile_av_info(h, C.byref(lv), C.byref(nc), C.byref(nl), C.byref(V)), "rift_ile_av_info")
+    return dict(level=lv.value, n_cells=nc.value, n_live=nl.value, V=V.value)
 
 
 def rift_batch_create(handles, n_iter, n_per_iter, stream=None):
@@ -500,6 +515,14 @@ class ILE:
 
     def kernel_launches(self):
         return rift_ile_kernel_launches(self.h)
+
+    def av(self, n_iter, n_per_iter, p_thr=0.9999, n_min_star=1000, capacity=None, restart=False):
+        """Adaptive-volume iterations (rift_ile_av); capacity defaults to 4 n_per_iter."""
+        cap = 4 * n_per_iter if capacity is None else capacity
+        return rift_ile_av(self.h, n_iter, n_per_iter, p_thr, n_min_star, cap, 1 if restart else 0).as_dict()
+
+    def av_info(self):
+        return rift_ile_av_info(self.h)
 
     def fair_draws(self, n_draws, seed=1):
         """Fair draws from the most recent batch: (theta [n][6], t [n], index [n])."""

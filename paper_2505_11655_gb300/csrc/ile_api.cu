@@ -55,18 +55,6 @@ void keep_pool_cached()
     });
 }
 
-template <typename T> int dalloc(rift_ile_t *h, T **p, size_t count)
-{
-    void *q = nullptr;
-    if (cudaMallocAsync(&q, count * sizeof(T) + 16, h->stream) != cudaSuccess) {
-        cudaGetLastError();
-        return RIFT_ENOMEM;
-    }
-    h->allocs.push_back(q);
-    *p = static_cast<T *>(q);
-    return RIFT_OK;
-}
-
 void release(rift_ile_t *h)
 {
     if (!h)
@@ -234,7 +222,7 @@ __global__ void prep_overlaps_kernel(const double2 *__restrict__ Q64, const doub
     }
 }
 
-int sync_and_err(rift_ile_t *h, int *flags_out = nullptr)
+int sync_and_err(rift_ile_t *h, int *flags_out)
 {
     int flags = 0;
     CK(cudaMemcpyAsync(&h->host_out[0], h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -274,7 +262,6 @@ cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *
 // RIFT_MIXED: samples whose log-weight is within kMixedMargin of the batch maximum
 // are re-evaluated in float64 (their weight relative to the largest is >= e^-40).
 constexpr double kMixedMargin = 40.0;
-constexpr int kScratchSlot = RIFT_MAX_ITER;
 
 int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, const double *lnpw, double *lnw)
 {

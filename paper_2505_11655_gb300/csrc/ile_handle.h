@@ -69,6 +69,25 @@ struct rift_ile {
     int32_t last_shape_iter = 0;   // shape of the previous direct adapt call
     int64_t last_shape_n = 0;
     std::vector<void *> allocs;
+    // adaptive-volume integrator state (allocated by the first rift_ile_av call)
+    struct AVState {
+        int64_t cap = 0;             // live-set capacity
+        int level = 0;               // 2^level cells per side
+        int64_t n_cells = 1;
+        double V = 1.0;              // volume of the active cells
+        int64_t n_live = 0;
+        bool has_thr = false;        // threshold (m, b): keep floor((m - ln L) 64) <= b
+        double m = 0.0;
+        int b = 0;
+        uint32_t iter = 0;
+        double *v = nullptr, *lnL = nullptr, *v2 = nullptr, *lnL2 = nullptr;   // live set, ping-pong
+        double *v_fresh = nullptr;                                               // [max_samples][6]
+        uint64_t *cells = nullptr, *keys = nullptr, *keys_tmp = nullptr;
+        uint32_t *flags = nullptr, *scan = nullptr, *sort = nullptr;
+        uint64_t *mass_part = nullptr, *mass = nullptr;
+        uint32_t *count_part = nullptr, *count = nullptr;
+        unsigned long long *maxbits = nullptr;
+    } av;
 };
 
 #define CK(call)                                                                                                        \
@@ -112,6 +131,22 @@ int grid_for_batch(rift_ile_t *h, int64_t n);
 cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
                          const double *lnpw, double *lnw);
 void drop_graph(rift_ile_t *h);
+cudaError_t mark(rift_ile_t *h, int slot, int stage);
+int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, const double *lnpw, double *lnw);
+int sync_and_err(rift_ile_t *h, int *flags_out = nullptr);
+// Device buffer from the stream-ordered pool on the handle's stream, freed at destroy.
+template <typename T> int dalloc(rift_ile_t *h, T **p, size_t count)
+{
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, count * sizeof(T) + 16, h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return RIFT_ENOMEM;
+    }
+    h->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return RIFT_OK;
+}
+constexpr int kScratchSlot = RIFT_MAX_ITER;
 
 }  // namespace host
 }  // namespace rift

@@ -118,6 +118,13 @@ cudaError_t launch_keys(const SkyGrid &G, const double *theta, int64_t n, uint32
 constexpr int kRadixBits = 10;
 constexpr int kRadixBuckets = 1 << kRadixBits;
 size_t sort_scratch_words(int64_t n_max);
+// Stable ascending sort of 64-bit keys in place (the low `bits` bits; tmp holds n keys,
+// scratch sort64_scratch_words(n) words).
+size_t sort64_scratch_words(int64_t n_max);
+cudaError_t launch_sort64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, uint32_t *scratch, cudaStream_t st,
+                          int *launched = nullptr);
+// Exclusive scan of 32-bit counts in place (L < 2^31); scratch holds scan_scratch_words(L).
+cudaError_t launch_scan_u32(uint32_t *data, int64_t L, uint32_t *scratch, cudaStream_t st, int *launched = nullptr);
 // Exclusive scan of 64-bit counts in place (L < 2^31); scratch holds scan_scratch_words(L).
 size_t scan_scratch_words(int64_t L);
 cudaError_t launch_scan_u64(uint64_t *data, int64_t L, uint64_t *scratch, cudaStream_t st, int *launched = nullptr);

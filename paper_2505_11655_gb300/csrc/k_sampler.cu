@@ -159,7 +159,8 @@ constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixPerWarp = 1024;
 constexpr int kRadixTile = kRadixWarps * kRadixPerWarp;
 
-__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t n,
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const K *__restrict__ keys, int64_t n,
                                                                    int shift, int nblk, uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t h[kRadixBuckets];
@@ -170,18 +171,19 @@ __global__ void __launch_bounds__(kRadixThreads) radix_hist_kernel(const uint32_
     for (int j = threadIdx.x; j < kRadixTile; j += kRadixThreads) {
         const int64_t i = base + j;
         if (i < n)
-            atomicAdd(&h[(keys[i] >> shift) & (kRadixBuckets - 1)], 1u);
+            atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kRadixBuckets - 1)], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kRadixBuckets; d += kRadixThreads)
         hist[(size_t)d * nblk + blockIdx.x] = h[d];
 }
 
-__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint32_t *__restrict__ keys_in,
+template <typename K>
+__global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const K *__restrict__ keys_in,
                                                                       const uint32_t *__restrict__ vals_in, int64_t n,
                                                                       int shift, int nblk,
                                                                       const uint32_t *__restrict__ offsets,
-                                                                      uint32_t *__restrict__ keys_out,
+                                                                      K *__restrict__ keys_out,
                                                                       uint32_t *__restrict__ vals_out)
 {
     __shared__ uint32_t wpos[kRadixWarps][kRadixBuckets];   // per-warp digit counts, then positions
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint
     for (int j = lane; j < kRadixPerWarp; j += 32) {
         const int64_t i = base + j;
         if (i < n)
-            atomicAdd(&wpos[w][(keys_in[i] >> shift) & (kRadixBuckets - 1)], 1u);
+            atomicAdd(&wpos[w][(uint32_t)(keys_in[i] >> shift) & (kRadixBuckets - 1)], 1u);
     }
     __syncthreads();
     // first position of each digit for each warp: the tile's offset, then warps in order
@@ -210,12 +212,13 @@ __global__ void __launch_bounds__(kRadixThreads) radix_scatter_kernel(const uint
     for (int j0 = 0; j0 < kRadixPerWarp && base + j0 < n; j0 += 32) {
         const int64_t i = base + j0 + lane;
         const bool ok = i < n;
-        const uint32_t k = ok ? keys_in[i] : 0u;
-        const uint32_t d = ok ? (k >> shift) & (kRadixBuckets - 1) : 0xffffffffu;
+        const K k = ok ? keys_in[i] : (K)0;
+        const uint32_t d = ok ? (uint32_t)(k >> shift) & (kRadixBuckets - 1) : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (ok) {
             const uint32_t pos = wpos[w][d] + __popc(peers & ((1u << lane) - 1u));
-            vals_out[pos] = vals_in ? vals_in[i] : (uint32_t)i;
+            if (vals_out)
+                vals_out[pos] = vals_in ? vals_in[i] : (uint32_t)i;
             if (keys_out)
                 keys_out[pos] = k;
         }
@@ -389,14 +392,67 @@ cudaError_t launch_sort(const SkyGrid &G, const uint32_t *key, int64_t n, uint32
         const bool last = pass == passes - 1;
         const uint32_t *kin = pass == 0 ? key : key_tmp;
         const uint32_t *vin = pass == 0 ? nullptr : val_tmp;
-        radix_hist_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, nblk, hist);
+        radix_hist_kernel<uint32_t><<<nblk, kRadixThreads, 0, st>>>(kin, n, shift, nblk, hist);
         count += 1 + launch_scan<uint32_t>(hist, L, scan_scratch, st);
-        radix_scatter_kernel<<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, nblk, hist,
-                                                             last ? nullptr : key_tmp, last ? perm : val_tmp);
+        radix_scatter_kernel<uint32_t><<<nblk, kRadixThreads, 0, st>>>(kin, vin, n, shift, nblk, hist,
+                                                                       last ? nullptr : key_tmp, last ? perm : val_tmp);
         count += 1;
     }
     if (launched)
         *launched = count;
+    return cudaGetLastError();
+}
+
+size_t sort64_scratch_words(int64_t n_max)
+{
+    const int64_t nblk = (n_max + kRadixTile - 1) / kRadixTile;
+    int64_t L = (int64_t)kRadixBuckets * (nblk > 0 ? nblk : 1), words = L;
+    while (L > 1) {
+        L = (L + kScanTile - 1) / kScanTile;
+        words += L;
+    }
+    return (size_t)(words + 64);
+}
+
+cudaError_t launch_sort64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, uint32_t *scratch, cudaStream_t st,
+                          int *launched)
+{
+    if (launched)
+        *launched = 0;
+    if (n <= 0)
+        return cudaSuccess;
+    const int nblk = (int)((n + kRadixTile - 1) / kRadixTile);
+    const int L = kRadixBuckets * nblk;
+    uint32_t *hist = scratch, *scan_scratch = scratch + L;
+    const int passes = bits <= 0 ? 0 : (bits + kRadixBits - 1) / kRadixBits;
+    int count = 0;
+    uint64_t *in = keys, *out = tmp;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = pass * kRadixBits;
+        radix_hist_kernel<uint64_t><<<nblk, kRadixThreads, 0, st>>>(in, n, shift, nblk, hist);
+        count += 1 + launch_scan<uint32_t>(hist, L, scan_scratch, st);
+        radix_scatter_kernel<uint64_t><<<nblk, kRadixThreads, 0, st>>>(in, nullptr, n, shift, nblk, hist, out,
+                                                                       nullptr);
+        count += 1;
+        uint64_t *t = in;
+        in = out;
+        out = t;
+    }
+    if (in != keys) {   // odd number of passes: the sorted keys are in tmp
+        cudaError_t e = cudaMemcpyAsync(keys, in, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    if (launched)
+        *launched = count;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_u32(uint32_t *data, int64_t L, uint32_t *scratch, cudaStream_t st, int *launched)
+{
+    const int k = L > 0 ? launch_scan<uint32_t>(data, (int)L, scratch, st) : 0;
+    if (launched)
+        *launched = k;
     return cudaGetLastError();
 }
 
