@@ -240,16 +240,18 @@ def make_problem(det_names=("H1", "L1"), n_modes=2, fs=4096.0, window=0.2, t_lo=
     U = np.zeros((K, M, M), complex)
     V = np.zeros((K, M, M), complex)
     noise_rng = np.random.default_rng(seed + 7919)
+    data = np.zeros((K, wf.freqs.size), complex)
     for k in range(K):
         d = wf.strain(a_true[k], t_true + dt_true[k])
         if noise:
             d = d + wf.noise(k, noise_rng)
+        data[k] = d
         times = q_t0[k] + np.arange(n_q) / fs
         Q[k] = wf.overlap_series(k, d, times)
         U[k], V[k] = wf.gram(k)
     d_ref = scale * d_true if scale > 0 else d_true
     meta = dict(seed=seed, snr=snr, a_true=a_true, dt_true=dt_true, t_true=t_true, d_true=d_true,
-                scale=scale, noise=noise, waveforms=wf)
+                scale=scale, noise=noise, waveforms=wf, data=data)
     return Problem(list(det_names), tens, pos, float(gmst), lm, float(fs), int(n_q), q_t0, Q, U, V,
                    float(t_lo), float(t_hi), int(n_t), float(d_ref), float(d_min), float(d_max),
                    int(quad_norm), meta)

@@ -679,3 +679,53 @@ def test_av_gaussian_target(orc):
     assert all(r["level"] >= 2 for r in late)
     for r in late:
         assert abs(r["reduce"]["lnZ"] - truth) < 4 * r["reduce"]["sigma_lnZ"] + 1e-3, (r["reduce"], truth)
+
+
+# ------------------------------------------------------------------------------ Q, U, V from waveforms
+
+def test_overlaps_identities(orc):
+    """Q, U, V from the frequency-domain inputs: U Hermitian, V symmetric, and for
+    noise-free data of mode amplitudes a arriving at t_arr, Q(t_arr) = 1/2 (U a +
+    conj(V) conj(a)) exactly (the data's transform is 1/2 sum a h + conj(a) conj(h(-f)))."""
+    from oracle import precompute as PC
+    p = S.make_problem(("H1", "V1"), 5, 4096.0, snr=20.0, noise=False, seed=61)
+    wf, data = p.meta["waveforms"], p.meta["data"]
+    Q, U, V = PC.overlaps(wf.freqs, wf.h, data, wf.w, p.q_t0, p.fs, p.n_q)
+    assert np.allclose(U, np.conj(np.transpose(U, (0, 2, 1))), atol=1e-12)
+    assert np.allclose(V, np.transpose(V, (0, 2, 1)), atol=1e-12)
+    a = p.meta["a_true"]
+    for k in range(2):
+        t_arr = p.meta["t_true"] + p.meta["dt_true"][k]
+        t = np.array([t_arr])
+        phase = np.exp(2j * np.pi * np.outer(t, wf.freqs))
+        q_arr = 2.0 * (phase @ (wf.w[k] * np.conj(wf.h) * data[k]).T)[0]
+        assert np.allclose(q_arr, 0.5 * (U[k] @ a[k] + np.conj(V[k]) @ np.conj(a[k])), rtol=1e-11, atol=1e-11)
+    # the decomposed likelihood built from these overlaps is <h|d> - 1/2 <h|h>
+    rng = np.random.default_rng(3)
+    c = rng.normal(size=(2, 5)) + 1j * rng.normal(size=(2, 5))
+    q_at = [Q[k, :, 0] for k in range(2)]
+    lin = sum(np.real(np.vdot(c[k], q_at[k])) for k in range(2))
+    quad = 0.25 * sum(np.real(np.vdot(c[k], U[k] @ c[k])) + np.real(c[k] @ V[k] @ c[k]) for k in range(2))
+    t0 = np.array(p.q_t0)
+    direct = 0.0
+    for k in range(2):
+        hk = wf.strain(c[k], t0[k])   # template arriving at Q sample 0
+        direct += np.real(wf.inner(k, hk, data[k])) - 0.5 * np.real(wf.inner(k, hk, hk))
+    assert lin - quad == pytest.approx(direct, rel=1e-10, abs=1e-9)
+
+
+def test_overlaps_single_line_closed_form(orc):
+    """One frequency line (and its mirror) in the data and one mode: Q is the closed-form
+    sinusoid 2 w conj(h) d exp(2 pi i f t) summed over the two lines."""
+    from oracle import precompute as PC
+    f = np.array([-10.0, -6.0, 6.0, 10.0])
+    h = np.array([[0.0, 1.0 + 0.5j, 0.2 - 0.1j, 0.0]])
+    d = np.array([[0.0, 0.3 - 0.7j, 0.3 + 0.7j, 0.0]])
+    w = np.array([[1.0, 1.5, 1.5, 1.0]])
+    Q, U, V = PC.overlaps(f, h, d, w, np.array([-0.1]), 100.0, 50)
+    t = -0.1 + np.arange(50) / 100.0
+    exp = 2 * 1.5 * (np.conj(h[0, 1]) * d[0, 1] * np.exp(2j * np.pi * -6.0 * t)
+                     + np.conj(h[0, 2]) * d[0, 2] * np.exp(2j * np.pi * 6.0 * t))
+    assert np.allclose(Q[0, 0], exp, atol=1e-13)
+    assert U[0, 0, 0] == pytest.approx(2 * 1.5 * (abs(h[0, 1]) ** 2 + abs(h[0, 2]) ** 2))
+    assert V[0, 0, 0] == pytest.approx(2 * 1.5 * 2 * h[0, 1] * h[0, 2])
