@@ -149,6 +149,27 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
  * their largest entry (Sec. V A symmetry relations); RIFT_ENONFINITE on NaN/Inf. */
 int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const void *V, int mem);
 
+/* Overlaps from frequency-domain inputs, computed on the device (Sec. II A, Eq. QUV; the
+ * precompute stage the paper runs on the CPU): on a two-sided grid of n_freq frequencies
+ * f_j, mirror symmetric (f[n_freq-1-j] == -f[j] exactly), with inverse-PSD weights
+ * w_k(f) symmetric in f,
+ *   Q_k,lm(t_s)  = 2 sum_j w_k(f_j) exp(2 pi i f_j t_s) conj(h_lm(f_j)) d_k(f_j),
+ *                  t_s = q_t0_s[k] + s / fs_hz, s = 0 .. n_q - 1,
+ *   U_k,lm,l'm'  = 2 sum_j w_k conj(h_lm) h_l'm',  V_k,lm,l'm' = 2 sum_j w_k h_lm(-f_j) h_l'm'(f_j)
+ * (only lm <= l'm' is summed; U is mirrored Hermitian, V symmetric), then installed as
+ * rift_ile_set_overlaps would install them.  All in float64.
+ *   freqs [n_freq] (Hz), hlm [n_modes][n_freq] complex128 (mode waveforms shared by the
+ *   detectors), data [n_det][n_freq] complex128, weights [n_det][n_freq]; all in `mem`,
+ *   read during the call (scratch about 16 n_det n_modes n_freq bytes from the pool).
+ * RIFT_EINVAL for a grid that is not mirror symmetric or weights that are negative or not
+ * symmetric; RIFT_ENONFINITE for non-finite weights or overlaps. */
+int rift_ile_set_waveforms(rift_ile_t *h, int32_t n_freq, const double *freqs, const void *hlm, const void *data,
+                           const double *weights, int mem);
+
+/* Copy the installed float64 overlaps out: Q [n_det][n_modes][n_q], U, V [n_det][n_modes]
+ * [n_modes] complex128 in `mem` (any may be NULL).  RIFT_ESTATE before overlaps are set. */
+int rift_ile_get_overlaps(const rift_ile_t *h, void *Q, void *U, void *V, int mem);
+
 /* Evaluate n samples theta [n][6] = (alpha, delta, psi, phi, iota, D):
  *   lnL_tmarg [n]      time-marginalised ln L = ln( (1/n_t) sum_j exp(ln L(theta, t_j)) )
  *   lnL_t [n][n_t]     ln L at every bin, or NULL

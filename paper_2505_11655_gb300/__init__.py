@@ -28,7 +28,7 @@ RIFT_FP64, RIFT_FP32, RIFT_MIXED = 0, 1, 2
 RIFT_MAX_ITER = 64
 RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 
-EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
+EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_set_waveforms", "rift_ile_get_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
             "rift_ile_get_plan", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = False):
     L.rift_srv_destroy.restype = None
     L.rift_ile_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     L.rift_ile_fair_draws.argtypes = [vp, i64, C.c_uint64, C.c_int, vp, vp, vp]
+    L.rift_ile_set_waveforms.argtypes = [vp, i32, vp, vp, vp, vp, C.c_int]
+    L.rift_ile_get_overlaps.argtypes = [vp, vp, vp, vp, C.c_int]
     L.rift_ile_av.argtypes = [vp, i32, i64, C.c_double, i64, i64, i32, C.POINTER(rift_ile_result)]
     L.rift_ile_av_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]
     L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
@@ -286,6 +288,17 @@ def rift_ile_get_plan(h):
     k, c = C.c_int32(), C.c_int32()
     _check(load().rift_ile_get_plan(h, C.byref(k), C.byref(c)), "rift_ile_get_plan")
     return k.value, c.value
+
+
+def rift_ile_set_waveforms(h, freqs, hlm, data, weights):
+    _check(load().rift_ile_set_waveforms(h, int(freqs.shape[0]), _ptr(freqs), _ptr(hlm), _ptr(data), _ptr(weights),
+                                         _mem(freqs)), "rift_ile_set_waveforms")
+
+
+def rift_ile_get_overlaps(h, Q=None, U=None, V=None):
+    bufs = [b for b in (Q, U, V) if b is not None]
+    mem = _mem(bufs[0]) if bufs else RIFT_MEM_HOST
+    _check(load().rift_ile_get_overlaps(h, _ptr(Q), _ptr(U), _ptr(V), mem), "rift_ile_get_overlaps")
 
 
 def rift_ile_fair_draws(h, n_draws, seed, theta=None, t=None, index=None):
@@ -479,6 +492,21 @@ class ILE:
         if isinstance(Q, np.ndarray):
             Q, U, V = (np.ascontiguousarray(x, np.complex128) for x in (Q, U, V))
         rift_ile_set_overlaps(self.h, Q, U, V)
+
+    def set_waveforms(self, freqs, hlm, data, weights):
+        """Q, U, V computed on the device from frequency-domain inputs (numpy or torch)."""
+        if isinstance(freqs, np.ndarray):
+            freqs = np.ascontiguousarray(freqs, np.float64)
+            hlm, data = (np.ascontiguousarray(x, np.complex128) for x in (hlm, data))
+            weights = np.ascontiguousarray(weights, np.float64)
+        rift_ile_set_waveforms(self.h, freqs, hlm, data, weights)
+
+    def get_overlaps(self, n_q):
+        Q = np.empty((self.n_det, self.n_modes, n_q), np.complex128)
+        U = np.empty((self.n_det, self.n_modes, self.n_modes), np.complex128)
+        V = np.empty_like(U)
+        rift_ile_get_overlaps(self.h, Q, U, V)
+        return Q, U, V
 
     def eval(self, theta, want_bins=False):
         if isinstance(theta, np.ndarray):

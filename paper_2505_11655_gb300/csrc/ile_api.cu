@@ -706,6 +706,93 @@ int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const voi
     CK(cudaMemcpyAsync(h->Q64, Q, qb, kind, h->stream));
     CK(cudaMemcpyAsync(h->U64, U, gb, kind, h->stream));
     CK(cudaMemcpyAsync(h->V64, V, gb, kind, h->stream));
+    return install_overlaps(h);
+}
+
+int rift_ile_set_waveforms(rift_ile_t *h, int32_t n_freq, const double *freqs, const void *hlm, const void *data,
+                           const double *weights, int mem)
+{
+    if (!h || n_freq < 2 || !freqs || !hlm || !data || !weights || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    const int K = h->prob.K, M = h->prob.M, F = n_freq;
+    const size_t fb = sizeof(double) * F, hb = sizeof(double2) * (size_t)M * F, db = sizeof(double2) * (size_t)K * F,
+                 wb = sizeof(double) * (size_t)K * F;
+    // host checks: mirror-symmetric grid, weights finite, non-negative and symmetric in f
+    std::vector<double> hf(F), hw((size_t)K * F);
+    const cudaMemcpyKind to_host = mem == RIFT_MEM_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(hf.data(), freqs, fb, to_host, h->stream));
+    CK(cudaMemcpyAsync(hw.data(), weights, wb, to_host, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int j = 0; j < F; ++j) {
+        if (!std::isfinite(hf[j]) || hf[F - 1 - j] != -hf[j])
+            return RIFT_EINVAL;
+        for (int k = 0; k < K; ++k) {
+            const double a = hw[(size_t)k * F + j];
+            if (!std::isfinite(a))
+                return RIFT_ENONFINITE;
+            if (a < 0.0 || a != hw[(size_t)k * F + (F - 1 - j)])
+                return RIFT_EINVAL;
+        }
+    }
+    std::vector<void *> tmp;
+    auto grab = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMallocAsync(&q, bytes, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        tmp.push_back(q);
+        return q;
+    };
+    auto A = static_cast<double2 *>(grab(sizeof(double2) * (size_t)K * M * F));
+    auto t0 = static_cast<double *>(grab(sizeof(double) * K));
+    const double *df = freqs, *dw = weights;
+    const double2 *dh = static_cast<const double2 *>(hlm), *dd = static_cast<const double2 *>(data);
+    int rc = (A && t0) ? RIFT_OK : RIFT_ENOMEM;
+    if (rc == RIFT_OK && mem == RIFT_MEM_HOST) {
+        auto f2 = static_cast<double *>(grab(fb));
+        auto h2 = static_cast<double2 *>(grab(hb));
+        auto d2 = static_cast<double2 *>(grab(db));
+        auto w2 = static_cast<double *>(grab(wb));
+        if (!f2 || !h2 || !d2 || !w2)
+            rc = RIFT_ENOMEM;
+        else if (cudaMemcpyAsync(f2, freqs, fb, cudaMemcpyHostToDevice, h->stream) ||
+                 cudaMemcpyAsync(h2, hlm, hb, cudaMemcpyHostToDevice, h->stream) ||
+                 cudaMemcpyAsync(d2, data, db, cudaMemcpyHostToDevice, h->stream) ||
+                 cudaMemcpyAsync(w2, weights, wb, cudaMemcpyHostToDevice, h->stream))
+            rc = RIFT_ECUDA;
+        df = f2;
+        dh = h2;
+        dd = d2;
+        dw = w2;
+    }
+    if (rc == RIFT_OK &&
+        (cudaMemcpyAsync(t0, h->q_t0.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream) ||
+         cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) ||
+         launch_precompute(dh, dd, dw, df, K, M, F, t0, h->prob.fs, h->prob.n_q, A, h->Q64, h->U64, h->V64,
+                           h->stream)))
+        rc = RIFT_ECUDA;
+    if (rc == RIFT_OK)
+        h->launches += 3;
+    for (void *q : tmp)
+        cudaFreeAsync(q, h->stream);
+    if (rc != RIFT_OK) {
+        cudaStreamSynchronize(h->stream);
+        cudaGetLastError();
+        return rc;
+    }
+    return install_overlaps(h);
+}
+
+}  // extern "C"
+
+namespace rift {
+namespace host {
+
+// float32 and tensor-core copies of the overlaps now in Q64/U64/V64; marks them set.
+int install_overlaps(rift_ile_t *h)
+{
+    const int K = h->prob.K, M = h->prob.M, nq = h->prob.n_q;
     int64_t tot = (int64_t)K * 2 * M * h->prob.n_q_pad;
     int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
     prep_overlaps_kernel<<<grid, 256, 0, h->stream>>>(h->Q64, h->U64, h->V64, K, M, nq, h->prob.n_q_pad, h->Qr32,
@@ -719,6 +806,29 @@ int rift_ile_set_overlaps(rift_ile_t *h, const void *Q, const void *U, const voi
     int rc = sync_and_err(h);
     h->have_overlaps = (rc == RIFT_OK);
     return rc;
+}
+
+}  // namespace host
+}  // namespace rift
+
+extern "C" {
+
+int rift_ile_get_overlaps(const rift_ile_t *h, void *Q, void *U, void *V, int mem)
+{
+    if (!h || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+        return RIFT_EINVAL;
+    if (!h->have_overlaps)
+        return RIFT_ESTATE;
+    const int K = h->prob.K, M = h->prob.M;
+    const cudaMemcpyKind kind = mem == RIFT_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (Q)
+        CK(cudaMemcpyAsync(Q, h->Q64, sizeof(double2) * (size_t)K * M * h->prob.n_q, kind, h->stream));
+    if (U)
+        CK(cudaMemcpyAsync(U, h->U64, sizeof(double2) * (size_t)K * M * M, kind, h->stream));
+    if (V)
+        CK(cudaMemcpyAsync(V, h->V64, sizeof(double2) * (size_t)K * M * M, kind, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return RIFT_OK;
 }
 
 int rift_ile_eval(rift_ile_t *h, const double *theta, int64_t n, int mem, double *lnL_tmarg, double *lnL_t)

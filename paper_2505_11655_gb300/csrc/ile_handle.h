@@ -131,6 +131,7 @@ int grid_for_batch(rift_ile_t *h, int64_t n);
 cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
                          const double *lnpw, double *lnw);
 void drop_graph(rift_ile_t *h);
+int install_overlaps(rift_ile_t *h);
 cudaError_t mark(rift_ile_t *h, int slot, int stage);
 int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, const double *lnpw, double *lnw);
 int sync_and_err(rift_ile_t *h, int *flags_out = nullptr);

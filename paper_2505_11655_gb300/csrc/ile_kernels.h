@@ -40,6 +40,13 @@ template <typename Kernel> inline cudaError_t allow_max_dynamic_smem(Kernel kern
     return e;
 }
 
+// Overlaps from frequency-domain inputs (k_precompute.cu): h [M][F], d [K][F] complex,
+// w [K][F], f [F] (mirror symmetric), q_t0 [K]; A_scratch [K][M][F]; Q [K][M][n_q],
+// U, V [K][M][M] (all device memory).
+cudaError_t launch_precompute(const double2 *h, const double2 *d, const double *w, const double *f, int K, int M,
+                              int F, const double *q_t0_dev, double fs, int n_q, double2 *A_scratch, double2 *Q,
+                              double2 *U, double2 *V, cudaStream_t st);
+
 // Fair draws (k_fair.cu): fixed-point weights of lnw (max from stats[slot]), their
 // running sums, and n_draws sample choices with their time-choice integers.
 cudaError_t launch_fair_select(const double *lnw, int64_t n, const double *stats, int slot, uint64_t *W,
