@@ -307,12 +307,8 @@ def run_ours(args, rank, world, local_rank):
     launches = ile.kernel_launches() - l0
     barrier()
     clocks = clk.stop()
-    total = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = n * args.steps * world / (total / 1e3)
+    value, total_s = aggregate_over_ranks(n * args.steps, sum(step_ms) / 1e3, world)
+    total = 1e3 * total_s
 
     # end to end through the public API with host buffers: Q, U, V uploaded from
     # pinned memory and the result record read back inside the timed region
@@ -327,12 +323,7 @@ def run_ours(args, rank, world, local_rank):
         ile.set_overlaps(pin["Q"], pin["U"], pin["V"])
         ile.adapt(1, n)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_t) if e2e_t else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = n * len(e2e_t) * world / e2e_total if e2e_t else None
+    e2e_value = aggregate_over_ranks(n * len(e2e_t), sum(e2e_t), world)[0] if e2e_t else None
 
     # the overlaps computed on the device from the frequency-domain inputs (the stage the
     # paper runs on the CPU), against uploading precomputed Q, U, V
@@ -394,13 +385,29 @@ def _lnl_kernel_name(G, plan):
             G.RIFT_KERNEL_FP64: "lnl_fp64_kernel"}[plan[0]]
 
 
-def _max_over_ranks(torch, world, x):
-    if world == 1:
-        return x
+def _reduce_device():
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
+def aggregate_over_ranks(units, seconds, world):
+    """Whole-job throughput of independent replicas: the units all ranks processed
+    divided by the slowest rank's time; returns (value, slowest seconds)."""
+    if world == 1:
+        return units / seconds, seconds
+    import torch
+    import torch.distributed as dist
+    dev = _reduce_device()
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
+def rank_points(rank, npts):
+    """Intrinsic points of the batched workload on one rank (disjoint across ranks)."""
+    return list(range(rank * npts, (rank + 1) * npts))
 
 
 def _clock_monitor(torch, local_rank):
@@ -416,7 +423,7 @@ def run_batched(args, rank, world, local_rank):
     """512 uneven solves as one graph per step; solves/s."""
     torch, G = _setup(local_rank)
     npts = args.points
-    pts = [S.batched_problem(i + rank * npts) for i in range(npts)]
+    pts = [S.batched_problem(i) for i in rank_points(rank, npts)]
     n_iter = 3
     nper = [max(1, -(-n // n_iter)) for _, n in pts]
     solves = [G.ILE(p, precision=G.RIFT_FP32, max_samples=m, n_bins=64, seed=1 + i)
@@ -452,8 +459,8 @@ def run_batched(args, rank, world, local_rank):
         step_ms.append(e0.elapsed_time(e1))
     barrier()
     clocks = clk.stop()
-    total = _max_over_ranks(torch, world, sum(step_ms))
-    value = npts * args.steps * world / (total / 1e3)
+    value, total_s = aggregate_over_ranks(npts * args.steps, sum(step_ms) / 1e3, world)
+    total = 1e3 * total_s
     launches = batch.kernel_launches() * args.steps
 
     # end to end: every point's Q, U, V uploaded from pinned host memory, then the run
@@ -468,8 +475,7 @@ def run_batched(args, rank, world, local_rank):
             sv.set_overlaps(d["Q"], d["U"], d["V"])
         batch.run()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_total = _max_over_ranks(torch, world, sum(e2e_t)) if e2e_t else None
-    e2e_value = npts * len(e2e_t) * world / e2e_total if e2e_t else None
+    e2e_value = aggregate_over_ranks(npts * len(e2e_t), sum(e2e_t), world)[0] if e2e_t else None
     kinds = {}
     for sv in solves:
         k = _lnl_kernel_name(G, sv.plan())
@@ -564,8 +570,8 @@ def run_high_snr(args, rank, world, local_rank):
         res.append(r)
     launches = ile.kernel_launches() - l0
     clocks = clk.stop()
-    total = _max_over_ranks(torch, world, sum(step_ms))
-    value = n * n_iter * args.steps * world / (total / 1e3)
+    value, total_s = aggregate_over_ranks(n * n_iter * args.steps, sum(step_ms) / 1e3, world)
+    total = 1e3 * total_s
     r = res[-1]
     # fair draws from the last batch (sample by weight, then time bin by per-bin ln L)
     torch.cuda.synchronize()
@@ -717,8 +723,7 @@ def run_serving(args, rank, world, local_rank):
             with G.ILE(p, precision=prec, max_samples=n, n_bins=64, seed=1 + i) as s:
                 s.adapt(it, n)
         seq[name] = m / (time.perf_counter() - t0)
-    total_solves = _max_over_ranks(torch, world, sat["span_s"])
-    value = len(reqs) * world / total_solves
+    value = aggregate_over_ranks(len(reqs), sat["span_s"], world)[0]
     mix = {k: int(sum(r[0] == k for r in reqs)) for k in ("plain", "batched", "large", "high_snr")}
     out = {
         "metric": "ILE serving solves/s (p50/p99 latency)", "value": value, "unit": "solves/s", "n_gpus": world,
