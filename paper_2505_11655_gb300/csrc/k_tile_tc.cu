@@ -527,8 +527,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     ++nfull[b];
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     tc::tc_fence_after();
-                    // every consumer is past the previous gather (R is free); agree on failure
-                    if (tc::named_bar_or(1, kTcConsumers, !ok || abort_s)) {
+                    // The rows of sample quarter q (TMEM lanes 32q..) are drained and gathered by
+                    // the same four warps (warp & 3 == q), so each quarter synchronises on its own
+                    // barrier: its warps are past their previous gather (its rows of R are free);
+                    // agree on failure.
+                    const int qbar = 2 + (warp & 3);
+                    if (tc::named_bar_or(qbar, kTcConsumers / 4, !ok || abort_s)) {
                         failed = 1;
                         break;
                     }
@@ -547,7 +551,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     __syncwarp();
                     if (lane == 0)
                         tc::mbar_arrive(emptyb + b);
-                    tc::named_bar(1, kTcConsumers);   // R complete
+                    tc::named_bar(qbar, kTcConsumers / 4);   // this quarter's rows of R complete
                     const int iw0 = win0(t);
                     // padding samples and samples of other sub-groups read at the group's lowest
                     // offset, which keeps every read in the row; their sums are discarded
