@@ -277,6 +277,15 @@ int rift_ile_get_sampler(const rift_ile_t *h, double *P);
  * admission control), or -1 if `cfg` is invalid.  Host memory only; no CUDA call. */
 int64_t rift_ile_footprint(const rift_ile_config *cfg);
 
+/* Check of the failure path (no counterpart in the paper).  Every wait in the tensor-core
+ * kernels is bounded by the GPU's global timer; when a wait runs out the kernel records a
+ * timeout in the handle's error word, releases what it holds and returns, and the call
+ * reports RIFT_ETIMEOUT with the context still usable.  This call runs that same bounded
+ * wait on a barrier that nothing completes, with a limit of limit_ns (1 us .. 2 s), and
+ * returns what the host reads back: RIFT_ETIMEOUT when the path works.  RIFT_EINVAL for a
+ * limit out of range. */
+int rift_ile_wait_selftest(rift_ile_t *h, int64_t limit_ns);
+
 /* Number of kernels this handle has launched since creation (diagnostics: lets a
  * caller count device launches inside a timed region).  Returns -1 for NULL. */
 int64_t rift_ile_kernel_launches(const rift_ile_t *h);

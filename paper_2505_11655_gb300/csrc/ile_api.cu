@@ -813,6 +813,16 @@ int install_overlaps(rift_ile_t *h)
 
 extern "C" {
 
+int rift_ile_wait_selftest(rift_ile_t *h, int64_t limit_ns)
+{
+    if (!h || limit_ns < 1000 || limit_ns > 2000000000)
+        return RIFT_EINVAL;
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream));
+    CK(launch_wait_probe((uint64_t)limit_ns, h->err, h->stream));
+    h->launches += 1;
+    return sync_and_err(h);
+}
+
 int rift_ile_get_overlaps(const rift_ile_t *h, void *Q, void *U, void *V, int mem)
 {
     if (!h || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))

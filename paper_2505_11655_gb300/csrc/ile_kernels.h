@@ -57,6 +57,9 @@ cudaError_t launch_fair_select(const double *lnw, int64_t n, const double *stats
 cudaError_t launch_fair_time(const double *lnL_t, int64_t m, int n_t, const uint64_t *U_time, double t_lo,
                              double t_step, int32_t *j_out, double *t_out, cudaStream_t st);
 
+// One bounded mbarrier wait on a barrier nothing completes (k_selftest.cu).
+cudaError_t launch_wait_probe(uint64_t limit_ns, int *err, cudaStream_t st);
+
 // Raise the dynamic shared-memory limits of every kernel that needs more than the
 // default; called before any launch can be captured into a graph.
 cudaError_t prepare_sampler_kernels();

@@ -414,3 +414,21 @@ def test_quad_norm_half_with_half_grams(G):
     h.U, h.V = p.U / 2, p.V / 2
     with G.ILE(p, precision=G.RIFT_FP64, max_samples=512) as a, G.ILE(h, precision=G.RIFT_FP64, max_samples=512) as b:
         assert rel(a.eval(th), b.eval(th)) < 1e-11
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(G):
+    """The tensor-core kernels' bounded wait, run on a barrier nothing completes, gives up
+    after its limit, the call returns RIFT_ETIMEOUT, and the handle keeps working."""
+    import time
+    p = S.plain_fp64_problem()
+    th = S.prior_samples(200, 3)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=256) as s:
+        before = s.eval(th)
+        t0 = time.perf_counter()
+        rc = G.rift_ile_wait_selftest(s.h, 20_000_000)   # 20 ms
+        dt = time.perf_counter() - t0
+        assert rc == G.RIFT_ETIMEOUT
+        assert dt >= 0.02
+        assert G.rift_ile_wait_selftest(s.h, 10) == G.RIFT_EINVAL
+        after = s.eval(th)
+    assert np.array_equal(before, after)
