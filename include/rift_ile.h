@@ -201,7 +201,8 @@ int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_r
  * *samples_per_cell = fill of the Hilbert sky-sort grid.  The plan is picked per
  * problem class by the autotuner (timed candidates on the first batch of a class;
  * RIFT_ILE_TUNE=0 disables the timing, RIFT_ILE_TUNE_CACHE=<file> persists the
- * choices) unless RIFT_ILE_TC=0/1 forces the kernel.  Either output may be NULL. */
+ * choices) unless RIFT_ILE_TC=0/1 forces the kernel; RIFT_ILE_DELAY3=0/1 forces the sort key
+ * of problems with three or more detectors (sky curve, or Morton key of three delays).  Either output may be NULL. */
 #define RIFT_KERNEL_FP64 0
 #define RIFT_KERNEL_CUDA_CORE 1
 #define RIFT_KERNEL_TENSOR 2

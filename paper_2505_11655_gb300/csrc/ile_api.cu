@@ -279,10 +279,15 @@ int grid_for_batch(rift_ile_t *h, int64_t n)
 {
     SkyGrid g = sky_grid_for(n, h->plan.per_cell);
     const Problem &P = h->prob;
-    if (P.K <= 2) {
-        g.mode = P.K == 1 ? kSortDelay1 : kSortDelay2;
+    const bool delay3 = P.K >= 3 && h->plan.delay3;
+    if (P.K <= 2 || delay3) {
+        g.mode = P.K == 1 ? kSortDelay1 : P.K == 2 ? kSortDelay2 : kSortDelay3;
+        if (delay3) {   // as many cells as the sky grid, 8 per level of three delays
+            g.order = std::max(1, 2 * g.order / 3);
+            g.n_cells = 1 << (3 * g.order);
+        }
         g.gmst = P.gmst;
-        for (int k = 0; k < P.K; ++k) {
+        for (int k = 0; k < std::min(P.K, 3); ++k) {
             double r2 = 0.0;
             for (int i = 0; i < 3; ++i) {
                 g.x[k][i] = P.xpos[k][i];
@@ -968,7 +973,7 @@ int rift_ile_adapt(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, rift_ile_r
     RK(ensure_events(h, n_iter));
     h->timed = true;
     const bool same_graph = h->graph && h->graph_iter == n_iter && h->graph_n == n_per_iter &&
-                            h->graph_plan.tc == h->plan.tc && h->graph_plan.per_cell == h->plan.per_cell;
+                            h->graph_plan == h->plan;
     const bool repeat = h->last_shape_iter == n_iter && h->last_shape_n == n_per_iter;
     if (graphs_enabled() && (same_graph || repeat)) {
         // a repeated shape: capture once, then replay

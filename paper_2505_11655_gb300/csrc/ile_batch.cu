@@ -257,7 +257,7 @@ int rift_batch_run(rift_batch_t *b, rift_ile_result *out)
             return RIFT_ESTATE;
         RK(choose_plan(h, b->n[i]));
         CK(cudaStreamSynchronize(h->stream));
-        if (!rebuild && (b->plans[i].tc != h->plan.tc || b->plans[i].per_cell != h->plan.per_cell))
+        if (!rebuild && b->plans[i] != h->plan)
             rebuild = true;
     }
     if (rebuild)

@@ -174,15 +174,15 @@ constexpr int kMaxCells = 1 << (2 * kMaxOrder);
 // tile's cost is the spread of its samples' arrival delays (the Q window it needs),
 // so with one or two detectors the key is built from the delays themselves; with
 // three, whose delays lie on a two-dimensional surface, from the sky position.
-enum SortMode : int { kSortSky = 0, kSortDelay1 = 1, kSortDelay2 = 2 };
+enum SortMode : int { kSortSky = 0, kSortDelay1 = 1, kSortDelay2 = 2, kSortDelay3 = 3 };
 
 struct SkyGrid {
-    int order;     // cells per side = 2^order
-    int n_cells;   // 4^order
+    int order;     // cells per side = 2^order (kSortDelay3: bits per delay)
+    int n_cells;   // 4^order (kSortDelay3: 8^order)
     int mode = kSortSky;
     double gmst = 0.0;
-    double x[2][3] = {};   // positions / c of the detectors whose delays form the key (s)
-    double span[2] = {};   // |x| / c: those delays lie in [-span, span]
+    double x[3][3] = {};   // positions / c of the detectors whose delays form the key (s)
+    double span[3] = {};   // |x| / c: those delays lie in [-span, span]
 };
 
 __device__ __forceinline__ uint32_t hilbert_index(uint32_t x, uint32_t y, int order)
@@ -212,13 +212,20 @@ __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const S
         sincos(alpha - G.gmst, &sa, &ca);
         sincos(delta, &sd, &cd);
         const double s0 = cd * ca, s1 = cd * sa, s2 = sd;
-        uint32_t q[2];
-        const int nd = G.mode == kSortDelay1 ? 1 : 2;
+        uint32_t q[3];
+        const int nd = G.mode == kSortDelay1 ? 1 : G.mode == kSortDelay2 ? 2 : 3;
         const int levels = G.mode == kSortDelay1 ? G.n_cells : (1 << G.order);
         for (int k = 0; k < nd; ++k) {
             const double dt = -(G.x[k][0] * s0 + G.x[k][1] * s1 + G.x[k][2] * s2);
             const double u = G.span[k] > 0.0 ? 0.5 * (dt / G.span[k] + 1.0) : 0.5;
             q[k] = (uint32_t)min(levels - 1, max(0, (int)(u * levels)));
+        }
+        if (G.mode == kSortDelay3) {   // Morton interleave of the three quantised delays
+            uint32_t key = 0;
+            for (int b = 0; b < G.order; ++b)
+                for (int k = 0; k < 3; ++k)
+                    key |= ((q[k] >> b) & 1u) << (3 * b + k);
+            return key;
         }
         return G.mode == kSortDelay1 ? q[0] : hilbert_index(q[0], q[1], G.order);
     }

@@ -16,6 +16,9 @@
 struct LaunchPlan {
     int tc = -1;         // 1 tensor-core tiles, 0 CUDA-core tiles, -1 not chosen yet
     int per_cell = 4;    // samples per Hilbert sky cell
+    int delay3 = 0;      // three or more detectors: 1 sorts by a Morton key of three delays
+    bool operator==(const LaunchPlan &o) const { return tc == o.tc && per_cell == o.per_cell && delay3 == o.delay3; }
+    bool operator!=(const LaunchPlan &o) const { return !(*this == o); }
 };
 
 struct rift_ile {

@@ -56,8 +56,11 @@ void load_file(TuneCache &c)
         std::istringstream is(line);
         std::string key;
         LaunchPlan p;
-        if ((is >> key >> p.tc >> p.per_cell) && (p.tc == 0 || p.tc == 1) && p.per_cell >= 1 && p.per_cell <= 64)
+        if ((is >> key >> p.tc >> p.per_cell) && (p.tc == 0 || p.tc == 1) && p.per_cell >= 1 && p.per_cell <= 64) {
+            if (!(is >> p.delay3) || (p.delay3 != 0 && p.delay3 != 1))
+                p.delay3 = 0;
             c.plans[key] = p;
+        }
     }
 }
 
@@ -67,7 +70,7 @@ void append_file(const std::string &key, const LaunchPlan &p)
     if (!path)
         return;
     std::ofstream f(path, std::ios::app);
-    f << key << ' ' << p.tc << ' ' << p.per_cell << '\n';
+    f << key << ' ' << p.tc << ' ' << p.per_cell << ' ' << p.delay3 << '\n';
 }
 
 std::string class_key(const rift_ile_t *h, int64_t n)
@@ -102,7 +105,11 @@ int time_plan(rift_ile_t *h, int64_t n, const LaunchPlan &p, cudaEvent_t e0, cud
 
 int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
 {
-    static const LaunchPlan candidates[] = {{0, 4}, {1, 2}, {1, 4}, {1, 8}};
+    // CUDA-core tiles; tensor-core tiles at three sky-cell fills; with three or more
+    // detectors also tensor-core tiles sorted by a Morton key of three delays (fewer
+    // tile sub-groups at low sample density)
+    static const LaunchPlan candidates[] = {{0, 4, 0}, {1, 2, 0}, {1, 4, 0}, {1, 8, 0}, {1, 4, 1}};
+    const int n_cand = h->prob.K >= 3 ? 5 : 4;
     h->plan = LaunchPlan{};
     RK(grid_for_batch(h, n));
     CK(launch_draw(sampler_of(h), h->grid, h->iter_dev, 0, n, h->theta, h->lnpw, h->bins, h->key, h->stream));
@@ -115,7 +122,8 @@ int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
     }
     float best = INFINITY;
     int rc = RIFT_OK;
-    for (const LaunchPlan &p : candidates) {
+    for (int ci = 0; ci < n_cand; ++ci) {
+        const LaunchPlan &p = candidates[ci];
         float t = 0;
         rc = time_plan(h, n, p, e0, e1, &t);
         if (rc != RIFT_OK)
@@ -136,16 +144,39 @@ int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
 
 }  // namespace
 
+namespace {
+
+// RIFT_ILE_DELAY3=0/1 forces the sort key of three-detector problems.
+void apply_sort_override(rift_ile_t *h)
+{
+    const char *env = std::getenv("RIFT_ILE_DELAY3");
+    if (env && (env[0] == '0' || env[0] == '1'))
+        h->plan.delay3 = (env[0] == '1' && h->prob.K >= 3) ? 1 : 0;
+}
+
+int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed);
+
+}  // namespace
+
 int choose_plan(rift_ile_t *h, int64_t n, bool measure_allowed)
+{
+    const int rc = choose_plan_tuned(h, n, measure_allowed);
+    apply_sort_override(h);
+    return rc;
+}
+
+namespace {
+
+int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed)
 {
     if (!use_fp32(h))
         return RIFT_OK;
     if (!h->tc_ok || h->tc_mode == 0) {
-        h->plan = LaunchPlan{0, 4};
+        h->plan = LaunchPlan{0, 4, 0};
         return RIFT_OK;
     }
     if (h->tc_mode == 1) {
-        h->plan = LaunchPlan{1, 4};
+        h->plan = LaunchPlan{1, 4, 0};
         return RIFT_OK;
     }
     const std::string key = class_key(h, n);
@@ -174,6 +205,8 @@ int choose_plan(rift_ile_t *h, int64_t n, bool measure_allowed)
     }
     return RIFT_OK;
 }
+
+}  // namespace
 
 }  // namespace host
 }  // namespace rift

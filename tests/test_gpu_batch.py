@@ -141,5 +141,6 @@ def test_tuner_appends_new_classes_to_cache_file(G, monkeypatch, tmp_path):
         s.adapt(1, 9000)
         k, cell = s.plan()
     lines = path.read_text().split()
-    assert len(lines) == 3 and lines[0].startswith("K1_kp1_nt333_")
+    assert len(lines) == 4 and lines[0].startswith("K1_kp1_nt333_")
     assert int(lines[1]) == (1 if k == G.RIFT_KERNEL_TENSOR else 0) and int(lines[2]) == cell
+    assert lines[3] == "0"   # the three-delay key is a candidate only with three detectors

@@ -432,3 +432,20 @@ def test_bounded_wait_reports_timeout_and_context_survives(G):
         assert G.rift_ile_wait_selftest(s.h, 10) == G.RIFT_EINVAL
         after = s.eval(th)
     assert np.array_equal(before, after)
+
+
+@pytest.mark.parametrize("delay3", ["0", "1"])
+def test_tc_path_three_detector_sort_keys(G, orc, monkeypatch, delay3):
+    """Three detectors sorted by the sky curve or by a Morton key of their three delays:
+    the same float32 results within the bar, through eval and through adaptation."""
+    monkeypatch.setenv("RIFT_ILE_TC", "1")
+    monkeypatch.setenv("RIFT_ILE_DELAY3", delay3)
+    p = S.single_large_problem()
+    th = S.prior_samples(1500, 91)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=20000, n_bins=32, seed=19) as s:
+        got = s.eval(th)
+        r = s.adapt(2, 20000)
+        bth, lr, ll, lw = s.last_batch(20000)
+    assert_fp32_close(got, *olnL(orc, p, th))
+    red = orc.reduce(orc.lnL(p, bth) + lr)
+    assert abs(r["lnZ_iter"][1] - red["lnZ"]) <= 1e-3
