@@ -51,6 +51,7 @@ class _Problem(C.Structure):
         ("q_t0", C.c_void_p), ("Q", C.c_void_p), ("U", C.c_void_p), ("V", C.c_void_p),
         ("t_lo", C.c_double), ("t_hi", C.c_double), ("n_t", C.c_int32),
         ("d_ref", C.c_double), ("d_min", C.c_double), ("d_max", C.c_double), ("kappa", C.c_double),
+        ("dist_marg", C.c_int32),
     ]
 
 
@@ -72,9 +73,9 @@ def lib():
             L.orc_philox4x32_10.restype = None
             L.orc_uniforms.argtypes = [C.c_uint64, C.c_uint32, i64, vp]
             L.orc_uniforms.restype = None
-            L.orc_draw.argtypes = [vp, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, vp, vp, vp]
+            L.orc_draw.argtypes = [vp, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, C.c_int, vp, vp, vp]
             L.orc_draw.restype = None
-            L.orc_adapt.argtypes = [vp, C.c_int, vp, vp, i64, dbl, dbl]
+            L.orc_adapt.argtypes = [vp, C.c_int, vp, vp, i64, dbl, dbl, C.c_int]
             L.orc_adapt.restype = None
             L.orc_wigner_d.argtypes = [C.c_int, C.c_int, dbl]
             L.orc_wigner_d.restype = dbl
@@ -96,6 +97,13 @@ def lib():
             L.orc_fair_time_bin.restype = i64
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = C.c_int
+            L.orc_set_gauss_legendre16.argtypes = [vp, vp]
+            L.orc_set_gauss_legendre16.restype = None
+            L.orc_ln_dist_marg.argtypes = [dbl, dbl, dbl, dbl, dbl]
+            L.orc_ln_dist_marg.restype = dbl
+            t, w = np.polynomial.legendre.leggauss(16)
+            t, w = np.ascontiguousarray(t), np.ascontiguousarray(w)
+            L.orc_set_gauss_legendre16(t.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p))
             _lib = L
     return _lib
 
@@ -110,8 +118,9 @@ KAPPA = {0: 0.25, 1: 0.5}
 class Problem:
     """Holds contiguous copies of a problem's arrays and the C struct pointing at them."""
 
-    def __init__(self, prob):
+    def __init__(self, prob, dist_marg=False):
         self.src = prob
+        self.dist_marg = bool(dist_marg)
         self.det_tensor = np.ascontiguousarray(prob.det_tensor, dtype=np.float64)
         self.det_pos = np.ascontiguousarray(prob.det_pos, dtype=np.float64)
         self.lm = np.ascontiguousarray(prob.lm, dtype=np.int32)
@@ -126,7 +135,7 @@ class Problem:
         self.s = _Problem(self.n_det, _p(self.det_tensor), _p(self.det_pos), float(prob.gmst), self.n_modes,
                           _p(self.lm), float(prob.fs), int(prob.n_q), _p(self.q_t0), _p(self.Q), _p(self.U),
                           _p(self.V), float(prob.t_lo), float(prob.t_hi), int(prob.n_t), float(prob.d_ref),
-                          float(prob.d_min), float(prob.d_max), KAPPA[int(prob.quad_norm)])
+                          float(prob.d_min), float(prob.d_max), KAPPA[int(prob.quad_norm)], int(self.dist_marg))
 
 
 def _as_problem(p):
@@ -205,15 +214,18 @@ def delay(pos, alpha, delta, gmst):
 
 
 class Sampler:
-    """Product-form adaptive histogram sampling prior: masses P[6][B]."""
+    """Product-form adaptive histogram sampling prior: masses P[6][B].  With dist_marg
+    the distance coordinate is marginalised: it carries no sampling weight and its masses
+    stay as they are."""
 
-    def __init__(self, n_bins=64, seed=1, floor=0.1, temper=1.0, d_min=100.0, d_max=1000.0):
+    def __init__(self, n_bins=64, seed=1, floor=0.1, temper=1.0, d_min=100.0, d_max=1000.0, dist_marg=False):
         self.B = int(n_bins)
         self.P = np.full((6, self.B), 1.0 / self.B)
         self.seed = int(seed)
         self.floor = float(floor)
         self.temper = float(temper)
         self.d_min, self.d_max = float(d_min), float(d_max)
+        self.dist_marg = bool(dist_marg)
         self.iteration = 0
 
     def draw(self, n, it=None, i0=0):
@@ -222,14 +234,15 @@ class Sampler:
         lr = np.empty(n)
         bins = np.empty((n, 6), np.int32)
         Pc = np.ascontiguousarray(self.P)
-        lib().orc_draw(_p(Pc), self.B, self.seed, it, i0, n, self.d_min, self.d_max, _p(th), _p(lr), _p(bins))
+        lib().orc_draw(_p(Pc), self.B, self.seed, it, i0, n, self.d_min, self.d_max, int(self.dist_marg), _p(th),
+                       _p(lr), _p(bins))
         return th, lr, bins
 
     def adapt(self, bins, lnw):
         Pc = np.ascontiguousarray(self.P)
         b = np.ascontiguousarray(bins, dtype=np.int32)
         w = np.ascontiguousarray(lnw, dtype=np.float64)
-        lib().orc_adapt(_p(Pc), self.B, _p(b), _p(w), w.size, self.floor, self.temper)
+        lib().orc_adapt(_p(Pc), self.B, _p(b), _p(w), w.size, self.floor, self.temper, int(self.dist_marg))
         self.P = Pc
 
 
@@ -298,6 +311,12 @@ def fair_draws(prob, theta, lnw, n_draws, seed):
     step = (t_hi - t_lo) / (P.n_t - 1) if P.n_t > 1 else 0.0
     t = t_lo + j * step
     return idx, th, j, t
+
+
+def ln_dist_marg(a, b, d_ref, d_min, d_max):
+    """ln of the distance-marginal likelihood of one bin with data term a and template
+    term b at D = D_ref (prior D^2 on [d_min, d_max])."""
+    return lib().orc_ln_dist_marg(float(d_ref), float(d_min), float(d_max), float(a), float(b))
 
 
 def num_threads() -> int:

@@ -52,6 +52,7 @@ typedef struct {
     int32_t n_t;
     double d_ref, d_min, d_max;
     double kappa;             /* 1/4 as printed in Eq. (def:lnL:Decomposed) */
+    int32_t dist_marg;        /* 1: ln L marginalised over the distance prior (see orc_ln_dist_marg) */
 } orc_problem;
 
 /* ---------------------------------------------------------------- geometry */
@@ -222,11 +223,78 @@ int orc_data_term(const orc_problem *P, const double complex *c, const double *d
  *   ln L_tmarg = ln( (1/N_t) sum_j exp(ln L_j) ),
  * a Riemann mean over the inclusive grid (uniform time prior on the window).
  * lnL_t may be NULL.  Returns 0 or -1 (Q window exceeded). */
-int orc_lnL_one(const orc_problem *P, const double *theta, double *lnL_t, double *lnL_tmarg, double *quad_out)
+/* ---------------------------------------------------------------- distance marginal */
+
+/* 16-point Gauss-Legendre nodes and weights on [-1, 1], set once by the Python side
+ * (a library routine) before any evaluation. */
+static double orc_gl_t[16], orc_gl_w[16];
+
+void orc_set_gauss_legendre16(const double *t, const double *w)
+{
+    for (int i = 0; i < 16; ++i) {
+        orc_gl_t[i] = t[i];
+        orc_gl_w[i] = w[i];
+    }
+}
+
+/* Distance-marginal likelihood of one bin.  ln L is exactly a x - b x^2 in x = D_ref/D
+ * (a: data term at D = D_ref, b: template term at D = D_ref).  With the prior
+ * p(D) = 3 D^2 / (D_max^3 - D_min^3) on [D_min, D_max],
+ *   ln int p(D) exp(a x - b x^2) dD = ln( 3 D_ref^3 / (D_max^3 - D_min^3) int x^-4 e^{a x - b x^2} dx )
+ * over x in [D_ref/D_max, D_ref/D_min].  Evaluated by composite 16-point Gauss-Legendre
+ * in u = ln x (integrand x^-3 e^{a x - b x^2}) with 200 equal panels over the part of the
+ * interval where a x - b x^2 is within 80 of its maximum on the interval (outside it the
+ * integrand is below e^-80 times the peak even with the x^-3 factor).  That part is
+ * [x_m - d, x_m + d] with x_m the maximiser and d = 2T / (g + sqrt(g^2 + 4 b T)),
+ * g = |d(ax - bx^2)/dx| at x_m: the distance at which the concave exponent has dropped by T. */
+double orc_ln_dist_marg(double d_ref, double d_min, double d_max, double a, double b)
+{
+    const double T = 80.0;
+    const int NP = 200;
+    const double xlo = d_ref / d_max, xhi = d_ref / d_min;
+    const double lnC = log(3.0 * d_ref * d_ref * d_ref / (d_max * d_max * d_max - d_min * d_min * d_min));
+    double xm;
+    if (b > 0.0)
+        xm = a / (2.0 * b);
+    else
+        xm = a > 0.0 ? xhi : xlo;
+    if (xm < xlo)
+        xm = xlo;
+    if (xm > xhi)
+        xm = xhi;
+    const double phim = a * xm - b * xm * xm;
+    const double g = fabs(a - 2.0 * b * xm);
+    const double den = g + sqrt(g * g + 4.0 * b * T);
+    double L = xlo, R = xhi;
+    if (den > 0.0) {
+        const double d = 2.0 * T / den;
+        if (xm - d > L)
+            L = xm - d;
+        if (xm + d < R)
+            R = xm + d;
+    }
+    const double ul = log(L), h = (log(R) - ul) / NP;
+    double s = 0.0;
+    for (int p = 0; p < NP; ++p) {
+        const double c0 = ul + (p + 0.5) * h;
+        for (int i = 0; i < 16; ++i) {
+            const double u = c0 + 0.5 * h * orc_gl_t[i];
+            const double x = exp(u);
+            s += 0.5 * h * orc_gl_w[i] * exp(a * x - b * x * x - 3.0 * u - phim);
+        }
+    }
+    return lnC + phim + log(s);
+}
+
+int orc_lnL_one(const orc_problem *P, const double *theta_in, double *lnL_t, double *lnL_tmarg, double *quad_out)
 {
     int K = P->n_det, M = P->n_modes;
     double complex F[8], Ylm[64], c[8 * 64];
     double dt[8];
+    double theta[6];
+    memcpy(theta, theta_in, sizeof(theta));
+    if (P->dist_marg)
+        theta[5] = P->d_ref;   /* coefficients at x = 1: lin and quad are a and b */
     orc_coeffs(P, theta, F, Ylm, c, dt);
     double quad = orc_quad(P, c);
     double *vals = malloc(sizeof(double) * (size_t)P->n_t);
@@ -239,7 +307,7 @@ int orc_lnL_one(const orc_problem *P, const double *theta, double *lnL_t, double
             free(vals);
             return -1;
         }
-        vals[j] = lin - quad;
+        vals[j] = P->dist_marg ? orc_ln_dist_marg(P->d_ref, P->d_min, P->d_max, lin, quad) : lin - quad;
         if (vals[j] > mx)
             mx = vals[j];
     }
@@ -399,7 +467,7 @@ void orc_uniforms(uint64_t seed, uint32_t iter, int64_t i, double u[6])
  * P, C[0] = 0), and v = (b + (u C[B] - C[b]) / P[b]) / B, the within-bin
  * fraction clamped to [0, 1). */
 void orc_draw(const double *P, int B, uint64_t seed, uint32_t iter, int64_t i0, int64_t n,
-              double d_min, double d_max, double *theta, double *lnp_minus_lnps, int32_t *bins)
+              double d_min, double d_max, int marg, double *theta, double *lnp_minus_lnps, int32_t *bins)
 {
     double *C = malloc(sizeof(double) * 6 * (size_t)(B + 1));
     for (int d = 0; d < 6; ++d) {
@@ -428,7 +496,8 @@ void orc_draw(const double *P, int B, uint64_t seed, uint32_t iter, int64_t i0, 
                 t = nextafter(1.0, 0.0);
             v[d] = (b + t) / B;
             bins[6 * s + d] = b;
-            lr -= log(B * Pd[b] / total);
+            if (!(marg && d == 5))   /* a marginalised distance carries no sampling weight */
+                lr -= log(B * Pd[b] / total);
         }
         double *th = theta + 6 * s;
         th[0] = 2.0 * ORC_PI * v[0];
@@ -447,7 +516,8 @@ void orc_draw(const double *P, int B, uint64_t seed, uint32_t iter, int64_t i0, 
  *   P[d][b] <- (1 - eps) H[d][b] / sum_b H[d][b] + eps / B
  * beta is the tempering exponent, eps the mixing floor.  A dimension whose
  * histogram is empty keeps its previous masses. */
-void orc_adapt(double *P, int B, const int32_t *bins, const double *lnw, int64_t n, double eps, double beta)
+void orc_adapt(double *P, int B, const int32_t *bins, const double *lnw, int64_t n, double eps, double beta,
+               int marg)
 {
     double mx = -INFINITY;
     for (int64_t i = 0; i < n; ++i)
@@ -459,7 +529,7 @@ void orc_adapt(double *P, int B, const int32_t *bins, const double *lnw, int64_t
         for (int d = 0; d < 6; ++d)
             H[d * B + bins[6 * i + d]] += w;
     }
-    for (int d = 0; d < 6; ++d) {
+    for (int d = 0; d < (marg ? 5 : 6); ++d) {   /* a marginalised distance keeps its masses */
         double tot = 0.0;
         for (int b = 0; b < B; ++b)
             tot += H[d * B + b];

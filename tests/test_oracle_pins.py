@@ -729,3 +729,79 @@ def test_overlaps_single_line_closed_form(orc):
     assert np.allclose(Q[0, 0], exp, atol=1e-13)
     assert U[0, 0, 0] == pytest.approx(2 * 1.5 * (abs(h[0, 1]) ** 2 + abs(h[0, 2]) ** 2))
     assert V[0, 0, 0] == pytest.approx(2 * 1.5 * 2 * h[0, 1] * h[0, 2])
+
+
+# ------------------------------------------------------------------------------ distance marginalisation
+
+DREF, DMIN, DMAX = 400.0, 100.0, 1000.0
+
+
+def test_dist_marg_zero_signal_is_the_prior_normalisation(orc):
+    assert abs(orc.ln_dist_marg(0.0, 0.0, DREF, DMIN, DMAX)) < 1e-13
+    assert abs(orc.ln_dist_marg(0.0, 0.0, 250.0, 50.0, 2000.0)) < 1e-13
+
+
+@pytest.mark.parametrize("a,b", [(3.0, 1.0), (40.0, 12.0), (-5.0, 2.0), (150.0, 30.0), (900.0, 400.0),
+                                 (0.5, 0.0), (-30.0, 0.0)])
+def test_dist_marg_against_library_quadrature_in_distance(orc, a, b):
+    """The integral over D of p(D) exp(a x - b x^2), x = D_ref/D, by scipy's adaptive
+    quadrature in D (with the peak as a break point)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    norm = 3.0 / (DMAX ** 3 - DMIN ** 3)
+    x = lambda D: DREF / D
+    xm = a / (2 * b) if b > 0 else (DREF / DMIN if a > 0 else DREF / DMAX)
+    xm = min(max(xm, DREF / DMAX), DREF / DMIN)
+    shift = a * xm - b * xm * xm
+    f = lambda D: norm * D * D * math.exp(a * x(D) - b * x(D) ** 2 - shift)
+    pts = [DREF / xm] if DMIN < DREF / xm < DMAX else None
+    val, err = integrate.quad(f, DMIN, DMAX, points=pts, epsabs=0, epsrel=1e-13, limit=500)
+    assert orc.ln_dist_marg(a, b, DREF, DMIN, DMAX) == pytest.approx(shift + math.log(val), abs=1e-10)
+
+
+def test_dist_marg_laplace_limit(orc):
+    """A sharp peak well inside the distance range: ln I tends to the Laplace value
+    ln C + a^2/4b - 4 ln x* + ln sqrt(pi/b), with an error falling like 1/(b x*^2)."""
+    lnC = math.log(3 * DREF ** 3 / (DMAX ** 3 - DMIN ** 3))
+    xs = 1.3
+    errs = []
+    for bx2 in (1e3, 4e3, 1.6e4):
+        b = bx2 / xs ** 2
+        a = 2 * b * xs
+        lap = lnC + a * a / (4 * b) - 4 * math.log(xs) + 0.5 * math.log(math.pi / b)
+        errs.append(abs(orc.ln_dist_marg(a, b, DREF, DMIN, DMAX) - lap))
+    assert errs[-1] < 1e-3
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3
+
+
+def test_dist_marg_likelihood_brute_force_over_a_distance_grid(orc):
+    """Per-bin distance-marginal ln L of the whole chain against the average over a
+    Gauss-Legendre grid in D of the ordinary per-bin likelihood at each D."""
+    p = S.make_problem(("H1", "L1"), 4, 4096.0, n_t=41, t_lo=-0.005, t_hi=0.005, snr=6.0, seed=81)
+    th = S.prior_samples(6, 4)
+    Pm = orc.Problem(p, dist_marg=True)
+    _, mb, _ = orc.lnL(Pm, th, want_bins=True)
+    xg, wg = np.polynomial.legendre.leggauss(48)
+    edges = np.linspace(p.d_min, p.d_max, 41)
+    Ds = ((edges[:-1, None] + edges[1:, None]) / 2 + (edges[1:, None] - edges[:-1, None]) / 2 * xg).ravel()
+    Ws = ((edges[1:, None] - edges[:-1, None]) / 2 * wg).ravel() * 3 * Ds ** 2 / (p.d_max ** 3 - p.d_min ** 3)
+    for i in range(th.shape[0]):
+        rows = np.repeat(th[i:i + 1], Ds.size, 0)
+        rows[:, 5] = Ds
+        _, bins, _ = orc.lnL(p, rows, want_bins=True)      # [nD][n_t]
+        m = bins.max(0)
+        brute = m + np.log(np.sum(Ws[:, None] * np.exp(bins - m), 0))
+        assert np.allclose(mb[i], brute, atol=1e-8, rtol=1e-10), np.max(np.abs(mb[i] - brute))
+
+
+def test_dist_marg_sampler_drops_the_distance_weight(orc):
+    rng = np.random.default_rng(5)
+    P = rng.uniform(0.2, 3.0, (6, 16))
+    P /= P.sum(1, keepdims=True)
+    full, marg = orc.Sampler(n_bins=16, seed=3), orc.Sampler(n_bins=16, seed=3, dist_marg=True)
+    full.P, marg.P = P.copy(), P.copy()
+    thf, lrf, bf = full.draw(500)
+    thm, lrm, bm = marg.draw(500)
+    assert np.array_equal(thf, thm) and np.array_equal(bf, bm)
+    assert np.allclose(lrf - lrm, -np.log(16 * P[5, bf[:, 5]]), atol=1e-12)
+    marg.adapt(bm, rng.normal(0, 3, 500))
+    assert np.array_equal(marg.P[5], P[5]) and not np.allclose(marg.P[:5], P[:5])
