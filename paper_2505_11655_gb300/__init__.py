@@ -50,6 +50,7 @@ class rift_ile_config(C.Structure):
         ("d_ref_mpc", C.c_double), ("d_min_mpc", C.c_double), ("d_max_mpc", C.c_double),
         ("quad_norm", C.c_int32), ("precision", C.c_int32), ("n_bins", C.c_int32), ("adapt_floor", C.c_double),
         ("adapt_temper", C.c_double), ("seed", C.c_uint64), ("max_samples", C.c_int64),
+        ("distance_marg", C.c_int32),
     ]
 
 
@@ -367,7 +368,7 @@ def rift_ile_strerror(code):
 # ---------------------------------------------------------------------------------- convenience
 
 def make_config(prob, precision=RIFT_FP32, max_samples=1 << 20, n_bins=64, adapt_floor=0.1, adapt_temper=1.0,
-                seed=1):
+                seed=1, distance_marg=False):
     """rift_ile_config for a problem (attributes of ile_synth.Problem) and the host
     arrays it points at (keep the returned dict alive as long as the config)."""
     keep = dict(
@@ -381,7 +382,7 @@ def make_config(prob, precision=RIFT_FP32, max_samples=1 << 20, n_bins=64, adapt
         keep["lm"].shape[0], _ptr(keep["lm"]), float(prob.fs), int(prob.n_q), _ptr(keep["q_t0"]), float(prob.t_lo),
         float(prob.t_hi), int(prob.n_t), float(prob.d_ref), float(prob.d_min), float(prob.d_max),
         int(prob.quad_norm), int(precision), int(n_bins), float(adapt_floor), float(adapt_temper), int(seed),
-        int(max_samples))
+        int(max_samples), int(bool(distance_marg)))
     return cfg, keep
 
 
@@ -393,8 +394,9 @@ class Server:
         self.h = rift_srv_create(hbm_budget_bytes, max_slots)
         self._keep = []
 
-    def submit(self, prob, n_iter, n_per_iter, tag, precision=RIFT_FP32, n_bins=64, seed=1):
-        cfg, keep = make_config(prob, precision, max_samples=n_per_iter, n_bins=n_bins, seed=seed)
+    def submit(self, prob, n_iter, n_per_iter, tag, precision=RIFT_FP32, n_bins=64, seed=1, distance_marg=False):
+        cfg, keep = make_config(prob, precision, max_samples=n_per_iter, n_bins=n_bins, seed=seed,
+                                distance_marg=distance_marg)
         arrs = [np.ascontiguousarray(x, np.complex128) for x in (prob.Q, prob.U, prob.V)]
         rift_srv_submit(self.h, cfg, arrs[0], arrs[1], arrs[2], n_iter, n_per_iter, tag)
 
@@ -476,7 +478,7 @@ class ILE:
     arrays (the attributes of ``ile_synth.Problem``)."""
 
     def __init__(self, prob, precision=RIFT_FP32, max_samples=1 << 20, n_bins=64, adapt_floor=0.1,
-                 adapt_temper=1.0, seed=1, stream=None, set_overlaps=True):
+                 adapt_temper=1.0, seed=1, stream=None, set_overlaps=True, distance_marg=False):
         self._keep = dict(
             det_tensor=np.ascontiguousarray(prob.det_tensor, np.float64),
             det_pos=np.ascontiguousarray(prob.det_pos, np.float64),
@@ -489,7 +491,8 @@ class ILE:
             self.n_det, _ptr(k["det_tensor"]), _ptr(k["det_pos"]), float(prob.gmst), self.n_modes, _ptr(k["lm"]),
             float(prob.fs), int(prob.n_q), _ptr(k["q_t0"]), float(prob.t_lo), float(prob.t_hi), int(prob.n_t),
             float(prob.d_ref), float(prob.d_min), float(prob.d_max), int(prob.quad_norm), int(precision),
-            int(n_bins), float(adapt_floor), float(adapt_temper), int(seed), int(max_samples))
+            int(n_bins), float(adapt_floor), float(adapt_temper), int(seed), int(max_samples),
+            int(bool(distance_marg)))
         self.h = rift_ile_create(self.cfg, stream)
         if set_overlaps:
             self.set_overlaps(prob.Q, prob.U, prob.V)

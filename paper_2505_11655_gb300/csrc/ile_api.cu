@@ -120,6 +120,30 @@ int wigner_table(int l, int m, double *coef, int8_t *pc, int8_t *ps)
     return nt;
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1]: Newton's method on P_n from the
+// three-term recurrence, starting at the Chebyshev-like guesses cos(pi (i + 3/4) / (n + 1/2)).
+void gauss_legendre(int n, double *t, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double x = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-16)
+                break;
+        }
+        t[n - 1 - i] = x;   // ascending
+        w[n - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
 int map_err(int flags)
 {
     if (flags & kErrTimeout)
@@ -144,12 +168,15 @@ SamplerDev sampler_of(const rift_ile_t *h)
     S.floor_eps = h->cfg.adapt_floor;
     S.temper = h->cfg.adapt_temper;
     S.seed = h->cfg.seed;
+    S.marg = h->cfg.distance_marg;
     return S;
 }
 
 int validate(const rift_ile_config *c)
 {
     if (!c || c->n_det < 1 || c->n_det > RIFT_MAX_DET || c->n_modes < 1 || c->n_modes > RIFT_MAX_MODES)
+        return RIFT_EINVAL;
+    if (c->distance_marg != 0 && c->distance_marg != 1)
         return RIFT_EINVAL;
     if (!c->det_tensor || !c->det_pos_m || !c->lm || !c->q_t0_s)
         return RIFT_EINVAL;
@@ -536,6 +563,24 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
     P.gmst = cfg->gmst_rad;
     P.d_ref = cfg->d_ref_mpc;
     P.kappa = cfg->quad_norm == RIFT_QUAD_HALF ? 0.5 : 0.25;
+    P.dist_marg = cfg->distance_marg;
+    P.dm_xlo = cfg->d_ref_mpc / cfg->d_max_mpc;
+    P.dm_xhi = cfg->d_ref_mpc / cfg->d_min_mpc;
+    P.dm_lnC = std::log(3.0 * cfg->d_ref_mpc * cfg->d_ref_mpc * cfg->d_ref_mpc /
+                        (cfg->d_max_mpc * cfg->d_max_mpc * cfg->d_max_mpc -
+                         cfg->d_min_mpc * cfg->d_min_mpc * cfg->d_min_mpc));
+    P.dm_lnub = P.dm_lnC + std::log((1.0 / (P.dm_xlo * P.dm_xlo * P.dm_xlo) -
+                                     1.0 / (P.dm_xhi * P.dm_xhi * P.dm_xhi)) / 3.0);
+    gauss_legendre(8, P.gl8_t, P.gl8_w);
+    gauss_legendre(16, P.gl16_t, P.gl16_w);
+    for (int i = 0; i < 8; ++i) {
+        P.gl8_tf[i] = (float)P.gl8_t[i];
+        P.gl8_wf[i] = (float)P.gl8_w[i];
+    }
+    P.dm_xlo_f = (float)P.dm_xlo;
+    P.dm_xhi_f = (float)P.dm_xhi;
+    P.dm_lnC_f = (float)P.dm_lnC;
+    P.dm_lnub_f = (float)P.dm_lnub;
     for (int k = 0; k < K; ++k) {
         const double *D = cfg->det_tensor + 9 * k;
         P.Dten[k][0] = D[0];
@@ -1017,7 +1062,7 @@ int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus
 int rift_ile_fair_draws(rift_ile_t *h, int64_t n_draws, uint64_t seed, int mem, double *theta, double *t,
                         int64_t *index)
 {
-    if (!h || n_draws < 0 || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE))
+    if (!h || n_draws < 0 || (mem != RIFT_MEM_HOST && mem != RIFT_MEM_DEVICE) || h->cfg.distance_marg)
         return RIFT_EINVAL;
     if (n_draws == 0)
         return RIFT_OK;

@@ -395,7 +395,7 @@ extern "C" {
 int rift_ile_av(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, double p_thr, int64_t n_min_star,
                 int64_t capacity, int32_t restart, rift_ile_result *out)
 {
-    if (!h || n_iter < 1 || n_iter > RIFT_MAX_ITER || n_per_iter < 1 || n_per_iter > h->cap || !(p_thr > 0.0) ||
+    if (!h || h->cfg.distance_marg || n_iter < 1 || n_iter > RIFT_MAX_ITER || n_per_iter < 1 || n_per_iter > h->cap || !(p_thr > 0.0) ||
         !(p_thr <= 1.0) || n_min_star < 1 || capacity < n_per_iter || capacity > ((int64_t)1 << 31) - 2)
         return RIFT_EINVAL;
     if (!h->have_overlaps)

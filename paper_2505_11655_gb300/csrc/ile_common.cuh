@@ -33,6 +33,15 @@ struct Problem {
     int K, M, n_q, n_t;
     int n_q_pad;            // row pitch (floats) of the float32 Q planes
     double fs, t_lo, t_step, gmst, d_ref, kappa;
+    // distance marginalisation (dist_marg = 1): x = D_ref/D in [dm_xlo, dm_xhi], prior
+    // normalisation ln(3 D_ref^3 / (D_max^3 - D_min^3)), Gauss-Legendre nodes on [-1, 1]
+    int dist_marg;
+    double dm_xlo, dm_xhi, dm_lnC;
+    double dm_lnub;   // dm_lnC + ln((dm_xlo^-3 - dm_xhi^-3) / 3): upper bound offset of the marginal
+    double gl8_t[8], gl8_w[8], gl16_t[16], gl16_w[16];
+    // float copies for the float32 quadrature (no float64 conversions in the kernels)
+    float gl8_tf[8], gl8_wf[8];
+    float dm_xlo_f, dm_xhi_f, dm_lnC_f, dm_lnub_f;
     double Dten[kMaxDet][6];   // response tensor: xx, yy, zz, xy, xz, yz
     double xpos[kMaxDet][3];   // vertex position / c (seconds)
     double q_t0[kMaxDet];
@@ -236,6 +245,70 @@ __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const S
     const uint32_t x = (uint32_t)min(side - 1, max(0, (int)(a * side)));
     const uint32_t y = (uint32_t)min(side - 1, max(0, (int)(z * side)));
     return hilbert_index(x, y, G.order);
+}
+
+__device__ __forceinline__ float fn_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double fn_exp(double x) { return exp(x); }
+__device__ __forceinline__ float fn_log(float x) { return __logf(x); }
+__device__ __forceinline__ double fn_log(double x) { return log(x); }
+
+// ln of the distance-marginal likelihood of one bin.  ln L is exactly a x - b x^2 in
+// x = D_ref/D (a, b: data and template terms at D = D_ref); with the prior
+// p(D) = 3 D^2 / (D_max^3 - D_min^3) on [D_min, D_max] the marginal is
+//   ln( C int x^-4 exp(a x - b x^2) dx ),  x in [D_ref/D_max, D_ref/D_min].
+// Composite Gauss-Legendre (NP panels of N nodes) in u = ln x (integrand x^-3 e^{...}, no
+// pole), over the part of the range where the exponent is within `thr` of its maximum
+// phi_m at x_m: [x_m - d, x_m + d] with d = 2 thr / (g + sqrt(g^2 + 4 b thr)), g the slope
+// at x_m (0 for an interior maximum).  The exponent is taken relative to phi_m through
+// phi(x) - phi_m = phi'(x_m) (x - x_m) - b (x - x_m)^2, free of cancellation.
+template <typename T, int N, int NP>
+__device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi, T lnC, T a, T b, T thr)
+{
+    T xm = b > (T)0 ? a / ((T)2 * b) : (a > (T)0 ? xhi : xlo);
+    xm = xm < xlo ? xlo : (xm > xhi ? xhi : xm);
+    const T slope = a - (T)2 * b * xm;
+    const T phim = xm * (a - b * xm);
+    const T g = slope < (T)0 ? -slope : slope;
+    const T den = g + sqrt(g * g + (T)4 * b * thr);
+    T L = xlo, R = xhi;
+    if (den > (T)0) {
+        const T d = (T)2 * thr / den;
+        L = xm - d > xlo ? xm - d : xlo;
+        R = xm + d < xhi ? xm + d : xhi;
+    }
+    const T ul = fn_log(L), h = (fn_log(R) - ul) / (T)NP;
+    T s = (T)0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const T c0 = ul + ((T)p + (T)0.5) * h;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const T u = c0 + (T)0.5 * h * gt[i];
+            const T dx = fn_exp(u) - xm;
+            s += gw[i] * fn_exp(slope * dx - b * dx * dx - (T)3 * u);
+        }
+    }
+    return lnC + phim + fn_log((T)0.5 * h * s);
+}
+
+// Upper bound of ln_dist_marg: the exponent at its maximum on the range, the x^-3 factor
+// integrated over the whole range.
+__device__ __forceinline__ float dm_bound32(const Problem &P, float a, float b)
+{
+    const float xlo = P.dm_xlo_f, xhi = P.dm_xhi_f;
+    float xm = b > 0.f ? a / (2.f * b) : (a > 0.f ? xhi : xlo);
+    xm = fminf(fmaxf(xm, xlo), xhi);
+    return P.dm_lnub_f + xm * (a - b * xm);
+}
+
+__device__ __forceinline__ float ln_dist_marg32(const Problem &P, float a, float b)
+{
+    return ln_dist_marg<float, 8, 3>(P.gl8_tf, P.gl8_wf, P.dm_xlo_f, P.dm_xhi_f, P.dm_lnC_f, a, b, 24.f);
+}
+
+__device__ __forceinline__ double ln_dist_marg64(const Problem &P, double a, double b)
+{
+    return ln_dist_marg<double, 16, 4>(P.gl16_t, P.gl16_w, P.dm_xlo, P.dm_xhi, P.dm_lnC, a, b, 44.0);
 }
 
 }  // namespace rift

@@ -115,6 +115,7 @@ struct SamplerDev {
     double d_min, d_max;
     double floor_eps, temper;
     uint64_t seed;
+    int marg;        // 1: the distance (dimension 5) is marginalised: no weight, masses kept
 };
 
 // Draw n samples of sampler iteration *iter_base + iter_off (the iteration counter is

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kF64Threads) lnl_fp64_kernel(Problem P, const 
     for (int64_t s = (int64_t)blockIdx.x * wpb + warp; s < n; s += (int64_t)gridDim.x * wpb) {
         const double *th = theta + 6 * s;
         Sky sky = sky_of(th[0], th[1], P.gmst);
-        double x = P.d_ref / th[5];
+        double x = P.dist_marg ? 1.0 : P.d_ref / th[5];   // marginalised: terms at D = D_ref
         if (lane < P.K) {
             double s2p, c2p;
             sincos(2.0 * th[2], &s2p, &c2p);
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kF64Threads) lnl_fp64_kernel(Problem P, const 
                     lin += c.x * qr + c.y * qi;
                 }
             }
-            double v = lin - quad;
+            double v = P.dist_marg ? ln_dist_marg64(P, lin, quad) : lin - quad;
             if (lnL_t)
                 lnL_t[s * P.n_t + j] = v;
             if (v > mx) {

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
         const uint32_t s = idx[w];
         const double *th = theta + 6 * (size_t)s;
         Sky sky = sky_of(th[0], th[1], P.gmst);
-        const double x = P.d_ref / th[5];
+        const double x = P.dist_marg ? 1.0 : P.d_ref / th[5];
         if (lane < K) {
             double s2p, c2p;
             sincos(2.0 * th[2], &s2p, &c2p);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
                     lin = fmaf((float)c.x, vr, fmaf((float)c.y, vi, lin));
                 }
             }
-            const double v = (double)lin - quad;
+            const double v = P.dist_marg ? (double)ln_dist_marg32(P, lin, (float)quad) : (double)lin - quad;
             vals[j] = v;
             mx32 = fmaxf(mx32, (float)v);
         }
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
                         lin += c.x * ((1.0 - f) * q0.x + f * q1.x) + c.y * ((1.0 - f) * q0.y + f * q1.y);
                     }
                 }
-                v = lin - quad;
+                v = P.dist_marg ? ln_dist_marg64(P, lin, quad) : lin - quad;
                 vals[j] = v;
             }
             mx = fmax(mx, v);

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
             if (t >= 1.0)
                 t = 0x1.fffffffffffffp-1;
             v[d] = (lo + t) / B;
-            lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
+            if (!(S.marg && d == 5))
+                lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
             packed |= (uint64_t)lo << (10 * d);
         }
         double th[6];
@@ -712,7 +713,7 @@ __global__ void adapt_final_kernel(SamplerDev S, const uint64_t *__restrict__ pa
 {
     const int B = S.B;
     const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;   // one warp per dimension
-    if (d >= 6)
+    if (d >= 6 || (S.marg && d == 5))   // a marginalised distance keeps its masses
         return;
     double tot = 0.0;
     for (int b = lane; b < B; b += 32) {

@@ -142,7 +142,7 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             float *pp = par + 8 * tid;
             pp[0] = c2p;
             pp[1] = s2p;
-            pp[2] = valid ? (float)(P.d_ref / th[5]) : 0.f;
+            pp[2] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
             pp[3] = (float)th[3];
             pp[4] = chalf;
             pp[5] = shalf;
@@ -392,11 +392,44 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                 for (int p = 0; p < 8; ++p) {
                     const float qd = qds[warp + 8 * p];
                     cmx[p] = -INFINITY;
+                    if (P.dist_marg) {
+                        // distance marginal per bin: upper bounds first; the sample's bin with
+                        // the highest bound is evaluated (by the lane holding it), and bins
+                        // whose bound lies more than 40 below the larger of that value and
+                        // the running maximum cannot move the marginal (< e^-40): left out
+                        float bnd[kBinsPerLane], bl = -INFINITY, al = 0.f;
 #pragma unroll
-                    for (int q = 0; q < kBinsPerLane; ++q) {
-                        lin[p][q] -= qd;
-                        if (lane + 32 * q < J)
-                            cmx[p] = fmaxf(cmx[p], lin[p][q]);
+                        for (int q = 0; q < kBinsPerLane; ++q) {
+                            bnd[q] = lane + 32 * q < J ? dm_bound32(P, lin[p][q], qd) : -INFINITY;
+                            if (bnd[q] > bl) {
+                                bl = bnd[q];
+                                al = lin[p][q];
+                            }
+                        }
+                        float bmax = bl;
+#pragma unroll
+                        for (int o = 16; o; o >>= 1)
+                            bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+                        const int owner = __ffs(__ballot_sync(0xffffffffu, bl == bmax)) - 1;
+                        float vbest = -INFINITY;
+                        if (lane == owner && bmax > -INFINITY)
+                            vbest = ln_dist_marg32(P, al, qd);
+                        vbest = __shfl_sync(0xffffffffu, vbest, owner);
+                        const float thr = lnL_t ? -INFINITY : fmaxf(run_mx[p], vbest) - 40.f;
+#pragma unroll
+                        for (int q = 0; q < kBinsPerLane; ++q) {
+                            lin[p][q] = (lane + 32 * q < J && bnd[q] >= thr) ? ln_dist_marg32(P, lin[p][q], qd)
+                                                                              : -INFINITY;
+                            if (lane + 32 * q < J)
+                                cmx[p] = fmaxf(cmx[p], lin[p][q]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < kBinsPerLane; ++q) {
+                            lin[p][q] -= qd;
+                            if (lane + 32 * q < J)
+                                cmx[p] = fmaxf(cmx[p], lin[p][q]);
+                        }
                     }
                 }
                 if (lnL_t) {

@@ -264,7 +264,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             float *pp = par + 8 * tid;
             pp[0] = c2p;
             pp[1] = s2p;
-            pp[2] = valid ? (float)(P.d_ref / th[5]) : 0.f;
+            pp[2] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
             pp[3] = (float)th[3];
             float *pc = pw + tid * 2 * kTcPow, *ps = pc + kTcPow;
             pc[0] = 1.f;
@@ -581,11 +581,36 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     if (k == K - 1) {
                         // fold this thread's bins of the chunk into its running log-sum-exp
                         float cmx = -INFINITY;
+                        if (P.dist_marg) {
+                            // distance marginal per bin: a cheap upper bound first; the bin
+                            // with the highest bound is evaluated, and a bin whose bound lies
+                            // more than 40 below the larger of that value and the running
+                            // maximum cannot move the marginal (< e^-40): left out
+                            float bnd[kTcBPT], bmax = -INFINITY, abest = 0.f;
 #pragma unroll
-                        for (int i = 0; i < kTcBPT; ++i) {
-                            lin[i] -= gqd;
-                            if (i < jn)
-                                cmx = fmaxf(cmx, lin[i]);
+                            for (int i = 0; i < kTcBPT; ++i) {
+                                bnd[i] = i < jn ? dm_bound32(P, lin[i], gqd) : -INFINITY;
+                                if (bnd[i] > bmax) {
+                                    bmax = bnd[i];
+                                    abest = lin[i];
+                                }
+                            }
+                            const float vbest = jn > 0 ? ln_dist_marg32(P, abest, gqd) : -INFINITY;
+                            // (every bin exact when the per-bin values are written out)
+                            const float thr = lnL_t ? -INFINITY : fmaxf(run_mx, vbest) - 40.f;
+#pragma unroll
+                            for (int i = 0; i < kTcBPT; ++i) {
+                                lin[i] = (i < jn && bnd[i] >= thr) ? ln_dist_marg32(P, lin[i], gqd) : -INFINITY;
+                                if (i < jn)
+                                    cmx = fmaxf(cmx, lin[i]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < kTcBPT; ++i) {
+                                lin[i] -= gqd;
+                                if (i < jn)
+                                    cmx = fmaxf(cmx, lin[i]);
+                            }
                         }
                         if (lnL_t && gok && in_grp) {
                             for (int i = 0; i < jn; ++i)

@@ -60,7 +60,7 @@ def _create_rc(lib, cfg):
 
 @pytest.mark.parametrize("field,value", [
     ("n_det", 0), ("n_det", 5), ("n_modes", 0), ("n_modes", 33), ("fs_hz", 0.0), ("n_q", 1), ("n_t", 0),
-    ("d_ref_mpc", 0.0), ("d_min_mpc", 2000.0), ("quad_norm", 2), ("precision", 7), ("n_bins", 1),
+    ("d_ref_mpc", 0.0), ("d_min_mpc", 2000.0), ("quad_norm", 2), ("precision", 7), ("n_bins", 1), ("distance_marg", 2),
     ("n_bins", 4096), ("adapt_floor", 1.0), ("adapt_temper", 0.0), ("max_samples", 0),
 ])
 def test_invalid_config_rejected(lib, field, value):

@@ -1,0 +1,108 @@
+"""Distance-marginalised likelihood (rift_ile_config.distance_marg) against the oracle.
+
+The oracle integrates x^-4 exp(a x - b x^2) by 200 panels of 16-point Gauss-Legendre
+(pinned to scipy's adaptive quadrature and to a brute-force distance grid); the device
+uses 4 panels of 16 nodes in float64 and 3 of 8 in float32 over the same closed-form
+support, whose quadrature error is below 1e-10 and 1e-5 in ln of the integral.
+"""
+import numpy as np
+import pytest
+
+import ile_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2505_11655_gb300 as G
+    G.load(build_if_missing=True)
+    return G
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_lib):
+    return oracle_lib
+
+
+def oracle_marg(orc, p, th):
+    P = orc.Problem(p, dist_marg=True)
+    ll, bins, quad = orc.lnL(P, th, want_bins=True)
+    return ll, bins, quad * (p.d_ref / p.d_min) ** 2   # largest template term over the prior range
+
+
+def close32(got, exp, quad):
+    d = np.abs(got - exp)
+    near = exp >= exp.max() - 100.0
+    assert np.max(d[near]) <= 1e-3, np.max(d[near])
+    assert np.all(d <= 1e-3 + 4e-7 * (np.abs(exp) + 2.0 * quad)), np.max(d)
+
+
+@pytest.mark.parametrize("problem", ["plain", "large"])
+def test_fp64_matches_oracle(G, orc, problem):
+    p = S.plain_fp64_problem() if problem == "plain" else S.single_large_problem()
+    th = S.prior_samples(600, 51)
+    exp, ebins, _ = oracle_marg(orc, p, th)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=1024, distance_marg=True) as s:
+        got, bins = s.eval(th, want_bins=True)
+        th2 = th.copy()
+        th2[:, 5] = 999.0   # the distance coordinate is not used
+        got2 = s.eval(th2)
+    assert np.max(np.abs(got - exp) / np.maximum(1.0, np.abs(exp))) < 1e-9
+    assert np.max(np.abs(bins - ebins) / np.maximum(1.0, np.abs(ebins))) < 1e-9
+    assert np.array_equal(got, got2)
+
+
+@pytest.mark.parametrize("tc", ["0", "1"])
+def test_fp32_matches_oracle(G, orc, monkeypatch, tc):
+    monkeypatch.setenv("RIFT_ILE_TC", tc)
+    p = S.single_large_problem()
+    th = S.prior_samples(1500, 52)
+    exp, _, quad = oracle_marg(orc, p, th)
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=2048, distance_marg=True) as s:
+        got = s.eval(th)
+    close32(got, exp, quad)
+
+
+def test_mixed_matches_oracle(G, orc):
+    p = S.single_large_problem()
+    th = S.prior_samples(1200, 53)
+    exp, _, quad = oracle_marg(orc, p, th)
+    with G.ILE(p, precision=G.RIFT_MIXED, max_samples=2048, distance_marg=True) as s:
+        got = s.eval(th)
+    close32(got, exp, quad)
+    near = exp >= exp.max() - 40.0
+    assert np.max(np.abs(got[near] - exp[near])) <= 1e-6   # the weighted samples are float64
+
+
+def test_adaptive_run_matches_oracle_chain(G, orc):
+    """Two adaptive iterations in float64: the device's draws and weights equal the
+    oracle's 5-D sampler chain (distance coordinate without weight, masses kept)."""
+    p = S.plain_fp64_problem()
+    n = 8000
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=16, seed=29, distance_marg=True) as s:
+        r = s.adapt(2, n)
+        th, lr, ll, lw = s.last_batch(n)
+        Pdev = s.sampler()
+    sm = orc.Sampler(n_bins=16, seed=29, d_min=p.d_min, d_max=p.d_max, dist_marg=True)
+    res = orc.run_adapt(orc.Problem(p, dist_marg=True), sm, 2, n)
+    assert np.allclose(th, res["theta"][-1], rtol=1e-10, atol=1e-12)
+    assert np.allclose(lr, res["lnw"][-1] - res["lnL"][-1], rtol=1e-10, atol=1e-10)
+    assert np.max(np.abs(ll - res["lnL"][-1]) / np.maximum(1.0, np.abs(res["lnL"][-1]))) < 1e-9
+    assert abs(r["lnZ"] - res["pooled"]["lnZ"]) <= 1e-9 * max(1.0, abs(res["pooled"]["lnZ"]))
+    assert np.allclose(Pdev[5], 1.0 / 16)   # the distance masses stay uniform
+
+
+def test_refusals(G):
+    p = S.plain_fp64_problem()
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=1000, distance_marg=True) as s:
+        s.marginalize(1000)
+        with pytest.raises(G.RiftError) as e:
+            s.fair_draws(10)
+        assert e.value.code == G.RIFT_EINVAL
+        with pytest.raises(G.RiftError) as e:
+            s.av(1, 1000)
+        assert e.value.code == G.RIFT_EINVAL
