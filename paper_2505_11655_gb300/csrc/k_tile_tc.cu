@@ -164,6 +164,9 @@ cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups
 
 // ---------------------------------------------------------------- the kernel
 
+// kDM: distance marginalisation (a separate instantiation, so that the plain path keeps
+// its registers)
+template <bool kDM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const uint32_t *__restrict__ perm, int64_t n,
               double *__restrict__ lnL_tmarg, double *__restrict__ lnL_t, const double *__restrict__ lnpw,
@@ -264,7 +267,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             float *pp = par + 8 * tid;
             pp[0] = c2p;
             pp[1] = s2p;
-            pp[2] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
+            pp[2] = valid ? (kDM ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
             pp[3] = (float)th[3];
             float *pc = pw + tid * 2 * kTcPow, *ps = pc + kTcPow;
             pc[0] = 1.f;
@@ -581,7 +584,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     if (k == K - 1) {
                         // fold this thread's bins of the chunk into its running log-sum-exp
                         float cmx = -INFINITY;
-                        if (P.dist_marg) {
+                        if (kDM) {
                             // distance marginal per bin: a cheap upper bound first; the bin
                             // with the highest bound is evaluated, and a bin whose bound lies
                             // more than 40 below the larger of that value and the running
@@ -694,7 +697,8 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     if (!lnl_tc_fits(P, max_smem))
         return cudaErrorInvalidConfiguration;
     const size_t smem = tc_layout(P.K, P.M, P.n_t).end;
-    cudaError_t e = allow_max_dynamic_smem(lnl_tc_kernel);
+    auto kern = P.dist_marg ? lnl_tc_kernel<true> : lnl_tc_kernel<false>;
+    cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess)
         return e;
     e = cudaMemsetAsync(tile_counter, 0, sizeof(int), st);
@@ -702,14 +706,15 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
         return e;
     const int64_t tiles = (n + kTcS - 1) / kTcS;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    lnl_tc_kernel<<<grid, kTcThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err,
+    kern<<<grid, kTcThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err,
                                                   tile_counter);
     return cudaGetLastError();
 }
 
 cudaError_t prepare_tc_kernels()
 {
-    return allow_max_dynamic_smem(lnl_tc_kernel);
+    cudaError_t e = allow_max_dynamic_smem(lnl_tc_kernel<false>);
+    return e != cudaSuccess ? e : allow_max_dynamic_smem(lnl_tc_kernel<true>);
 }
 
 }  // namespace rift
