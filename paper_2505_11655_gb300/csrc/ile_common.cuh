@@ -43,24 +43,32 @@ struct Problem {
     float gl8_tf[8], gl8_wf[8];
     float dm_xlo_f, dm_xhi_f, dm_lnC_f, dm_lnub_f;
     double Dten[kMaxDet][6];   // response tensor: xx, yy, zz, xy, xz, yz
+    float Dten_f[kMaxDet][6];  // float copy for the float32 response
     double xpos[kMaxDet][3];   // vertex position / c (seconds)
     double q_t0[kMaxDet];
+    // Q-sample position of the first bin: u = ufs0_k + xfs_k . n with n the unit vector
+    // to the source (ufs0 = (t_lo - q_t0) fs, xfs = -x fs)
+    double ufs0[kMaxDet];
+    double xfs[kMaxDet][3];
     int mode_m[kMaxModes];
     // -2Y_lm(iota, .) = sum_t wcoef[t] cos(iota/2)^wpc[t] sin(iota/2)^wps[t]  (normalisation folded in)
     double wcoef[kMaxModes][kMaxWTerms];
     int8_t wpc[kMaxModes][kMaxWTerms];
     int8_t wps[kMaxModes][kMaxWTerms];
     int8_t wn[kMaxModes];
+    float wcoef_f[kMaxModes][kMaxWTerms];   // float copy of wcoef
     const double2 *Q64;     // [K][M][n_q]
     const double2 *U64;     // [K][M][M]
     const double2 *V64;
     const float *Qr32;      // [K][2M][n_q_pad] split planes, zero padded
     const float2 *U32;
     const float2 *V32;
+    const float4 *UV32;     // [K][M][M] (U re, U im, V re, V im) interleaved
     // tensor-core copy of Q: [K][hi, lo][tc_groups][Kp/8][8][8] float16, scaled by 2^e
     // with e from the float bits of max|Q| (*qmax_bits)
     const __half *Qtc;
     int tc_groups;
+    int tc_uv;              // tensor-core kernel keeps the upper triangle of UV32 in shared memory
     const unsigned int *qmax_bits;
 };
 
@@ -117,6 +125,24 @@ __device__ __forceinline__ Cx<T> response(const Problem &P, int k, const Sky &s,
     T B = ed0 * dd0 + ed1 * dd1 + ed2 * dd2;
     T Cc = ed0 * da0 + ed1 * da1 + ed2 * da2;
     T pr = A - B, pi = (T)2 * Cc;
+    return {pr * c2psi - pi * s2psi, pr * s2psi + pi * c2psi};
+}
+
+// The same response in float32 from the sky basis vectors already rounded to float
+// (ea = (ea0, ea1, 0), ed = (ed0, ed1, ed2)) and the float copy of the tensor; the
+// operations are those of response<float>.
+__device__ __forceinline__ Cx<float> response_f(const float *D, float ea0, float ea1, float ed0, float ed1, float ed2,
+                                                float c2psi, float s2psi)
+{
+    const float xx = D[0], yy = D[1], zz = D[2], xy = D[3], xz = D[4], yz = D[5];
+    const float da0 = xx * ea0 + xy * ea1, da1 = xy * ea0 + yy * ea1, da2 = xz * ea0 + yz * ea1;
+    const float dd0 = xx * ed0 + xy * ed1 + xz * ed2;
+    const float dd1 = xy * ed0 + yy * ed1 + yz * ed2;
+    const float dd2 = xz * ed0 + yz * ed1 + zz * ed2;
+    const float A = ea0 * da0 + ea1 * da1;
+    const float B = ed0 * dd0 + ed1 * dd1 + ed2 * dd2;
+    const float Cc = ed0 * da0 + ed1 * da1 + ed2 * da2;
+    const float pr = A - B, pi = 2.f * Cc;
     return {pr * c2psi - pi * s2psi, pr * s2psi + pi * c2psi};
 }
 

@@ -87,6 +87,8 @@ size_t lnl_fp32_smem_bytes(const Problem &P);
 
 // Tensor-core variant of the float32 tiled path (tiles of 128 samples, tcgen05 MMA).
 bool lnl_tc_fits(const Problem &P, int max_smem);
+// Whether the tensor-core kernel can also hold the Gram table (upper triangle) in shared memory.
+bool lnl_tc_uv_fits(const Problem &P, int max_smem);
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
                           int *tile_counter, cudaStream_t st);

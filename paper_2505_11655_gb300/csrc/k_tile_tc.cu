@@ -30,8 +30,9 @@ namespace rift {
 constexpr int kTcS = 128;          // samples per tile (MMA M)
 constexpr int kTcW = 128;          // window columns per step (MMA N)
 constexpr int kTcConsumers = 512;  // 16 consumer warps: drain, gather, log-sum-exp
-constexpr int kTcThreads = kTcConsumers + 32;   // plus one producer warp: TMA staging and MMA issue
-constexpr int kTcProducerWarp = kTcConsumers / 32;
+constexpr int kTcThreads = kTcConsumers + 64;   // plus an MMA-issue warp and a TMA-staging warp
+constexpr int kTcIssuerWarp = kTcConsumers / 32;
+constexpr int kTcStagerWarp = kTcIssuerWarp + 1;
 constexpr int kTcQ = kTcConsumers / kTcS;  // threads per sample in the gather (bin quarters)
 constexpr int kTcBPT = 16;         // bins per thread per chunk
 constexpr int kTcMaxBins = kTcQ * kTcBPT;
@@ -39,19 +40,29 @@ constexpr int kTcMaxBins = kTcQ * kTcBPT;
 // the gather (lane = sample, per-sample column) both touch bank = sample, conflict-free.
 constexpr int kTcPow = 16;
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32: relative error ~2^-22,
+// 0 for arguments below the float range)
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 // A tile whose samples span more than this many Q samples at some detector is cut
 // into contiguous sub-groups (compact along the sort order) that are windowed apart.
 constexpr int kTcSpreadLimit = 64;
 
 struct TcLayout {
-    size_t a, b, r, bini, binf, i0, f0, inv, quad, gid, lse, bar, tptr, end;
-    size_t sky, par, pw, fx, qpart;   // prologue scratch, aliased on the B buffers
+    size_t a, b, r, bini, binf, i0, f0, inv, quad, gid, lse, uv, bar, tptr, end;
+    size_t sky, e5, par, pw, pe, fx, qpart;   // prologue scratch, aliased on the B buffers
     int kp;
 };
 
 __host__ __device__ inline size_t tc_al(size_t o, size_t a = 128) { return (o + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
+__host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t, bool uv)
 {
     TcLayout L;
     L.kp = (2 * M + 15) / 16 * 16;
@@ -60,15 +71,19 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     o = tc_al(o + (size_t)K * 2 * kTcS * L.kp * 2);
     L.b = o;
     const size_t bbytes = (size_t)2 * 2 * kTcW * L.kp * 2;
+    // prologue scratch, every table sample-minor ([row][kTcS]) so that the lanes of a
+    // warp (consecutive samples) touch consecutive words
     size_t s = L.b;
-    L.sky = s;   s = tc_al(s + (size_t)kTcS * 4 * 8, 16);
-    L.par = s;   s = tc_al(s + (size_t)kTcS * 8 * 4, 16);
-    L.pw = s;    s = tc_al(s + (size_t)kTcS * 2 * kTcPow * 4, 16);
+    L.sky = s;   s = tc_al(s + (size_t)3 * kTcS * 8, 16);
+    L.e5 = s;    s = tc_al(s + (size_t)5 * kTcS * 4, 16);
+    L.par = s;   s = tc_al(s + (size_t)4 * kTcS * 4, 16);
+    L.pw = s;    s = tc_al(s + (size_t)2 * kTcPow * kTcS * 4, 16);
+    L.pe = s;    s = tc_al(s + (size_t)(kMaxL + 1) * kTcS * 8, 16);
     L.fx = s;    s = tc_al(s + (size_t)K * kTcS * 8, 16);
     L.qpart = s; s = tc_al(s + (size_t)kTcQ * kTcS * 4, 16);
     o = tc_al(L.b + (bbytes > s - L.b ? bbytes : s - L.b));
     L.r = o;
-    const size_t rbytes = (size_t)kTcW * kTcS * 4, cbytes = (size_t)K * 2 * M * kTcS * 4;
+    const size_t rbytes = (size_t)kTcW * kTcS * 4, cbytes = (size_t)M * kTcS * 8;
     o = tc_al(o + (rbytes > cbytes ? rbytes : cbytes), 16);
     L.bini = o; o = tc_al(o + (size_t)n_t * 4, 16);
     L.binf = o; o = tc_al(o + (size_t)n_t * 4, 16);
@@ -78,6 +93,9 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.quad = o; o = tc_al(o + (size_t)kTcS * 4, 16);
     L.gid = o;  o = tc_al(o + (size_t)kTcS * 4, 16);
     L.lse = o;  o = tc_al(o + (size_t)2 * kTcQ * kTcS * 4, 16);
+    L.uv = o;   // [pair a <= b][K] float4, row-major upper triangle (when it fits)
+    if (uv)
+        o = tc_al(o + (size_t)(M * (M + 1) / 2) * K * 16, 16);
     L.bar = o;  o = tc_al(o + 6 * 8, 16);
     L.tptr = o; o = tc_al(o + 16, 16);
     L.end = o;
@@ -88,9 +106,14 @@ bool lnl_tc_fits(const Problem &P, int max_smem)
 {
     if (P.Qtc == nullptr || P.tc_groups <= 0)
         return false;
-    const TcLayout L = tc_layout(P.K, P.M, P.n_t);
+    const TcLayout L = tc_layout(P.K, P.M, P.n_t, P.tc_uv != 0);
     // plus the kernel's static shared memory (sub-group table, ~5 KB)
     return L.kp <= 64 && L.end + 8192 <= (size_t)max_smem;
+}
+
+bool lnl_tc_uv_fits(const Problem &P, int max_smem)
+{
+    return tc_layout(P.K, P.M, P.n_t, true).end + 8192 <= (size_t)max_smem;
 }
 
 // ---------------------------------------------------------------- Q copy for the tensor path
@@ -173,12 +196,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
               double *__restrict__ lnw, int *err, int *tile_counter)
 {
     extern __shared__ __align__(128) unsigned char sm[];
-    const int K = P.K, M = P.M, R2 = 2 * M, NT = P.n_t;
-    const TcLayout L = tc_layout(K, M, NT);
+    const int K = P.K, M = P.M, NT = P.n_t;
+    const TcLayout L = tc_layout(K, M, NT, P.tc_uv != 0);
     const int kp = L.kp, kcores = kp / 8;
     __half *As = reinterpret_cast<__half *>(sm + L.a);          // [K][2][kTcS x kp] canonical K-major
     __half *Bs = reinterpret_cast<__half *>(sm + L.b);          // [2 buf][2 part][kTcW x kp]
-    float *Rs = reinterpret_cast<float *>(sm + L.r);            // Rt [kTcW][kTcS] (prologue: C [K][2M][kTcS])
+    float *Rs = reinterpret_cast<float *>(sm + L.r);            // Rt [kTcW][kTcS] (prologue: Y [M][kTcS])
     int *bini = reinterpret_cast<int *>(sm + L.bini);
     float *binf = reinterpret_cast<float *>(sm + L.binf);
     int *i0s = reinterpret_cast<int *>(sm + L.i0);              // [K][kTcS]
@@ -186,17 +209,20 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     float *invs = reinterpret_cast<float *>(sm + L.inv);        // [K][kTcS] 2^-(row exponent + Q exponent)
     float *qds = reinterpret_cast<float *>(sm + L.quad);
     uint32_t *gid = reinterpret_cast<uint32_t *>(sm + L.gid);
+    const float4 *uvs = P.tc_uv ? reinterpret_cast<const float4 *>(sm + L.uv) : nullptr;
     uint64_t *bbar = reinterpret_cast<uint64_t *>(sm + L.bar);  // [0,1] windows staged
     uint64_t *fullb = bbar + 2;   // [0,1] MMAs of an accumulator complete (tcgen05.commit)
     uint64_t *emptyb = bbar + 4;  // [0,1] accumulator drained by the 16 consumer warps
     uint32_t *tptr = reinterpret_cast<uint32_t *>(sm + L.tptr);
-    double *sky = reinterpret_cast<double *>(sm + L.sky);
-    float *par = reinterpret_cast<float *>(sm + L.par);
-    float *pw = reinterpret_cast<float *>(sm + L.pw);
-    float2 *fx = reinterpret_cast<float2 *>(sm + L.fx);
+    double *sky = reinterpret_cast<double *>(sm + L.sky);      // [3][kTcS] float64 unit vector n
+    float *e5 = reinterpret_cast<float *>(sm + L.e5);          // [5][kTcS] sky basis of the response
+    float *par = reinterpret_cast<float *>(sm + L.par);        // [cos 2psi, sin 2psi, D_ref/D][kTcS]
+    float *pw = reinterpret_cast<float *>(sm + L.pw);          // [2 kTcPow][kTcS] cos^q, sin^q (iota/2)
+    float2 *pe = reinterpret_cast<float2 *>(sm + L.pe);        // [kMaxL + 1][kTcS] exp(-i j phi)
+    float2 *fx = reinterpret_cast<float2 *>(sm + L.fx);        // [K][kTcS] (D_ref/D) F_k
     float *qpart = reinterpret_cast<float *>(sm + L.qpart);
     float *lse = reinterpret_cast<float *>(sm + L.lse);         // [2][kTcQ][kTcS] running max, sum
-    float *Cs = Rs;
+    float2 *Ys = reinterpret_cast<float2 *>(Rs);               // [M][kTcS] -2Y_lm(iota, -phi)
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
     __shared__ int glo[kTcS][kMaxDet], ghi[kTcS][kMaxDet], gstart[kTcS + 1];
     __shared__ int tile_s, abort_s, ngroups_s;
@@ -214,6 +240,20 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         bini[j] = bt.bin_i[j];
         binf[j] = bt.bin_f[j];
     }
+    if (P.tc_uv) {
+        // Gram table, upper triangle in row-major pair order, all detectors of a pair adjacent
+        float4 *uvw = reinterpret_cast<float4 *>(sm + L.uv);
+        const int npairs = M * (M + 1) / 2;
+        for (int e = tid; e < npairs * K; e += blockDim.x) {
+            const int p = e / K, k = e - p * K;
+            int a = 0, b = p;
+            while (b >= M - a) {
+                b -= M - a;
+                ++a;
+            }
+            uvw[e] = P.UV32[((size_t)k * M + a) * M + a + b];
+        }
+    }
     if (warp == 0)
         tc::tmem_alloc(tptr, 256);
     if (tid == 0) {
@@ -228,10 +268,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tptr;
-    // completed-phase counters per buffer: windows staged (producer), MMA commits
-    // (producer and consumers keep their own copies), accumulator drains (producer)
-    uint32_t nstage[2] = {0u, 0u}, ncommit[2] = {0u, 0u}, nfull[2] = {0u, 0u}, ndrain[2] = {0u, 0u};
-    const bool producer = warp == kTcProducerWarp;
+    // phase counters per buffer, each kept by the thread that waits on the barrier: windows
+    // staged (stager: nstaged) and consumed (issuer: nstage), MMA commits (issuer) and
+    // completions (consumers: nfull), accumulator drains (issuer)
+    uint32_t nstaged[2] = {0u, 0u}, nstage[2] = {0u, 0u}, ncommit[2] = {0u, 0u}, nfull[2] = {0u, 0u},
+             ndrain[2] = {0u, 0u};
+    const bool producer = warp >= kTcIssuerWarp;   // issuer or stager
 
     for (;;) {
         if (tid == 0)
@@ -256,35 +298,47 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 for (int d = 0; d < 6; ++d)
                     th[d] = theta[6 * (int64_t)g + d];
             Sky sk = sky_of(th[0], th[1], P.gmst);
-            double *sp = sky + 4 * tid;
-            sp[0] = sk.cd;
-            sp[1] = sk.sd;
-            sp[2] = sk.ch;
-            sp[3] = sk.sh;
-            float s2p, c2p, shalf, chalf;
+            // unit vector to the source (Earth frame), float64 for the arrival delays
+            sky[tid] = sk.cd * sk.ch;
+            sky[kTcS + tid] = sk.cd * sk.sh;
+            sky[2 * kTcS + tid] = sk.sd;
+            // e_a = (-sin h, cos h, 0), e_d = (-sin d cos h, -sin d sin h, cos d), rounded once
+            e5[tid] = (float)(-sk.sh);
+            e5[kTcS + tid] = (float)sk.ch;
+            e5[2 * kTcS + tid] = (float)(-sk.sd * sk.ch);
+            e5[3 * kTcS + tid] = (float)(-sk.sd * sk.sh);
+            e5[4 * kTcS + tid] = (float)sk.cd;
+            float s2p, c2p, shalf, chalf, sphi, cphi;
             sincosf((float)(2.0 * th[2]), &s2p, &c2p);
             sincosf((float)(0.5 * th[4]), &shalf, &chalf);
-            float *pp = par + 8 * tid;
-            pp[0] = c2p;
-            pp[1] = s2p;
-            pp[2] = valid ? (kDM ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
-            pp[3] = (float)th[3];
-            float *pc = pw + tid * 2 * kTcPow, *ps = pc + kTcPow;
-            pc[0] = 1.f;
-            ps[0] = 1.f;
+            sincosf((float)th[3], &sphi, &cphi);
+            par[tid] = c2p;
+            par[kTcS + tid] = s2p;
+            par[2 * kTcS + tid] = valid ? (kDM ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
+            float pc = 1.f, ps = 1.f;
+            pw[tid] = 1.f;
+            pw[kTcPow * kTcS + tid] = 1.f;
             for (int q = 1; q <= kMaxPow; ++q) {
-                pc[q] = pc[q - 1] * chalf;
-                ps[q] = ps[q - 1] * shalf;
+                pc *= chalf;
+                ps *= shalf;
+                pw[q * kTcS + tid] = pc;
+                pw[(kTcPow + q) * kTcS + tid] = ps;
+            }
+            // exp(-i j phi) for j = 0..kMaxL by repeated multiplication with exp(-i phi)
+            float2 e = make_float2(1.f, 0.f);
+            pe[tid] = e;
+            for (int j = 1; j <= kMaxL; ++j) {
+                e = make_float2(e.x * cphi + e.y * sphi, e.y * cphi - e.x * sphi);
+                pe[j * kTcS + tid] = e;
             }
         }
         __syncthreads();
         // ---------------- B: delays, interpolation node split, x F_k
         for (int it = tid; tid < kTcConsumers && it < kTcS * K; it += kTcConsumers) {
             const int s = it % kTcS, k = it / kTcS;
-            const double *sp = sky + 4 * s;
-            Sky sk{sp[0], sp[1], sp[2], sp[3]};
-            const float *pp = par + 8 * s;
-            double u0 = (P.t_lo + arrival_delay(P, k, sk) - P.q_t0[k]) * P.fs;
+            // Q-sample position of the first bin, (t_lo + dt_k - q_t0_k) fs
+            const double u0 =
+                fma(P.xfs[k][0], sky[s], fma(P.xfs[k][1], sky[kTcS + s], fma(P.xfs[k][2], sky[2 * kTcS + s], P.ufs0[k])));
             double fl = floor(u0);
             int i0 = (int)fl;
             i0s[k * kTcS + s] = i0;
@@ -293,8 +347,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 atomicMin(&lo_s[k], i0);
                 atomicMax(&hi_s[k], i0);
             }
-            Cx<float> F = response<float>(P, k, sk, pp[0], pp[1]);
-            fx[k * kTcS + s] = make_float2(pp[2] * F.re, pp[2] * F.im);
+            const Cx<float> F = response_f(P.Dten_f[k], e5[s], e5[kTcS + s], e5[2 * kTcS + s], e5[3 * kTcS + s],
+                                           e5[4 * kTcS + s], par[s], par[kTcS + s]);
+            const float amp = par[2 * kTcS + s];
+            fx[k * kTcS + s] = make_float2(amp * F.re, amp * F.im);
         }
         __syncthreads();
         // sub-groups: the whole tile when it is compact, else a greedy cut along the sort order
@@ -349,46 +405,80 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             gstart[ng] = kTcS;
             ngroups_s = ng;
         }
-        // ---------------- C: harmonics and coefficients C [K][2M][kTcS] (float32)
+        // ---------------- C: harmonics Y_m = -2Y_lm(iota, -phi) [M][kTcS] (float32); the mode
+        // coefficient of detector k is c_k,m = fx_k Y_m
         for (int it = tid; tid < kTcConsumers && it < kTcS * M; it += kTcConsumers) {
             const int s = it % kTcS, m = it / kTcS;
-            const float *pc = pw + s * 2 * kTcPow, *ps = pc + kTcPow;
             float d = 0.f;
             for (int t = 0; t < P.wn[m]; ++t)
-                d += (float)P.wcoef[m][t] * pc[P.wpc[m][t]] * ps[P.wps[m][t]];
-            float sy, cy;
-            sincosf(-(float)P.mode_m[m] * par[8 * s + 3], &sy, &cy);
-            const float yr = d * cy, yi = d * sy;
-            for (int k = 0; k < K; ++k) {
-                float2 f = fx[k * kTcS + s];
-                Cs[(k * R2 + 2 * m) * kTcS + s] = f.x * yr - f.y * yi;
-                Cs[(k * R2 + 2 * m + 1) * kTcS + s] = f.x * yi + f.y * yr;
-            }
+                d += P.wcoef_f[m][t] * pw[P.wpc[m][t] * kTcS + s] * pw[(kTcPow + P.wps[m][t]) * kTcS + s];
+            const int mm = P.mode_m[m];
+            const float2 e = pe[(mm < 0 ? -mm : mm) * kTcS + s];   // exp(-i |m| phi)
+            Ys[m * kTcS + s] = make_float2(d * e.x, d * (mm < 0 ? -e.y : e.y));
         }
         __syncthreads();
-        // ---------------- D: template term (Hermitian U, symmetric V halving), kTcQ threads per sample
+        // ---------------- D: template term.  With c_k = f_k Y (f_k = fx_k):
+        //   c_k^H U_k c_k = |f_k|^2 Y^H U_k Y,   c_k^T V_k c_k = f_k^2 Y^T V_k Y,
+        // so each product of two components of Y (pair a <= b) is formed once and serves
+        // every detector.  The pairs of the upper triangle are split evenly over kTcQ
+        // threads per sample; off-diagonal pairs count twice (U Hermitian, V symmetric).
         if (tid < kTcConsumers) {
             const int s = tid & (kTcS - 1), part = tid >> 7;
-            float acc = 0.f;
-            for (int k = 0; k < K; ++k) {
-                const float *Ck = Cs + (size_t)k * R2 * kTcS + s;
-                for (int a = part; a < M; a += kTcQ) {
-                    const float2 *Ur = P.U32 + ((size_t)k * M + a) * M;
-                    const float2 *Vr = P.V32 + ((size_t)k * M + a) * M;
-                    const float ar = Ck[(2 * a) * kTcS], ai = Ck[(2 * a + 1) * kTcS];
-                    float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f;
-                    for (int b = a + 1; b < M; ++b) {
-                        const float cr = Ck[(2 * b) * kTcS], ci = Ck[(2 * b + 1) * kTcS];
-                        const float2 u = __ldg(Ur + b), v = __ldg(Vr + b);
-                        ur = fmaf(u.x, cr, fmaf(-u.y, ci, ur));
-                        ui = fmaf(u.x, ci, fmaf(u.y, cr, ui));
-                        vr = fmaf(v.x, cr, fmaf(-v.y, ci, vr));
-                        vi = fmaf(v.x, ci, fmaf(v.y, cr, vi));
+            const int npairs = M * (M + 1) / 2, per = (npairs + kTcQ - 1) / kTcQ;
+            const int p0 = min(npairs, part * per), p1 = min(npairs, p0 + per);
+            int a = 0, b = p0;   // pair p0 in row-major order of the upper triangle
+            while (a < M && b >= M - a) {
+                b -= M - a;
+                ++a;
+            }
+            b += a;
+            float2 hu[kMaxDet], hv[kMaxDet];
+#pragma unroll
+            for (int k = 0; k < kMaxDet; ++k) {
+                hu[k] = make_float2(0.f, 0.f);
+                hv[k] = make_float2(0.f, 0.f);
+            }
+            // the pair loop, with the Gram entries from shared memory or (when the table did
+            // not fit) from the global copy
+            auto pair_loop = [&](auto gram) {
+                for (int q = p0; q < p1; ++a, b = a) {
+                    // row a, columns b .. bend - 1 of this thread's range; pair (a, c) has index qr + c
+                    const int bend = min(M, b + (p1 - q));
+                    const int qr = q - b;
+                    q += bend - b;
+                    const float2 ya = Ys[a * kTcS + s];
+#pragma unroll 4
+                    for (int c = b; c < bend; ++c) {
+                        const float2 yb = Ys[c * kTcS + s];
+                        const float w = c == a ? 1.f : 2.f;
+                        const float xr = w * ya.x, xi = w * ya.y;
+                        // conj(w Y_a) Y_b = (pr, pi) and (w Y_a) Y_b = (sr, si), packed
+                        const float2 u = __fmul2_rn(make_float2(xr, xr), yb);
+                        const float2 pq = __ffma2_rn(make_float2(xi, -xi), make_float2(yb.y, yb.x), u);
+                        const float2 sq = __ffma2_rn(make_float2(-xi, xi), make_float2(yb.y, yb.x), u);
+#pragma unroll
+                        for (int k = 0; k < kMaxDet; ++k) {
+                            if (k < K) {
+                                const float4 g = gram(qr + c, a, c, k);   // U re, U im, V re, V im
+                                hu[k] = __ffma2_rn(make_float2(g.x, g.y), pq, hu[k]);   // Re(U P) = x - y
+                                hv[k] = __ffma2_rn(make_float2(g.z, g.z), sq, hv[k]);   // V S
+                                hv[k] = __ffma2_rn(make_float2(-g.w, g.w), make_float2(sq.y, sq.x), hv[k]);
+                            }
+                        }
                     }
-                    const float2 ud = __ldg(Ur + a), vd = __ldg(Vr + a);
-                    const float a2r = ar * ar - ai * ai, a2i = 2.f * ar * ai;
-                    acc += ud.x * (ar * ar + ai * ai) + 2.f * (ar * ur + ai * ui);
-                    acc += (vd.x * a2r - vd.y * a2i) + 2.f * (ar * vr - ai * vi);
+                }
+            };
+            if (uvs)
+                pair_loop([&](int pidx, int, int, int k) { return uvs[pidx * K + k]; });
+            else
+                pair_loop([&](int, int ra, int cb, int k) { return __ldg(P.UV32 + ((size_t)k * M + ra) * M + cb); });
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxDet; ++k) {
+                if (k < K) {
+                    const float2 f = fx[k * kTcS + s];
+                    const float fa = f.x * f.x + f.y * f.y, f2r = f.x * f.x - f.y * f.y, f2i = 2.f * f.x * f.y;
+                    acc += fa * (hu[k].x - hu[k].y) + (f2r * hv[k].x - f2i * hv[k].y);
                 }
             }
             qpart[part * kTcS + s] = acc;
@@ -397,14 +487,17 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         if (tid < kTcS)
             qds[tid] = (float)P.kappa * ((qpart[tid] + qpart[kTcS + tid]) + (qpart[2 * kTcS + tid] + qpart[3 * kTcS + tid]));
 
-        // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector)
+        // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector);
+        // each thread writes one sample row of a detector, 8 components (4 modes) per 16-byte store
         {
             for (int it = tid; tid < kTcConsumers && it < kTcS * K; it += kTcConsumers) {
                 const int s = it % kTcS, k = it / kTcS;
-                const float *Ck = Cs + (size_t)k * R2 * kTcS + s;
+                const float2 f = fx[k * kTcS + s];
                 float mx = 0.f;
-                for (int r = 0; r < R2; ++r)
-                    mx = fmaxf(mx, fabsf(Ck[r * kTcS]));
+                for (int m = 0; m < M; ++m) {
+                    const float2 y = Ys[m * kTcS + s];
+                    mx = fmaxf(mx, fmaxf(fabsf(f.x * y.x - f.y * y.y), fabsf(f.x * y.y + f.y * y.x)));
+                }
                 int ex = 0;
                 if (mx > 0.f)
                     frexpf(mx, &ex);
@@ -414,13 +507,25 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 __half *Ahi = As + (size_t)(k * 2) * kTcS * kp;
                 __half *Alo = Ahi + (size_t)kTcS * kp;
                 const int rowbase = ((s >> 3) * kcores * 8 + (s & 7)) * 8;
-                for (int r = 0; r < kp; ++r) {
-                    const float v = r < R2 ? Ck[r * kTcS] * sc : 0.f;
-                    const __half hi = __float2half_rn(v);
-                    const __half lo = __float2half_rn(v - __half2float(hi));
-                    const int off = rowbase + (r >> 3) * 64 + (r & 7);
-                    Ahi[off] = hi;
-                    Alo[off] = lo;
+                for (int c8 = 0; c8 < kcores; ++c8) {
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int m = 4 * c8 + j;
+                        float cr = 0.f, ci = 0.f;
+                        if (m < M) {
+                            const float2 y = Ys[m * kTcS + s];
+                            cr = (f.x * y.x - f.y * y.y) * sc;
+                            ci = (f.x * y.y + f.y * y.x) * sc;
+                        }
+                        const __half hr = __float2half_rn(cr), hi = __float2half_rn(ci);
+                        const __half lr = __float2half_rn(cr - __half2float(hr));
+                        const __half li = __float2half_rn(ci - __half2float(hi));
+                        hw[j] = (uint32_t)__half_as_ushort(hr) | ((uint32_t)__half_as_ushort(hi) << 16);
+                        lw[j] = (uint32_t)__half_as_ushort(lr) | ((uint32_t)__half_as_ushort(li) << 16);
+                    }
+                    *reinterpret_cast<uint4 *>(Ahi + rowbase + c8 * 64) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4 *>(Alo + rowbase + c8 * 64) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
             }
             tc::fence_proxy_async_smem();
@@ -435,74 +540,88 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         int failed = 0;
         const int ngroups = ngroups_s;
         for (int grp = 0; grp < ngroups && !failed; ++grp) {
-            int glo_k[kMaxDet];
             int spread = 0;
-            for (int k = 0; k < K; ++k) {
-                glo_k[k] = glo[grp][k];
+            for (int k = 0; k < K; ++k)
                 spread = max(spread, ghi[grp][k] - glo[grp][k]);
-            }
             const bool in_grp = gs >= gstart[grp] && gs < gstart[grp + 1];
             int jmax = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
             jmax = max(1, min(jmax, kTcMaxBins));
             const int n_chunks = (NT + jmax - 1) / jmax;
             const int jnom = (NT + n_chunks - 1) / n_chunks;
             const int n_steps = n_chunks * K;
-            // window of step t: detector t % K, bins of chunk t / K; clamped so that a
-            // window never leaves the allocation of the Q copy
-            auto win0 = [&](int t) {
-                const int k = t % K, j0 = (t / K) * jnom;
-                return min(max(glo_k[k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
+            // Step t covers detector t % K and the bins of chunk t / K (both tracked as
+            // counters).  First Q column of the window of detector k for the chunk starting at
+            // bin j0, clamped so that a window never leaves the allocation of the Q copy.
+            auto win0 = [&](int k, int j0) {
+                return min(max(glo[grp][k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
             };
 
-            if (producer) {
-                // ============ producer warp, lane 0: stage windows, issue MMAs
+            if (warp == kTcIssuerWarp) {
+                // ============ issuer warp, lane 0: one MMA batch per staged window
                 if (lane == 0) {
-                    auto stage = [&](int t) {
-                        const int k = t % K, b = t & 1;
-                        const int g0 = win0(t) >> 3;
-                        const __half *src = P.Qtc + ((size_t)k * 2 * P.tc_groups + g0) * (size_t)kp * 8;
-                        __half *dst = Bs + (size_t)b * 2 * part_halves;
-                        tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
-                        tc::bulk_g2s(dst, src, part_bytes, bbar + b);
-                        tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
-                        ++nstage[b];
-                    };
-                    stage(0);
-                    if (n_steps > 1)
-                        stage(1);
-                    for (int t = 0; t < n_steps && !failed; ++t) {
-                        const int k = t % K, b = t & 1;
+                    // shared-memory matrix descriptors: the high word (stride byte offset,
+                    // version) is the same for every operand; the low word holds the start
+                    // address and the leading byte offset, so an operand offset is an addition
+                    // to the address field (all addresses < 256 KB: no carry out of it)
+                    const uint32_t dhi = ((sbo >> 4) & 0x3FFFu) | (1u << 14);
+                    const uint32_t lbo_f = (128u >> 4) << 16;
+                    const uint32_t a_lo0 = ((tc::smem_u32(As) & 0x3FFFFu) >> 4) | lbo_f;
+                    const uint32_t b_lo0 = ((tc::smem_u32(Bs) & 0x3FFFFu) >> 4) | lbo_f;
+                    const uint32_t a_part = (uint32_t)(kTcS * kp * 2) >> 4, b_part = part_bytes >> 4;
+                    auto desc = [&](uint32_t lo) { return ((uint64_t)dhi << 32) | lo; };
+                    int k = 0;
+                    for (int t = 0; t < n_steps && !failed; ++t, k = k + 1 == K ? 0 : k + 1) {
+                        const int b = t & 1;
                         // window t staged; accumulator b drained by the consumers
-                        if (!tc::mbar_wait(bbar + b, (nstage[b] - 1) & 1u, kWaitNs) ||
+                        if (!tc::mbar_wait(bbar + b, nstage[b] & 1u, kWaitNs) ||
                             (ncommit[b] > ndrain[b] && !tc::mbar_wait(emptyb + b, ndrain[b] & 1u, kWaitNs))) {
                             failed = 1;
                             break;
                         }
+                        ++nstage[b];
                         if (ncommit[b] > ndrain[b])
                             ++ndrain[b];
                         tc::tc_fence_after();
                         const uint32_t d = tmem + (uint32_t)(b * kTcW);
-                        const uint32_t a_hi = tc::smem_u32(As + (size_t)(k * 2) * kTcS * kp);
-                        const uint32_t a_lo = a_hi + (uint32_t)(kTcS * kp * 2);
-                        const uint32_t b_hi = tc::smem_u32(Bs + (size_t)b * 2 * part_halves);
-                        const uint32_t b_lo = b_hi + part_bytes;
+                        const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
+                        const uint32_t bh = b_lo0 + (uint32_t)(2 * b) * b_part, bl = bh + b_part;
                         for (int kk = 0; kk < kp / 16; ++kk) {
-                            const uint32_t o = (uint32_t)kk * 256u;
-                            tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc,
-                                        kk > 0);
-                            tc::mma_f16(d, tc::smem_desc(a_hi + o, 128, sbo), tc::smem_desc(b_lo + o, 128, sbo), idesc, 1);
-                            tc::mma_f16(d, tc::smem_desc(a_lo + o, 128, sbo), tc::smem_desc(b_hi + o, 128, sbo), idesc, 1);
+                            const uint32_t o = (uint32_t)kk * 16u;   // 256 bytes: the next 16 components
+                            tc::mma_f16(d, desc(ah + o), desc(bh + o), idesc, kk > 0);
+                            tc::mma_f16(d, desc(ah + o), desc(bl + o), idesc, 1);
+                            tc::mma_f16(d, desc(al + o), desc(bh + o), idesc, 1);
                         }
                         tc::mma_commit(fullb + b);
                         ++ncommit[b];
-                        // window t + 1 goes into the other buffer once the MMAs of step t - 1 are done
-                        if (t >= 1 && t + 1 < n_steps) {
-                            const int bo = (t - 1) & 1;
-                            if (!tc::mbar_wait(fullb + bo, (ncommit[bo] - 1) & 1u, kWaitNs)) {
-                                failed = 1;
-                                break;
-                            }
-                            stage(t + 1);
+                    }
+                    if (failed)
+                        abort_s = 1;
+                }
+                __syncwarp();
+            } else if (warp == kTcStagerWarp) {
+                // ============ stager warp, lane 0: windows into the two B buffers.  Every
+                // window staged into buffer b is consumed by exactly one MMA batch that commits
+                // to fullb[b], so before the j-th window into b the stager waits for the
+                // (j - 1)-th completion of fullb[b] (that of the previous group or tile when
+                // this is a group's first window into b).
+                if (lane == 0) {
+                    int sk = 0, sch = 0;   // detector and chunk of the next window
+                    for (int t = 0; t < n_steps && !failed; ++t) {
+                        const int b = t & 1;
+                        if (nstaged[b] > 0 && !tc::mbar_wait(fullb + b, (nstaged[b] - 1) & 1u, kWaitNs)) {
+                            failed = 1;
+                            break;
+                        }
+                        const int g0 = win0(sk, sch * jnom) >> 3;
+                        const __half *src = P.Qtc + ((size_t)sk * 2 * P.tc_groups + g0) * (size_t)kp * 8;
+                        __half *dst = Bs + (size_t)b * 2 * part_halves;
+                        tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
+                        tc::bulk_g2s(dst, src, part_bytes, bbar + b);
+                        tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
+                        ++nstaged[b];
+                        if (++sk == K) {
+                            sk = 0;
+                            ++sch;
                         }
                     }
                     if (failed)
@@ -519,8 +638,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     bfj[i] = 0.f;
                     bj[i] = 0;
                 }
-                for (int t = 0; t < n_steps; ++t) {
-                    const int k = t % K, b = t & 1, j0 = (t / K) * jnom, J = min(jnom, NT - j0);
+                for (int t = 0, k = 0, j0 = 0; t < n_steps; ++t) {
+                    const int b = t & 1, J = min(jnom, NT - j0);
                     const int jq = (J + kTcQ - 1) / kTcQ;                 // bins per quarter
                     const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins
                     // one lane per warp waits for the MMAs of step t
@@ -555,11 +674,11 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     if (lane == 0)
                         tc::mbar_arrive(emptyb + b);
                     tc::named_bar(qbar, kTcConsumers / 4);   // this quarter's rows of R complete
-                    const int iw0 = win0(t);
+                    const int iw0 = win0(k, j0);
                     // padding samples and samples of other sub-groups read at the group's lowest
                     // offset, which keeps every read in the row; their sums are discarded
                     const bool mine = gok && in_grp;
-                    const float *Rcol = Rs + ((mine ? i0s[k * kTcS + gs] : glo_k[k]) - iw0) * kTcS + gs;
+                    const float *Rcol = Rs + ((mine ? i0s[k * kTcS + gs] : glo[grp][k]) - iw0) * kTcS + gs;
                     const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
                     const float sc = invs[k * kTcS + gs];
                     if (k == 0) {
@@ -572,14 +691,18 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             bfj[i] = binf[j];
                         }
                     }
+                    // two bins per packed float32 operation (the same roundings as one at a time)
 #pragma unroll
-                    for (int i = 0; i < kTcBPT; ++i) {
-                        const float sf = ff + bfj[i];
-                        const int carry = sf >= 1.f;
-                        const float fr = sf - (float)carry;
-                        const float *rr = Rcol + (bj[i] + carry) * kTcS;
-                        const float r0 = rr[0], r1 = rr[kTcS];
-                        lin[i] = fmaf(sc, fmaf(fr, r1 - r0, r0), lin[i]);
+                    for (int i = 0; i < kTcBPT; i += 2) {
+                        const float2 sf = __fadd2_rn(make_float2(ff, ff), make_float2(bfj[i], bfj[i + 1]));
+                        const int c0 = sf.x >= 1.f, c1 = sf.y >= 1.f;
+                        const float2 fr = __fadd2_rn(sf, make_float2(-(float)c0, -(float)c1));
+                        const float *ra = Rcol + (bj[i] + c0) * kTcS, *rb = Rcol + (bj[i + 1] + c1) * kTcS;
+                        const float2 r0 = make_float2(ra[0], rb[0]), r1 = make_float2(ra[kTcS], rb[kTcS]);
+                        const float2 v = __ffma2_rn(fr, __fadd2_rn(r1, make_float2(-r0.x, -r0.y)), r0);
+                        const float2 l = __ffma2_rn(make_float2(sc, sc), v, make_float2(lin[i], lin[i + 1]));
+                        lin[i] = l.x;
+                        lin[i + 1] = l.y;
                     }
                     if (k == K - 1) {
                         // fold this thread's bins of the chunk into its running log-sum-exp
@@ -608,33 +731,54 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                                     cmx = fmaxf(cmx, lin[i]);
                             }
                         } else {
+                            // lin holds the overlap term; ln L = lin - gqd (max commutes with
+                            // the subtraction)
 #pragma unroll
-                            for (int i = 0; i < kTcBPT; ++i) {
-                                lin[i] -= gqd;
+                            for (int i = 0; i < kTcBPT; ++i)
                                 if (i < jn)
                                     cmx = fmaxf(cmx, lin[i]);
-                            }
+                            cmx -= gqd;
                         }
                         if (lnL_t && gok && in_grp) {
                             for (int i = 0; i < jn; ++i)
 #pragma unroll
                                 for (int u = 0; u < kTcBPT; ++u)
                                     if (u == i)
-                                        lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)lin[u];
+                                        lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)(kDM ? lin[u] : lin[u] - gqd);
                         }
                         if (jn > 0 && in_grp) {
                             const float nm = fmaxf(run_mx, cmx);
                             float cs = 0.f;
+                            if (kDM) {
 #pragma unroll
-                            for (int i = 0; i < kTcBPT; ++i)
-                                if (i < jn)
-                                    cs += __expf(lin[i] - nm);
+                                for (int i = 0; i < kTcBPT; ++i)
+                                    if (i < jn)
+                                        cs += __expf(lin[i] - nm);
+                            } else {
+                                // exp(lin - gqd - nm) = 2^(lin log2(e) - (gqd + nm) log2(e)), two bins
+                                // per packed operation
+                                const float off = (gqd + nm) * kLog2e;
+                                float2 cs2 = make_float2(0.f, 0.f);
+#pragma unroll
+                                for (int i = 0; i < kTcBPT; i += 2) {
+                                    const float2 x = __ffma2_rn(make_float2(lin[i], lin[i + 1]), make_float2(kLog2e, kLog2e),
+                                                                make_float2(-off, -off));
+                                    const float2 ev = make_float2(i < jn ? ex2_approx(x.x) : 0.f,
+                                                                  i + 1 < jn ? ex2_approx(x.y) : 0.f);
+                                    cs2 = __fadd2_rn(cs2, ev);
+                                }
+                                cs = cs2.x + cs2.y;
+                            }
                             run_sum = (run_mx == -INFINITY ? 0.f : run_sum * __expf(run_mx - nm)) + cs;
                             run_mx = nm;
                         }
 #pragma unroll
                         for (int i = 0; i < kTcBPT; ++i)
                             lin[i] = 0.f;
+                    }
+                    if (++k == K) {
+                        k = 0;
+                        j0 += jnom;
                     }
                 }
             }
@@ -675,7 +819,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
     }
-    // leave: make sure no bulk copy or MMA of this block is still in flight, then free TMEM
+    // leave: no bulk copy of this block may still be landing (after a failure the issuer may
+    // not have consumed the last windows; bounded wait), no MMA in flight; then free TMEM
+    if (warp == kTcStagerWarp && lane == 0)
+        for (int b = 0; b < 2; ++b)
+            if (nstaged[b] > 0)
+                tc::mbar_wait(bbar + b, (nstaged[b] - 1) & 1u, kWaitNs);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -696,7 +845,7 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!lnl_tc_fits(P, max_smem))
         return cudaErrorInvalidConfiguration;
-    const size_t smem = tc_layout(P.K, P.M, P.n_t).end;
+    const size_t smem = tc_layout(P.K, P.M, P.n_t, P.tc_uv != 0).end;
     auto kern = P.dist_marg ? lnl_tc_kernel<true> : lnl_tc_kernel<false>;
     cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess)
