@@ -222,7 +222,7 @@ int validate(const rift_ile_config *c)
 __global__ void prep_overlaps_kernel(const double2 *__restrict__ Q64, const double2 *__restrict__ U64,
                                      const double2 *__restrict__ V64, int K, int M, int n_q, int n_q_pad,
                                      float *__restrict__ Qr32, float2 *__restrict__ U32, float2 *__restrict__ V32,
-                                     float4 *__restrict__ UV32, int *err)
+                                     int *err)
 {
     const int64_t total = (int64_t)K * 2 * M * n_q_pad;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -246,7 +246,6 @@ __global__ void prep_overlaps_kernel(const double2 *__restrict__ Q64, const doub
             atomicOr(err, kErrNonFinite);
         U32[e] = make_float2((float)u.x, (float)u.y);
         V32[e] = make_float2((float)v.x, (float)v.y);
-        UV32[e] = make_float4((float)u.x, (float)u.y, (float)v.x, (float)v.y);
     }
 }
 
@@ -617,7 +616,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
     if ((rc = dalloc(h, &h->Q64, (size_t)K * M * cfg->n_q)) || (rc = dalloc(h, &h->U64, (size_t)K * M * M)) ||
         (rc = dalloc(h, &h->V64, (size_t)K * M * M)) || (rc = dalloc(h, &h->Qr32, (size_t)K * 2 * M * P.n_q_pad)) ||
         (rc = dalloc(h, &h->U32, (size_t)K * M * M)) || (rc = dalloc(h, &h->V32, (size_t)K * M * M)) ||
-        (rc = dalloc(h, &h->UV32, (size_t)K * M * M)) ||
+        (rc = dalloc(h, &h->Ttc, (size_t)K * 2 * ((2 * M + 15) / 16 * 16) * ((2 * M + 15) / 16 * 16))) ||
+        (rc = dalloc(h, &h->tt_exp, (size_t)K)) ||
         (rc = dalloc(h, &h->bin_i, (size_t)cfg->n_t)) || (rc = dalloc(h, &h->bin_f, (size_t)cfg->n_t)) ||
         (rc = dalloc(h, &h->theta, (size_t)N * 6)) || (rc = dalloc(h, &h->lnpw, (size_t)N)) ||
         (rc = dalloc(h, &h->lnL, (size_t)N)) || (rc = dalloc(h, &h->lnw, (size_t)N)) ||
@@ -669,7 +669,6 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-        P.tc_uv = lnl_tc_uv_fits(P, max_smem) ? 1 : 0;
         h->tc_ok = major == 10 && lnl_tc_fits(P, max_smem);
         const char *env = std::getenv("RIFT_ILE_TC");
         if (env && env[0] == '0')
@@ -689,7 +688,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
     P.Qr32 = h->Qr32;
     P.U32 = h->U32;
     P.V32 = h->V32;
-    P.UV32 = h->UV32;
+    P.Ttc = h->Ttc;
+    P.tt_exp = h->tt_exp;
     *out = h;
     return RIFT_OK;
 }
@@ -718,7 +718,8 @@ int64_t rift_ile_footprint(const rift_ile_config *cfg)
     const int64_t nq = cfg->n_q, nq_pad = ((nq + 3) & ~3) + kQPad;
     const int64_t groups = (nq + 7) / 8 + 17, kp = (2 * M + 15) / 16 * 16;
     const int64_t sizes[] = {
-        K * M * nq * 16, 2 * K * M * M * 16, K * 2 * M * nq_pad * 4, 2 * K * M * M * 8, K * M * M * 16, 2 * nt * 4,
+        K * M * nq * 16, 2 * K * M * M * 16, K * 2 * M * nq_pad * 4, 2 * K * M * M * 8, K * 2 * kp * kp * 2, K * 4,
+        2 * nt * 4,
         N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, (int64_t)sort_scratch_words(N) * 4, 16, 16,
         K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 12 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
         N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16};
@@ -857,12 +858,13 @@ int install_overlaps(rift_ile_t *h)
     int64_t tot = (int64_t)K * 2 * M * h->prob.n_q_pad;
     int grid = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
     prep_overlaps_kernel<<<grid, 256, 0, h->stream>>>(h->Q64, h->U64, h->V64, K, M, nq, h->prob.n_q_pad, h->Qr32,
-                                                      h->U32, h->V32, h->UV32, h->err);
+                                                      h->U32, h->V32, h->err);
     CK(cudaGetLastError());
     h->launches += 1;
     if (h->tc_ok) {
         CK(launch_prep_tc(h->Q64, K, M, nq, h->prob.tc_groups, h->qmax_bits, h->Qtc, h->stream));
-        h->launches += 2;
+        CK(launch_prep_tt(h->U64, h->V64, K, M, h->Ttc, h->tt_exp, h->stream));
+        h->launches += 3;
     }
     int rc = sync_and_err(h);
     h->have_overlaps = (rc == RIFT_OK);

@@ -63,12 +63,16 @@ struct Problem {
     const float *Qr32;      // [K][2M][n_q_pad] split planes, zero padded
     const float2 *U32;
     const float2 *V32;
-    const float4 *UV32;     // [K][M][M] (U re, U im, V re, V im) interleaved
     // tensor-core copy of Q: [K][hi, lo][tc_groups][Kp/8][8][8] float16, scaled by 2^e
     // with e from the float bits of max|Q| (*qmax_bits)
     const __half *Qtc;
     int tc_groups;
-    int tc_uv;              // tensor-core kernel keeps the upper triangle of UV32 in shared memory
+    // Template term of the tensor-core kernel as a real quadratic form: with z the 2M real
+    // components of c_k (re, im per mode), c^H U c + Re c^T V c = z^T T_k z.  Ttc holds
+    // T_k^T (= B operand, rows n, K-major) scaled by 2^tt_exp[k], float16 hi/lo:
+    // [K][hi, lo][Kp/8 row groups][Kp/8][8][8].
+    const __half *Ttc;
+    const int *tt_exp;
     const unsigned int *qmax_bits;
 };
 

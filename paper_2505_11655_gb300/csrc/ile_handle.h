@@ -34,7 +34,8 @@ struct rift_ile {
     double2 *Q64 = nullptr, *U64 = nullptr, *V64 = nullptr;
     float *Qr32 = nullptr;
     float2 *U32 = nullptr, *V32 = nullptr;
-    float4 *UV32 = nullptr;
+    __half *Ttc = nullptr;   // template matrices for the tensor-core kernel (see Problem::Ttc)
+    int *tt_exp = nullptr;
     int *bin_i = nullptr;
     float *bin_f = nullptr;
     // per-sample buffers

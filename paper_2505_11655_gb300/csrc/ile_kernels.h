@@ -87,8 +87,9 @@ size_t lnl_fp32_smem_bytes(const Problem &P);
 
 // Tensor-core variant of the float32 tiled path (tiles of 128 samples, tcgen05 MMA).
 bool lnl_tc_fits(const Problem &P, int max_smem);
-// Whether the tensor-core kernel can also hold the Gram table (upper triangle) in shared memory.
-bool lnl_tc_uv_fits(const Problem &P, int max_smem);
+// Template matrices T_k of the tensor-core kernel from the float64 Gram matrices.
+cudaError_t launch_prep_tt(const double2 *U64, const double2 *V64, int K, int M, __half *Ttc, int *tt_exp,
+                           cudaStream_t st);
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
                           int *tile_counter, cudaStream_t st);

@@ -55,14 +55,14 @@ __device__ __forceinline__ float ex2_approx(float x)
 constexpr int kTcSpreadLimit = 64;
 
 struct TcLayout {
-    size_t a, b, r, bini, binf, i0, f0, inv, quad, gid, lse, uv, bar, tptr, end;
-    size_t sky, e5, par, pw, pe, fx, qpart;   // prologue scratch, aliased on the B buffers
+    size_t a, b, r, tt, bini, binf, i0, f0, inv, qsc, gid, lse, bar, tptr, end;
+    size_t sky, e5, par, pw, pe, fx;   // prologue scratch, aliased on the B buffers
     int kp;
 };
 
 __host__ __device__ inline size_t tc_al(size_t o, size_t a = 128) { return (o + a - 1) / a * a; }
 
-__host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t, bool uv)
+__host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
 {
     TcLayout L;
     L.kp = (2 * M + 15) / 16 * 16;
@@ -80,23 +80,22 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t, bool uv)
     L.pw = s;    s = tc_al(s + (size_t)2 * kTcPow * kTcS * 4, 16);
     L.pe = s;    s = tc_al(s + (size_t)(kMaxL + 1) * kTcS * 8, 16);
     L.fx = s;    s = tc_al(s + (size_t)K * kTcS * 8, 16);
-    L.qpart = s; s = tc_al(s + (size_t)kTcQ * kTcS * 4, 16);
     o = tc_al(L.b + (bbytes > s - L.b ? bbytes : s - L.b));
+    // R tile; during the prologue it holds Y [M][kTcS] and, behind it, the template
+    // matrices T_k (staged by a bulk copy at the start of every tile)
     L.r = o;
-    const size_t rbytes = (size_t)kTcW * kTcS * 4, cbytes = (size_t)M * kTcS * 8;
-    o = tc_al(o + (rbytes > cbytes ? rbytes : cbytes), 16);
+    L.tt = tc_al(L.r + (size_t)M * kTcS * 8);
+    const size_t rbytes = (size_t)kTcW * kTcS * 4, pbytes = L.tt - L.r + (size_t)K * 2 * L.kp * L.kp * 2;
+    o = tc_al(o + (rbytes > pbytes ? rbytes : pbytes), 16);
     L.bini = o; o = tc_al(o + (size_t)n_t * 4, 16);
     L.binf = o; o = tc_al(o + (size_t)n_t * 4, 16);
     L.i0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.f0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.inv = o;  o = tc_al(o + (size_t)K * kTcS * 4, 16);
-    L.quad = o; o = tc_al(o + (size_t)kTcS * 4, 16);
+    L.qsc = o;  o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.gid = o;  o = tc_al(o + (size_t)kTcS * 4, 16);
     L.lse = o;  o = tc_al(o + (size_t)2 * kTcQ * kTcS * 4, 16);
-    L.uv = o;   // [pair a <= b][K] float4, row-major upper triangle (when it fits)
-    if (uv)
-        o = tc_al(o + (size_t)(M * (M + 1) / 2) * K * 16, 16);
-    L.bar = o;  o = tc_al(o + 6 * 8, 16);
+    L.bar = o;  o = tc_al(o + 8 * 8, 16);
     L.tptr = o; o = tc_al(o + 16, 16);
     L.end = o;
     return L;
@@ -106,14 +105,9 @@ bool lnl_tc_fits(const Problem &P, int max_smem)
 {
     if (P.Qtc == nullptr || P.tc_groups <= 0)
         return false;
-    const TcLayout L = tc_layout(P.K, P.M, P.n_t, P.tc_uv != 0);
+    const TcLayout L = tc_layout(P.K, P.M, P.n_t);
     // plus the kernel's static shared memory (sub-group table, ~5 KB)
     return L.kp <= 64 && L.end + 8192 <= (size_t)max_smem;
-}
-
-bool lnl_tc_uv_fits(const Problem &P, int max_smem)
-{
-    return tc_layout(P.K, P.M, P.n_t, true).end + 8192 <= (size_t)max_smem;
 }
 
 // ---------------------------------------------------------------- Q copy for the tensor path
@@ -185,6 +179,70 @@ cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- template matrices
+
+// One block per detector k.  With z = (Re c_0, Im c_0, Re c_1, ...) the template term of
+// detector k is c^H U c + Re(c^T V c) = z^T T z with (U = Ur + i Ui, V = Vr + i Vi)
+//   T[2a][2b] = Ur + Vr,  T[2a+1][2b+1] = Ur - Vr,  T[2a][2b+1] = -Ui - Vi,  T[2a+1][2b] = Ui - Vi
+// (entries ab).  Stored transposed (row n = column n of T) as the B operand of W = Z T,
+// scaled by 2^e with max|T| 2^e in [2^13, 2^14), float16 hi/lo, in the canonical K-major
+// layout of the other operands.
+__device__ __forceinline__ double tt_entry(const double2 *U, const double2 *V, int M, int r, int c)
+{
+    const int a = r >> 1, b = c >> 1;
+    const double2 u = U[(size_t)a * M + b], v = V[(size_t)a * M + b];
+    if (!(r & 1))
+        return (c & 1) ? -u.y - v.y : u.x + v.x;
+    return (c & 1) ? u.x - v.x : u.y - v.y;
+}
+
+__global__ void prep_tt_kernel(const double2 *__restrict__ U64, const double2 *__restrict__ V64, int M, int kp,
+                               __half *__restrict__ Ttc, int *__restrict__ tt_exp)
+{
+    __shared__ float red[32];
+    __shared__ int e_s;
+    const int k = blockIdx.x, R2 = 2 * M;
+    const double2 *U = U64 + (size_t)k * M * M, *V = V64 + (size_t)k * M * M;
+    float m = 0.f;
+    for (int e = threadIdx.x; e < R2 * R2; e += blockDim.x)
+        m = fmaxf(m, fabsf((float)tt_entry(U, V, M, e / R2, e % R2)));
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float mx = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            mx = fmaxf(mx, red[w]);
+        int ex = 0;
+        if (mx > 0.f)
+            frexpf(mx, &ex);
+        e_s = mx > 0.f ? 14 - ex : 0;
+        tt_exp[k] = e_s;
+    }
+    __syncthreads();
+    const float sc = ldexpf(1.f, e_s);
+    const int kc = kp / 8;
+    __half *hi = Ttc + (size_t)k * 2 * kp * kp, *lo = hi + (size_t)kp * kp;
+    for (int e = threadIdx.x; e < kp * kp; e += blockDim.x) {
+        const int n = e / kp, c = e % kp;   // row n of the operand = column n of T, component c
+        const float v = (n < R2 && c < R2) ? (float)tt_entry(U, V, M, c, n) * sc : 0.f;
+        const __half h = __float2half_rn(v);
+        const size_t off = ((size_t)((n >> 3) * kc + (c >> 3)) * 8 + (n & 7)) * 8 + (c & 7);
+        hi[off] = h;
+        lo[off] = __float2half_rn(v - __half2float(h));
+    }
+}
+
+cudaError_t launch_prep_tt(const double2 *U64, const double2 *V64, int K, int M, __half *Ttc, int *tt_exp,
+                           cudaStream_t st)
+{
+    prep_tt_kernel<<<K, 256, 0, st>>>(U64, V64, M, (2 * M + 15) / 16 * 16, Ttc, tt_exp);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- the kernel
 
 // kDM: distance marginalisation (a separate instantiation, so that the plain path keeps
@@ -197,7 +255,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 {
     extern __shared__ __align__(128) unsigned char sm[];
     const int K = P.K, M = P.M, NT = P.n_t;
-    const TcLayout L = tc_layout(K, M, NT, P.tc_uv != 0);
+    const TcLayout L = tc_layout(K, M, NT);
     const int kp = L.kp, kcores = kp / 8;
     __half *As = reinterpret_cast<__half *>(sm + L.a);          // [K][2][kTcS x kp] canonical K-major
     __half *Bs = reinterpret_cast<__half *>(sm + L.b);          // [2 buf][2 part][kTcW x kp]
@@ -207,12 +265,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     int *i0s = reinterpret_cast<int *>(sm + L.i0);              // [K][kTcS]
     float *f0s = reinterpret_cast<float *>(sm + L.f0);
     float *invs = reinterpret_cast<float *>(sm + L.inv);        // [K][kTcS] 2^-(row exponent + Q exponent)
-    float *qds = reinterpret_cast<float *>(sm + L.quad);
+    float *qsc = reinterpret_cast<float *>(sm + L.qsc);         // [K][kTcS] 2^-(2 row exponent)
     uint32_t *gid = reinterpret_cast<uint32_t *>(sm + L.gid);
-    const float4 *uvs = P.tc_uv ? reinterpret_cast<const float4 *>(sm + L.uv) : nullptr;
     uint64_t *bbar = reinterpret_cast<uint64_t *>(sm + L.bar);  // [0,1] windows staged
     uint64_t *fullb = bbar + 2;   // [0,1] MMAs of an accumulator complete (tcgen05.commit)
     uint64_t *emptyb = bbar + 4;  // [0,1] accumulator drained by the 16 consumer warps
+    uint64_t *tbar = bbar + 6;    // template matrices staged (once per tile)
+    uint64_t *wbar = bbar + 7;    // template products W = Z T complete (once per tile)
     uint32_t *tptr = reinterpret_cast<uint32_t *>(sm + L.tptr);
     double *sky = reinterpret_cast<double *>(sm + L.sky);      // [3][kTcS] float64 unit vector n
     float *e5 = reinterpret_cast<float *>(sm + L.e5);          // [5][kTcS] sky basis of the response
@@ -220,8 +279,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     float *pw = reinterpret_cast<float *>(sm + L.pw);          // [2 kTcPow][kTcS] cos^q, sin^q (iota/2)
     float2 *pe = reinterpret_cast<float2 *>(sm + L.pe);        // [kMaxL + 1][kTcS] exp(-i j phi)
     float2 *fx = reinterpret_cast<float2 *>(sm + L.fx);        // [K][kTcS] (D_ref/D) F_k
-    float *qpart = reinterpret_cast<float *>(sm + L.qpart);
     float *lse = reinterpret_cast<float *>(sm + L.lse);         // [2][kTcQ][kTcS] running max, sum
+    float *qsum = lse;                                          // [kTcQ][kTcS] template term partials
     float2 *Ys = reinterpret_cast<float2 *>(Rs);               // [M][kTcS] -2Y_lm(iota, -phi)
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
     __shared__ int glo[kTcS][kMaxDet], ghi[kTcS][kMaxDet], gstart[kTcS + 1];
@@ -235,32 +294,30 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     const size_t part_halves = (size_t)kTcW * kp;                 // one B part
     const uint32_t part_bytes = (uint32_t)(part_halves * 2);
     const int qexp = q_exponent(*P.qmax_bits);
+    // Shared-memory matrix descriptors (used by the issuer only; recomputed where used so
+    // that nothing stays live in the other warps): the high word (stride byte offset,
+    // version) is the same for every operand; the low word holds the start address and the
+    // leading byte offset, so an operand offset is an addition to the address field (all
+    // addresses < 256 KB: no carry out of it).
+    auto desc = [&](uint32_t lo) { return ((uint64_t)(((sbo >> 4) & 0x3FFFu) | (1u << 14)) << 32) | lo; };
+    auto desc_lo = [&](const void *p) { return ((tc::smem_u32(p) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16); };
+    const uint32_t a_part = (uint32_t)(kTcS * kp * 2) >> 4;
 
     for (int j = tid; j < NT; j += blockDim.x) {
         bini[j] = bt.bin_i[j];
         binf[j] = bt.bin_f[j];
     }
-    if (P.tc_uv) {
-        // Gram table, upper triangle in row-major pair order, all detectors of a pair adjacent
-        float4 *uvw = reinterpret_cast<float4 *>(sm + L.uv);
-        const int npairs = M * (M + 1) / 2;
-        for (int e = tid; e < npairs * K; e += blockDim.x) {
-            const int p = e / K, k = e - p * K;
-            int a = 0, b = p;
-            while (b >= M - a) {
-                b -= M - a;
-                ++a;
-            }
-            uvw[e] = P.UV32[((size_t)k * M + a) * M + a + b];
-        }
-    }
+    // tensor memory: two 128-column accumulators of the main contraction, then the
+    // template products W_k = Z_k T_k at column 256 + 64 k
     if (warp == 0)
-        tc::tmem_alloc(tptr, 256);
+        tc::tmem_alloc(tptr, 512);
     if (tid == 0) {
         for (int i = 0; i < 4; ++i)
             tc::mbar_init(bbar + i, 1);
         for (int i = 4; i < 6; ++i)
             tc::mbar_init(bbar + i, kTcConsumers / 32);
+        tc::mbar_init(tbar, 1);
+        tc::mbar_init(wbar, 1);
         tc::fence_mbar_init();
         abort_s = 0;
     }
@@ -268,14 +325,19 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tptr;
-    // phase counters per buffer, each kept by the thread that waits on the barrier: windows
-    // staged (stager: nstaged) and consumed (issuer: nstage), MMA commits (issuer) and
-    // completions (consumers: nfull), accumulator drains (issuer)
-    uint32_t nstaged[2] = {0u, 0u}, nstage[2] = {0u, 0u}, ncommit[2] = {0u, 0u}, nfull[2] = {0u, 0u},
-             ndrain[2] = {0u, 0u};
+    // Barrier phase parities, bit b for buffer b, each kept by the thread that waits: windows
+    // staged into b so far (stager: stg, and used = b staged at least once), windows consumed
+    // (issuer: cons), accumulator drains awaited (issuer: drn) and commits not yet matched by
+    // a drain wait (issuer: pend), MMA completions awaited (consumers: full).
+    uint32_t stg = 0u, used = 0u, cons = 0u, drn = 0u, pend = 0u, full = 0u;
+    // tiles begun by this block: parity of the per-tile barriers (tbar, wbar)
+    uint32_t tpar = 0u;
     const bool producer = warp >= kTcIssuerWarp;   // issuer or stager
 
     for (;;) {
+        // the R tile, written by this thread's drains, is the target of the next tile's bulk
+        // copy of the template matrices
+        tc::fence_proxy_async_smem();
         if (tid == 0)
             tile_s = abort_s ? INT_MAX : atomicAdd(tile_counter, 1);
         if (tid < kMaxDet) {
@@ -286,6 +348,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         const int64_t tile = tile_s;
         if (tile >= n_tiles)
             break;
+        if (warp == kTcStagerWarp && lane == 0) {
+            // template matrices into the tail of the R tile (free: the previous tile's last
+            // gather is behind the barrier above)
+            const uint32_t tt_bytes = (uint32_t)(K * 2 * kp * kp * 2);
+            tc::mbar_expect_tx(tbar, tt_bytes);
+            tc::bulk_g2s(sm + L.tt, P.Ttc, tt_bytes, tbar);
+        }
 
         // ---------------- prologue A: sky trigonometry (float64) and per-sample scalars
         if (tid < kTcS) {
@@ -417,76 +486,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             Ys[m * kTcS + s] = make_float2(d * e.x, d * (mm < 0 ? -e.y : e.y));
         }
         __syncthreads();
-        // ---------------- D: template term.  With c_k = f_k Y (f_k = fx_k):
-        //   c_k^H U_k c_k = |f_k|^2 Y^H U_k Y,   c_k^T V_k c_k = f_k^2 Y^T V_k Y,
-        // so each product of two components of Y (pair a <= b) is formed once and serves
-        // every detector.  The pairs of the upper triangle are split evenly over kTcQ
-        // threads per sample; off-diagonal pairs count twice (U Hermitian, V symmetric).
-        if (tid < kTcConsumers) {
-            const int s = tid & (kTcS - 1), part = tid >> 7;
-            const int npairs = M * (M + 1) / 2, per = (npairs + kTcQ - 1) / kTcQ;
-            const int p0 = min(npairs, part * per), p1 = min(npairs, p0 + per);
-            int a = 0, b = p0;   // pair p0 in row-major order of the upper triangle
-            while (a < M && b >= M - a) {
-                b -= M - a;
-                ++a;
-            }
-            b += a;
-            float2 hu[kMaxDet], hv[kMaxDet];
-#pragma unroll
-            for (int k = 0; k < kMaxDet; ++k) {
-                hu[k] = make_float2(0.f, 0.f);
-                hv[k] = make_float2(0.f, 0.f);
-            }
-            // the pair loop, with the Gram entries from shared memory or (when the table did
-            // not fit) from the global copy
-            auto pair_loop = [&](auto gram) {
-                for (int q = p0; q < p1; ++a, b = a) {
-                    // row a, columns b .. bend - 1 of this thread's range; pair (a, c) has index qr + c
-                    const int bend = min(M, b + (p1 - q));
-                    const int qr = q - b;
-                    q += bend - b;
-                    const float2 ya = Ys[a * kTcS + s];
-#pragma unroll 4
-                    for (int c = b; c < bend; ++c) {
-                        const float2 yb = Ys[c * kTcS + s];
-                        const float w = c == a ? 1.f : 2.f;
-                        const float xr = w * ya.x, xi = w * ya.y;
-                        // conj(w Y_a) Y_b = (pr, pi) and (w Y_a) Y_b = (sr, si), packed
-                        const float2 u = __fmul2_rn(make_float2(xr, xr), yb);
-                        const float2 pq = __ffma2_rn(make_float2(xi, -xi), make_float2(yb.y, yb.x), u);
-                        const float2 sq = __ffma2_rn(make_float2(-xi, xi), make_float2(yb.y, yb.x), u);
-#pragma unroll
-                        for (int k = 0; k < kMaxDet; ++k) {
-                            if (k < K) {
-                                const float4 g = gram(qr + c, a, c, k);   // U re, U im, V re, V im
-                                hu[k] = __ffma2_rn(make_float2(g.x, g.y), pq, hu[k]);   // Re(U P) = x - y
-                                hv[k] = __ffma2_rn(make_float2(g.z, g.z), sq, hv[k]);   // V S
-                                hv[k] = __ffma2_rn(make_float2(-g.w, g.w), make_float2(sq.y, sq.x), hv[k]);
-                            }
-                        }
-                    }
-                }
-            };
-            if (uvs)
-                pair_loop([&](int pidx, int, int, int k) { return uvs[pidx * K + k]; });
-            else
-                pair_loop([&](int, int ra, int cb, int k) { return __ldg(P.UV32 + ((size_t)k * M + ra) * M + cb); });
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxDet; ++k) {
-                if (k < K) {
-                    const float2 f = fx[k * kTcS + s];
-                    const float fa = f.x * f.x + f.y * f.y, f2r = f.x * f.x - f.y * f.y, f2i = 2.f * f.x * f.y;
-                    acc += fa * (hu[k].x - hu[k].y) + (f2r * hv[k].x - f2i * hv[k].y);
-                }
-            }
-            qpart[part * kTcS + s] = acc;
-        }
-        __syncthreads();
-        if (tid < kTcS)
-            qds[tid] = (float)P.kappa * ((qpart[tid] + qpart[kTcS + tid]) + (qpart[2 * kTcS + tid] + qpart[3 * kTcS + tid]));
-
         // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector);
         // each thread writes one sample row of a detector, 8 components (4 modes) per 16-byte store
         {
@@ -504,6 +503,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 const int es = mx > 0.f ? 14 - ex : 0;
                 const float sc = ldexpf(1.f, es);
                 invs[k * kTcS + s] = ldexpf(1.f, -es - qexp);
+                qsc[k * kTcS + s] = ldexpf(1.f, -2 * es);
                 __half *Ahi = As + (size_t)(k * 2) * kTcS * kp;
                 __half *Alo = Ahi + (size_t)kTcS * kp;
                 const int rowbase = ((s >> 3) * kcores * 8 + (s & 7)) * 8;
@@ -535,9 +535,83 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         // gather / fold ownership: thread -> sample s, bin quarter h of every chunk
         const int gs = tid & (kTcS - 1), gh = (tid >> 7) & (kTcQ - 1);
         const bool gok = !producer && gid[gs] != 0xffffffffu;
-        const float gqd = qds[gs];
+
+        // ---------------- D: template term on the tensor cores.  W_k = Z_k T_k (Z_k: the A
+        // operand, row s = 2^es_ks z_ks; T_k scaled by 2^e_k), then
+        //   z_ks^T T_k z_ks = 2^-(2 es_ks + e_k) sum_n Z_k[s][n] W_k[s][n].
+        int wfail = 0;
+        if (warp == kTcIssuerWarp) {
+            if (lane == 0) {
+                if (!tc::mbar_wait(tbar, tpar, kWaitNs)) {
+                    wfail = 1;
+                } else {
+                    tc::tc_fence_after();
+                    const uint32_t wdesc = tc::idesc_f16_f32(kTcS, kp);
+                    const uint32_t a_lo0 = desc_lo(As), t_lo0 = desc_lo(sm + L.tt);
+                    const uint32_t t_part = (uint32_t)(kp * kp * 2) >> 4;
+                    for (int k = 0; k < K; ++k) {
+                        const uint32_t d = tmem + 256u + 64u * (uint32_t)k;
+                        const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
+                        const uint32_t th = t_lo0 + (uint32_t)(2 * k) * t_part, tl = th + t_part;
+                        for (int kk = 0; kk < kp / 16; ++kk) {
+                            const uint32_t o = (uint32_t)kk * 16u;
+                            // all four hi/lo products (the template term is cheap on the tensor pipe)
+                            tc::mma_f16(d, desc(ah + o), desc(th + o), wdesc, kk > 0);
+                            tc::mma_f16(d, desc(ah + o), desc(tl + o), wdesc, 1);
+                            tc::mma_f16(d, desc(al + o), desc(th + o), wdesc, 1);
+                            tc::mma_f16(d, desc(al + o), desc(tl + o), wdesc, 1);
+                        }
+                    }
+                    tc::mma_commit(wbar);
+                }
+            }
+            wfail = __shfl_sync(0xffffffffu, wfail, 0);
+        } else if (!producer) {
+            // warp (q, cb) drains 16-column chunks cb, cb + 4, ... of the K W tiles for the
+            // 32 samples of its lane quarter q
+            int ok = 1;
+            if (lane == 0)
+                ok = tc::mbar_wait(wbar, tpar, kWaitNs) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            tc::tc_fence_after();
+            const int q = warp & 3, cb = warp >> 2, s = 32 * q + lane;
+            float qp = 0.f;
+            if (ok) {
+                const int cpd = kp / 16;
+                const int rowbase = ((s >> 3) * kcores * 8 + (s & 7)) * 8;
+                for (int c = cb; c < K * cpd; c += 4) {
+                    const int k = c / cpd, n0 = (c - k * cpd) * 16;
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256u + 64u * (uint32_t)k + (uint32_t)n0, v);
+                    const __half *zh = As + (size_t)(k * 2) * kTcS * kp + rowbase + (n0 >> 3) * 64;
+                    const __half *zl = zh + (size_t)kTcS * kp;
+                    tc::tmem_ld_wait();
+                    float acc = 0.f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {   // 8 components (one core column) at a time
+                        const uint4 hq = *reinterpret_cast<const uint4 *>(zh + 64 * h);
+                        const uint4 lq = *reinterpret_cast<const uint4 *>(zl + 64 * h);
+                        const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w}, lw[4] = {lq.x, lq.y, lq.z, lq.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float2 zhf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[j]));
+                            const float2 zlf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[j]));
+                            acc = fmaf(zhf.x + zlf.x, __uint_as_float(v[8 * h + 2 * j]), acc);
+                            acc = fmaf(zhf.y + zlf.y, __uint_as_float(v[8 * h + 2 * j + 1]), acc);
+                        }
+                    }
+                    qp += acc * ldexpf(qsc[k * kTcS + s], -P.tt_exp[k]);
+                }
+            }
+            qsum[cb * kTcS + s] = qp;
+            wfail = !ok;
+        }
+        tc::tc_fence_before();
+        int failed = __syncthreads_or(wfail);
+        tpar ^= 1u;
+        const float gqd =
+            (float)P.kappa * ((qsum[gs] + qsum[kTcS + gs]) + (qsum[2 * kTcS + gs] + qsum[3 * kTcS + gs]));
         float run_mx = -INFINITY, run_sum = 0.f;
-        int failed = 0;
         const int ngroups = ngroups_s;
         for (int grp = 0; grp < ngroups && !failed; ++grp) {
             int spread = 0;
@@ -559,28 +633,20 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             if (warp == kTcIssuerWarp) {
                 // ============ issuer warp, lane 0: one MMA batch per staged window
                 if (lane == 0) {
-                    // shared-memory matrix descriptors: the high word (stride byte offset,
-                    // version) is the same for every operand; the low word holds the start
-                    // address and the leading byte offset, so an operand offset is an addition
-                    // to the address field (all addresses < 256 KB: no carry out of it)
-                    const uint32_t dhi = ((sbo >> 4) & 0x3FFFu) | (1u << 14);
-                    const uint32_t lbo_f = (128u >> 4) << 16;
-                    const uint32_t a_lo0 = ((tc::smem_u32(As) & 0x3FFFFu) >> 4) | lbo_f;
-                    const uint32_t b_lo0 = ((tc::smem_u32(Bs) & 0x3FFFFu) >> 4) | lbo_f;
-                    const uint32_t a_part = (uint32_t)(kTcS * kp * 2) >> 4, b_part = part_bytes >> 4;
-                    auto desc = [&](uint32_t lo) { return ((uint64_t)dhi << 32) | lo; };
+                    const uint32_t a_lo0 = desc_lo(As), b_lo0 = desc_lo(Bs), b_part = part_bytes >> 4;
                     int k = 0;
                     for (int t = 0; t < n_steps && !failed; ++t, k = k + 1 == K ? 0 : k + 1) {
                         const int b = t & 1;
                         // window t staged; accumulator b drained by the consumers
-                        if (!tc::mbar_wait(bbar + b, nstage[b] & 1u, kWaitNs) ||
-                            (ncommit[b] > ndrain[b] && !tc::mbar_wait(emptyb + b, ndrain[b] & 1u, kWaitNs))) {
+                        const uint32_t bit = 1u << b;
+                        if (!tc::mbar_wait(bbar + b, (cons >> b) & 1u, kWaitNs) ||
+                            ((pend & bit) && !tc::mbar_wait(emptyb + b, (drn >> b) & 1u, kWaitNs))) {
                             failed = 1;
                             break;
                         }
-                        ++nstage[b];
-                        if (ncommit[b] > ndrain[b])
-                            ++ndrain[b];
+                        cons ^= bit;
+                        if (pend & bit)
+                            drn ^= bit;
                         tc::tc_fence_after();
                         const uint32_t d = tmem + (uint32_t)(b * kTcW);
                         const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
@@ -592,7 +658,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             tc::mma_f16(d, desc(al + o), desc(bh + o), idesc, 1);
                         }
                         tc::mma_commit(fullb + b);
-                        ++ncommit[b];
+                        pend |= bit;
                     }
                     if (failed)
                         abort_s = 1;
@@ -608,7 +674,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     int sk = 0, sch = 0;   // detector and chunk of the next window
                     for (int t = 0; t < n_steps && !failed; ++t) {
                         const int b = t & 1;
-                        if (nstaged[b] > 0 && !tc::mbar_wait(fullb + b, (nstaged[b] - 1) & 1u, kWaitNs)) {
+                        const uint32_t bit = 1u << b;
+                        if ((used & bit) && !tc::mbar_wait(fullb + b, ((stg >> b) & 1u) ^ 1u, kWaitNs)) {
                             failed = 1;
                             break;
                         }
@@ -618,7 +685,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                         tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
                         tc::bulk_g2s(dst, src, part_bytes, bbar + b);
                         tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
-                        ++nstaged[b];
+                        stg ^= bit;
+                        used |= bit;
                         if (++sk == K) {
                             sk = 0;
                             ++sch;
@@ -645,8 +713,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     // one lane per warp waits for the MMAs of step t
                     int ok = 1;
                     if (lane == 0)
-                        ok = tc::mbar_wait(fullb + b, nfull[b] & 1u, kWaitNs) ? 1 : 0;
-                    ++nfull[b];
+                        ok = tc::mbar_wait(fullb + b, (full >> b) & 1u, kWaitNs) ? 1 : 0;
+                    full ^= 1u << b;
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     tc::tc_fence_after();
                     // The rows of sample quarter q (TMEM lanes 32q..) are drained and gathered by
@@ -662,12 +730,16 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                         // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
                         const int q = warp & 3, cb = warp >> 2;
                         float *Rcol = Rs + (32 * cb) * kTcS + 32 * q + lane;
-                        uint32_t v[32];
-                        tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcW + 32 * cb), v);
-                        tc::tmem_ld_wait();
+                        // two loads of 16 columns (fewer live registers than one of 32)
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            Rcol[i * kTcS] = __uint_as_float(v[i]);
+                        for (int h = 0; h < 2; ++h) {
+                            uint32_t v[16];
+                            tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcW + 32 * cb + 16 * h), v);
+                            tc::tmem_ld_wait();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                Rcol[(16 * h + i) * kTcS] = __uint_as_float(v[i]);
+                        }
                     }
                     tc::tc_fence_before();
                     __syncwarp();
@@ -823,13 +895,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     // not have consumed the last windows; bounded wait), no MMA in flight; then free TMEM
     if (warp == kTcStagerWarp && lane == 0)
         for (int b = 0; b < 2; ++b)
-            if (nstaged[b] > 0)
-                tc::mbar_wait(bbar + b, (nstaged[b] - 1) & 1u, kWaitNs);
+            if ((used >> b) & 1u)
+                tc::mbar_wait(bbar + b, ((stg >> b) & 1u) ^ 1u, kWaitNs);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 256);
+        tc::tmem_dealloc(tmem, 512);
     }
 }
 
@@ -845,7 +917,7 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (!lnl_tc_fits(P, max_smem))
         return cudaErrorInvalidConfiguration;
-    const size_t smem = tc_layout(P.K, P.M, P.n_t, P.tc_uv != 0).end;
+    const size_t smem = tc_layout(P.K, P.M, P.n_t).end;
     auto kern = P.dist_marg ? lnl_tc_kernel<true> : lnl_tc_kernel<false>;
     cudaError_t e = allow_max_dynamic_smem(kern);
     if (e != cudaSuccess)

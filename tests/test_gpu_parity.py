@@ -269,7 +269,12 @@ def test_tc_path_bins_and_cuda_core_agree(G, orc, monkeypatch):
     exp, ebins, quad = orc.lnL(p, th, want_bins=True)
     assert np.all(np.abs(b_tc - ebins) <= fp32_floor(ebins, quad[:, None]))
     assert_fp32_close(g_tc, exp, quad)
-    assert np.max(np.abs(g_tc - g_cc)) <= 2e-3
+    # two float32 evaluations, each within the float32 bar of the oracle, agree within the
+    # sum of their bars
+    d = np.abs(g_tc - g_cc)
+    near = exp >= np.max(exp) - 100.0
+    assert np.max(d[near]) <= 2e-3, np.max(d[near])
+    assert np.all(d <= 2.0 * fp32_floor(exp, quad)), np.max(d - 2.0 * fp32_floor(exp, quad))
 
 
 def test_tc_path_plain_config_and_spread_sky(G, orc, monkeypatch):
