@@ -55,7 +55,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 constexpr int kTcSpreadLimit = 64;
 
 struct TcLayout {
-    size_t a, b, r, tt, bini, binf, i0, f0, inv, qsc, gid, lse, bar, tptr, end;
+    size_t a, b, r, tt, bins, i0, f0, inv, qsc, gid, lse, bar, tptr, end;
     size_t sky, e5, par, pw, pe, fx;   // prologue scratch, aliased on the B buffers
     int kp;
 };
@@ -87,8 +87,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.tt = tc_al(L.r + (size_t)M * kTcS * 8);
     const size_t rbytes = (size_t)kTcW * kTcS * 4, pbytes = L.tt - L.r + (size_t)K * 2 * L.kp * L.kp * 2;
     o = tc_al(o + (rbytes > pbytes ? rbytes : pbytes), 16);
-    L.bini = o; o = tc_al(o + (size_t)n_t * 4, 16);
-    L.binf = o; o = tc_al(o + (size_t)n_t * 4, 16);
+    L.bins = o; o = tc_al(o + (size_t)n_t * 8, 16);   // (integer offset, fraction) per bin
     L.i0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.f0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.inv = o;  o = tc_al(o + (size_t)K * kTcS * 4, 16);
@@ -260,8 +259,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __half *As = reinterpret_cast<__half *>(sm + L.a);          // [K][2][kTcS x kp] canonical K-major
     __half *Bs = reinterpret_cast<__half *>(sm + L.b);          // [2 buf][2 part][kTcW x kp]
     float *Rs = reinterpret_cast<float *>(sm + L.r);            // Rt [kTcW][kTcS] (prologue: Y [M][kTcS])
-    int *bini = reinterpret_cast<int *>(sm + L.bini);
-    float *binf = reinterpret_cast<float *>(sm + L.binf);
+    int2 *bins = reinterpret_cast<int2 *>(sm + L.bins);          // (bin_i, bits of bin_f) per bin
     int *i0s = reinterpret_cast<int *>(sm + L.i0);              // [K][kTcS]
     float *f0s = reinterpret_cast<float *>(sm + L.f0);
     float *invs = reinterpret_cast<float *>(sm + L.inv);        // [K][kTcS] 2^-(row exponent + Q exponent)
@@ -304,8 +302,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     const uint32_t a_part = (uint32_t)(kTcS * kp * 2) >> 4;
 
     for (int j = tid; j < NT; j += blockDim.x) {
-        bini[j] = bt.bin_i[j];
-        binf[j] = bt.bin_f[j];
+        bins[j] = make_int2(bt.bin_i[j], __float_as_int(bt.bin_f[j]));
     }
     // tensor memory: two 128-column accumulators of the main contraction, then the
     // template products W_k = Z_k T_k at column 256 + 64 k
@@ -325,13 +322,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tptr;
-    // Barrier phase parities, bit b for buffer b, each kept by the thread that waits: windows
-    // staged into b so far (stager: stg, and used = b staged at least once), windows consumed
-    // (issuer: cons), accumulator drains awaited (issuer: drn) and commits not yet matched by
-    // a drain wait (issuer: pend), MMA completions awaited (consumers: full).
-    uint32_t stg = 0u, used = 0u, cons = 0u, drn = 0u, pend = 0u, full = 0u;
-    // tiles begun by this block: parity of the per-tile barriers (tbar, wbar)
-    uint32_t tpar = 0u;
+    // Barrier phase parities in one register (each role touches its own bits; bit b of a
+    // field is buffer b): MMA completions awaited (consumers), windows consumed, accumulator
+    // drains awaited and commits not yet matched by a drain wait (issuer), windows staged and
+    // buffer staged at least once (stager), and the parity of the per-tile barriers (tbar,
+    // wbar) over the tiles this block began.
+    constexpr int kPhFull = 0, kPhCons = 2, kPhDrn = 4, kPhPend = 6, kPhStg = 8, kPhUsed = 10, kPhTile = 12;
+    uint32_t ph = 0u;
+    auto phbit = [&](int f, int b) { return (ph >> (f + b)) & 1u; };
     const bool producer = warp >= kTcIssuerWarp;   // issuer or stager
 
     for (;;) {
@@ -542,7 +540,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         int wfail = 0;
         if (warp == kTcIssuerWarp) {
             if (lane == 0) {
-                if (!tc::mbar_wait(tbar, tpar, kWaitNs)) {
+                if (!tc::mbar_wait(tbar, phbit(kPhTile, 0), kWaitNs)) {
                     wfail = 1;
                 } else {
                     tc::tc_fence_after();
@@ -571,7 +569,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             // 32 samples of its lane quarter q
             int ok = 1;
             if (lane == 0)
-                ok = tc::mbar_wait(wbar, tpar, kWaitNs) ? 1 : 0;
+                ok = tc::mbar_wait(wbar, phbit(kPhTile, 0), kWaitNs) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             tc::tc_fence_after();
             const int q = warp & 3, cb = warp >> 2, s = 32 * q + lane;
@@ -608,7 +606,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         tc::tc_fence_before();
         int failed = __syncthreads_or(wfail);
-        tpar ^= 1u;
+        ph ^= 1u << kPhTile;
         const float gqd =
             (float)P.kappa * ((qsum[gs] + qsum[kTcS + gs]) + (qsum[2 * kTcS + gs] + qsum[3 * kTcS + gs]));
         float run_mx = -INFINITY, run_sum = 0.f;
@@ -627,7 +625,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             // counters).  First Q column of the window of detector k for the chunk starting at
             // bin j0, clamped so that a window never leaves the allocation of the Q copy.
             auto win0 = [&](int k, int j0) {
-                return min(max(glo[grp][k] + bini[j0], 0), 8 * (P.tc_groups - 16)) & ~7;
+                return min(max(glo[grp][k] + bins[j0].x, 0), 8 * (P.tc_groups - 16)) & ~7;
             };
 
             if (warp == kTcIssuerWarp) {
@@ -638,15 +636,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     for (int t = 0; t < n_steps && !failed; ++t, k = k + 1 == K ? 0 : k + 1) {
                         const int b = t & 1;
                         // window t staged; accumulator b drained by the consumers
-                        const uint32_t bit = 1u << b;
-                        if (!tc::mbar_wait(bbar + b, (cons >> b) & 1u, kWaitNs) ||
-                            ((pend & bit) && !tc::mbar_wait(emptyb + b, (drn >> b) & 1u, kWaitNs))) {
+                        if (!tc::mbar_wait(bbar + b, phbit(kPhCons, b), kWaitNs) ||
+                            (phbit(kPhPend, b) && !tc::mbar_wait(emptyb + b, phbit(kPhDrn, b), kWaitNs))) {
                             failed = 1;
                             break;
                         }
-                        cons ^= bit;
-                        if (pend & bit)
-                            drn ^= bit;
+                        ph ^= 1u << (kPhCons + b);
+                        if (phbit(kPhPend, b))
+                            ph ^= 1u << (kPhDrn + b);
                         tc::tc_fence_after();
                         const uint32_t d = tmem + (uint32_t)(b * kTcW);
                         const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
@@ -658,7 +655,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             tc::mma_f16(d, desc(al + o), desc(bh + o), idesc, 1);
                         }
                         tc::mma_commit(fullb + b);
-                        pend |= bit;
+                        ph |= 1u << (kPhPend + b);
                     }
                     if (failed)
                         abort_s = 1;
@@ -674,8 +671,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     int sk = 0, sch = 0;   // detector and chunk of the next window
                     for (int t = 0; t < n_steps && !failed; ++t) {
                         const int b = t & 1;
-                        const uint32_t bit = 1u << b;
-                        if ((used & bit) && !tc::mbar_wait(fullb + b, ((stg >> b) & 1u) ^ 1u, kWaitNs)) {
+                        if (phbit(kPhUsed, b) && !tc::mbar_wait(fullb + b, phbit(kPhStg, b) ^ 1u, kWaitNs)) {
                             failed = 1;
                             break;
                         }
@@ -685,8 +681,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                         tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
                         tc::bulk_g2s(dst, src, part_bytes, bbar + b);
                         tc::bulk_g2s(dst + part_halves, src + (size_t)P.tc_groups * kp * 8, part_bytes, bbar + b);
-                        stg ^= bit;
-                        used |= bit;
+                        ph ^= 1u << (kPhStg + b);
+                        ph |= 1u << (kPhUsed + b);
                         if (++sk == K) {
                             sk = 0;
                             ++sch;
@@ -713,8 +709,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     // one lane per warp waits for the MMAs of step t
                     int ok = 1;
                     if (lane == 0)
-                        ok = tc::mbar_wait(fullb + b, (full >> b) & 1u, kWaitNs) ? 1 : 0;
-                    full ^= 1u << b;
+                        ok = tc::mbar_wait(fullb + b, phbit(kPhFull, b), kWaitNs) ? 1 : 0;
+                    ph ^= 1u << (kPhFull + b);
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     tc::tc_fence_after();
                     // The rows of sample quarter q (TMEM lanes 32q..) are drained and gathered by
@@ -759,8 +755,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 #pragma unroll
                         for (int i = 0; i < kTcBPT; ++i) {
                             const int j = min(jb + i, j0 + J - 1);
-                            bj[i] = bini[j];
-                            bfj[i] = binf[j];
+                            const int2 bv = bins[j];   // one 8-byte broadcast load
+                            bj[i] = bv.x;
+                            bfj[i] = __int_as_float(bv.y);
                         }
                     }
                     // two bins per packed float32 operation (the same roundings as one at a time)
@@ -895,8 +892,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     // not have consumed the last windows; bounded wait), no MMA in flight; then free TMEM
     if (warp == kTcStagerWarp && lane == 0)
         for (int b = 0; b < 2; ++b)
-            if ((used >> b) & 1u)
-                tc::mbar_wait(bbar + b, ((stg >> b) & 1u) ^ 1u, kWaitNs);
+            if (phbit(kPhUsed, b))
+                tc::mbar_wait(bbar + b, phbit(kPhStg, b) ^ 1u, kWaitNs);
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0) {
