@@ -55,7 +55,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 constexpr int kTcSpreadLimit = 64;
 
 struct TcLayout {
-    size_t a, b, r, tt, bins, i0, f0, inv, qsc, gid, lse, bar, tptr, end;
+    size_t b, r, r2, tt, bins, i0, f0, inv, qsc, gid, lse, bar, tptr, end;
     size_t sky, e5, par, pw, pe, fx;   // prologue scratch, aliased on the B buffers
     int kp;
 };
@@ -67,8 +67,6 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     TcLayout L;
     L.kp = (2 * M + 15) / 16 * 16;
     size_t o = 0;
-    L.a = o;
-    o = tc_al(o + (size_t)K * 2 * kTcS * L.kp * 2);
     L.b = o;
     const size_t bbytes = (size_t)2 * 2 * kTcW * L.kp * 2;
     // prologue scratch, every table sample-minor ([row][kTcS]) so that the lanes of a
@@ -86,7 +84,9 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.r = o;
     L.tt = tc_al(L.r + (size_t)M * kTcS * 8);
     const size_t rbytes = (size_t)kTcW * kTcS * 4, pbytes = L.tt - L.r + (size_t)K * 2 * L.kp * L.kp * 2;
-    o = tc_al(o + (rbytes > pbytes ? rbytes : pbytes), 16);
+    o = tc_al(o + (rbytes > pbytes ? rbytes : pbytes));
+    L.r2 = o;   // second R tile: steps alternate between the two
+    o = tc_al(o + rbytes, 16);
     L.bins = o; o = tc_al(o + (size_t)n_t * 8, 16);   // (integer offset, fraction) per bin
     L.i0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.f0 = o;   o = tc_al(o + (size_t)K * kTcS * 4, 16);
@@ -256,9 +256,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     const int K = P.K, M = P.M, NT = P.n_t;
     const TcLayout L = tc_layout(K, M, NT);
     const int kp = L.kp, kcores = kp / 8;
-    __half *As = reinterpret_cast<__half *>(sm + L.a);          // [K][2][kTcS x kp] canonical K-major
     __half *Bs = reinterpret_cast<__half *>(sm + L.b);          // [2 buf][2 part][kTcW x kp]
     float *Rs = reinterpret_cast<float *>(sm + L.r);            // Rt [kTcW][kTcS] (prologue: Y [M][kTcS])
+    float *Rs2 = reinterpret_cast<float *>(sm + L.r2);          // Rt of the odd steps
     int2 *bins = reinterpret_cast<int2 *>(sm + L.bins);          // (bin_i, bits of bin_f) per bin
     int *i0s = reinterpret_cast<int *>(sm + L.i0);              // [K][kTcS]
     float *f0s = reinterpret_cast<float *>(sm + L.f0);
@@ -299,13 +299,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     // addresses < 256 KB: no carry out of it).
     auto desc = [&](uint32_t lo) { return ((uint64_t)(((sbo >> 4) & 0x3FFFu) | (1u << 14)) << 32) | lo; };
     auto desc_lo = [&](const void *p) { return ((tc::smem_u32(p) & 0x3FFFFu) >> 4) | ((128u >> 4) << 16); };
-    const uint32_t a_part = (uint32_t)(kTcS * kp * 2) >> 4;
+    // tensor memory columns: accumulators 0..255 (the template products W_k use columns
+    // 64 k.. before the first window); the A operand (coefficients, float16 hi/lo, two
+    // components per column) of detector k, part p at 256 + (2 k + p) kp / 2
+    auto a_col = [&](int k, int part) { return 256u + (uint32_t)((2 * k + part) * (kp / 2)); };
 
     for (int j = tid; j < NT; j += blockDim.x) {
         bins[j] = make_int2(bt.bin_i[j], __float_as_int(bt.bin_f[j]));
     }
-    // tensor memory: two 128-column accumulators of the main contraction, then the
-    // template products W_k = Z_k T_k at column 256 + 64 k
     if (warp == 0)
         tc::tmem_alloc(tptr, 512);
     if (tid == 0) {
@@ -484,9 +485,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             Ys[m * kTcS + s] = make_float2(d * e.x, d * (mm < 0 ? -e.y : e.y));
         }
         __syncthreads();
-        // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample, detector);
-        // each thread writes one sample row of a detector, 8 components (4 modes) per 16-byte store
+        // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample,
+        // detector), written into tensor memory: the thread of sample s writes lane s (its
+        // warp's lane quarter), 16 components (8 columns) per store.  The previous tile's MMAs,
+        // the last readers of these columns, completed before the barriers above.
         {
+            tc::tc_fence_after();
             for (int it = tid; tid < kTcConsumers && it < kTcS * K; it += kTcConsumers) {
                 const int s = it % kTcS, k = it / kTcS;
                 const float2 f = fx[k * kTcS + s];
@@ -501,15 +505,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 const int es = mx > 0.f ? 14 - ex : 0;
                 const float sc = ldexpf(1.f, es);
                 invs[k * kTcS + s] = ldexpf(1.f, -es - qexp);
-                qsc[k * kTcS + s] = ldexpf(1.f, -2 * es);
-                __half *Ahi = As + (size_t)(k * 2) * kTcS * kp;
-                __half *Alo = Ahi + (size_t)kTcS * kp;
-                const int rowbase = ((s >> 3) * kcores * 8 + (s & 7)) * 8;
-                for (int c8 = 0; c8 < kcores; ++c8) {
-                    uint32_t hw[4], lw[4];
+                qsc[k * kTcS + s] = ldexpf(1.f, -es);
+                const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+                for (int kk = 0; kk < kp / 16; ++kk) {
+                    uint32_t hw[8], lw[8];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int m = 4 * c8 + j;
+                    for (int j = 0; j < 8; ++j) {
+                        const int m = 8 * kk + j;
                         float cr = 0.f, ci = 0.f;
                         if (m < M) {
                             const float2 y = Ys[m * kTcS + s];
@@ -522,11 +524,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                         hw[j] = (uint32_t)__half_as_ushort(hr) | ((uint32_t)__half_as_ushort(hi) << 16);
                         lw[j] = (uint32_t)__half_as_ushort(lr) | ((uint32_t)__half_as_ushort(li) << 16);
                     }
-                    *reinterpret_cast<uint4 *>(Ahi + rowbase + c8 * 64) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4 *>(Alo + rowbase + c8 * 64) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    tc::tmem_st8(lane_base + a_col(k, 0) + 8u * (uint32_t)kk, hw);
+                    tc::tmem_st8(lane_base + a_col(k, 1) + 8u * (uint32_t)kk, lw);
                 }
+                tc::tmem_st_wait();
             }
-            tc::fence_proxy_async_smem();
+            tc::tc_fence_before();
         }
         __syncthreads();
 
@@ -535,8 +538,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         const bool gok = !producer && gid[gs] != 0xffffffffu;
 
         // ---------------- D: template term on the tensor cores.  W_k = Z_k T_k (Z_k: the A
-        // operand, row s = 2^es_ks z_ks; T_k scaled by 2^e_k), then
-        //   z_ks^T T_k z_ks = 2^-(2 es_ks + e_k) sum_n Z_k[s][n] W_k[s][n].
+        // operand, row s = 2^es_ks z_ks rounded to float16 hi/lo; T_k scaled by 2^e_k), into the
+        // accumulator columns 64 k.. (free until the first window's MMAs, which follow the
+        // barrier below), then with the float32 components z_ks
+        //   z_ks^T T_k z_ks = 2^-(es_ks + e_k) sum_n z_ks[n] W_k[s][n].
         int wfail = 0;
         if (warp == kTcIssuerWarp) {
             if (lane == 0) {
@@ -545,19 +550,19 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                 } else {
                     tc::tc_fence_after();
                     const uint32_t wdesc = tc::idesc_f16_f32(kTcS, kp);
-                    const uint32_t a_lo0 = desc_lo(As), t_lo0 = desc_lo(sm + L.tt);
+                    const uint32_t t_lo0 = desc_lo(sm + L.tt);
                     const uint32_t t_part = (uint32_t)(kp * kp * 2) >> 4;
                     for (int k = 0; k < K; ++k) {
-                        const uint32_t d = tmem + 256u + 64u * (uint32_t)k;
-                        const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
+                        const uint32_t d = tmem + 64u * (uint32_t)k;
+                        const uint32_t ah = tmem + a_col(k, 0), al = tmem + a_col(k, 1);
                         const uint32_t th = t_lo0 + (uint32_t)(2 * k) * t_part, tl = th + t_part;
                         for (int kk = 0; kk < kp / 16; ++kk) {
-                            const uint32_t o = (uint32_t)kk * 16u;
+                            const uint32_t o = (uint32_t)kk * 16u, oa = (uint32_t)kk * 8u;
                             // all four hi/lo products (the template term is cheap on the tensor pipe)
-                            tc::mma_f16(d, desc(ah + o), desc(th + o), wdesc, kk > 0);
-                            tc::mma_f16(d, desc(ah + o), desc(tl + o), wdesc, 1);
-                            tc::mma_f16(d, desc(al + o), desc(th + o), wdesc, 1);
-                            tc::mma_f16(d, desc(al + o), desc(tl + o), wdesc, 1);
+                            tc::mma_f16_ta(d, ah + oa, desc(th + o), wdesc, kk > 0);
+                            tc::mma_f16_ta(d, ah + oa, desc(tl + o), wdesc, 1);
+                            tc::mma_f16_ta(d, al + oa, desc(th + o), wdesc, 1);
+                            tc::mma_f16_ta(d, al + oa, desc(tl + o), wdesc, 1);
                         }
                     }
                     tc::mma_commit(wbar);
@@ -576,26 +581,20 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             float qp = 0.f;
             if (ok) {
                 const int cpd = kp / 16;
-                const int rowbase = ((s >> 3) * kcores * 8 + (s & 7)) * 8;
                 for (int c = cb; c < K * cpd; c += 4) {
                     const int k = c / cpd, n0 = (c - k * cpd) * 16;
                     uint32_t v[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 256u + 64u * (uint32_t)k + (uint32_t)n0, v);
-                    const __half *zh = As + (size_t)(k * 2) * kTcS * kp + rowbase + (n0 >> 3) * 64;
-                    const __half *zl = zh + (size_t)kTcS * kp;
+                    tc::tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + 64u * (uint32_t)k + (uint32_t)n0, v);
+                    const float2 f = fx[k * kTcS + s];
                     tc::tmem_ld_wait();
                     float acc = 0.f;
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {   // 8 components (one core column) at a time
-                        const uint4 hq = *reinterpret_cast<const uint4 *>(zh + 64 * h);
-                        const uint4 lq = *reinterpret_cast<const uint4 *>(zl + 64 * h);
-                        const uint32_t hw[4] = {hq.x, hq.y, hq.z, hq.w}, lw[4] = {lq.x, lq.y, lq.z, lq.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const float2 zhf = __half22float2(*reinterpret_cast<const __half2 *>(&hw[j]));
-                            const float2 zlf = __half22float2(*reinterpret_cast<const __half2 *>(&lw[j]));
-                            acc = fmaf(zhf.x + zlf.x, __uint_as_float(v[8 * h + 2 * j]), acc);
-                            acc = fmaf(zhf.y + zlf.y, __uint_as_float(v[8 * h + 2 * j + 1]), acc);
+                    for (int j = 0; j < 8; ++j) {   // modes n0 / 2 + j: components (re, im)
+                        const int m = n0 / 2 + j;
+                        if (m < M) {
+                            const float2 y = Ys[m * kTcS + s];
+                            acc = fmaf(f.x * y.x - f.y * y.y, __uint_as_float(v[2 * j]), acc);
+                            acc = fmaf(f.x * y.y + f.y * y.x, __uint_as_float(v[2 * j + 1]), acc);
                         }
                     }
                     qp += acc * ldexpf(qsc[k * kTcS + s], -P.tt_exp[k]);
@@ -631,7 +630,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             if (warp == kTcIssuerWarp) {
                 // ============ issuer warp, lane 0: one MMA batch per staged window
                 if (lane == 0) {
-                    const uint32_t a_lo0 = desc_lo(As), b_lo0 = desc_lo(Bs), b_part = part_bytes >> 4;
+                    const uint32_t b_lo0 = desc_lo(Bs), b_part = part_bytes >> 4;
                     int k = 0;
                     for (int t = 0; t < n_steps && !failed; ++t, k = k + 1 == K ? 0 : k + 1) {
                         const int b = t & 1;
@@ -646,13 +645,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             ph ^= 1u << (kPhDrn + b);
                         tc::tc_fence_after();
                         const uint32_t d = tmem + (uint32_t)(b * kTcW);
-                        const uint32_t ah = a_lo0 + (uint32_t)(2 * k) * a_part, al = ah + a_part;
+                        const uint32_t ah = tmem + a_col(k, 0), al = tmem + a_col(k, 1);
                         const uint32_t bh = b_lo0 + (uint32_t)(2 * b) * b_part, bl = bh + b_part;
                         for (int kk = 0; kk < kp / 16; ++kk) {
                             const uint32_t o = (uint32_t)kk * 16u;   // 256 bytes: the next 16 components
-                            tc::mma_f16(d, desc(ah + o), desc(bh + o), idesc, kk > 0);
-                            tc::mma_f16(d, desc(ah + o), desc(bl + o), idesc, 1);
-                            tc::mma_f16(d, desc(al + o), desc(bh + o), idesc, 1);
+                            const uint32_t oa = (uint32_t)kk * 8u;   // 16 components = 8 columns of A
+                            tc::mma_f16_ta(d, ah + oa, desc(bh + o), idesc, kk > 0);
+                            tc::mma_f16_ta(d, ah + oa, desc(bl + o), idesc, 1);
+                            tc::mma_f16_ta(d, al + oa, desc(bh + o), idesc, 1);
                         }
                         tc::mma_commit(fullb + b);
                         ph |= 1u << (kPhPend + b);
@@ -714,18 +714,16 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     ok = __shfl_sync(0xffffffffu, ok, 0);
                     tc::tc_fence_after();
                     // The rows of sample quarter q (TMEM lanes 32q..) are drained and gathered by
-                    // the same four warps (warp & 3 == q), so each quarter synchronises on its own
-                    // barrier: its warps are past their previous gather (its rows of R are free);
-                    // agree on failure.
+                    // the same four warps (warp & 3 == q), which synchronise on their own barrier
+                    // once per step, after the drain.  Steps alternate between two R tiles: the
+                    // tile step t drains into was last read by the gathers of step t - 2, which
+                    // every warp of the quarter finished before the barrier of step t - 1.
                     const int qbar = 2 + (warp & 3);
-                    if (tc::named_bar_or(qbar, kTcConsumers / 4, !ok || abort_s)) {
-                        failed = 1;
-                        break;
-                    }
+                    float *Rt = (t & 1) ? Rs2 : Rs;
                     {
                         // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
                         const int q = warp & 3, cb = warp >> 2;
-                        float *Rcol = Rs + (32 * cb) * kTcS + 32 * q + lane;
+                        float *Rcol = Rt + (32 * cb) * kTcS + 32 * q + lane;
                         // two loads of 16 columns (fewer live registers than one of 32)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
@@ -741,12 +739,16 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     __syncwarp();
                     if (lane == 0)
                         tc::mbar_arrive(emptyb + b);
-                    tc::named_bar(qbar, kTcConsumers / 4);   // this quarter's rows of R complete
+                    // this quarter's rows of R complete; agree on failure
+                    if (tc::named_bar_or(qbar, kTcConsumers / 4, !ok || abort_s)) {
+                        failed = 1;
+                        break;
+                    }
                     const int iw0 = win0(k, j0);
                     // padding samples and samples of other sub-groups read at the group's lowest
                     // offset, which keeps every read in the row; their sums are discarded
                     const bool mine = gok && in_grp;
-                    const float *Rcol = Rs + ((mine ? i0s[k * kTcS + gs] : glo[grp][k]) - iw0) * kTcS + gs;
+                    const float *Rcol = Rt + ((mine ? i0s[k * kTcS + gs] : glo[grp][k]) - iw0) * kTcS + gs;
                     const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
                     const float sc = invs[k * kTcS + gs];
                     if (k == 0) {
