@@ -36,6 +36,9 @@ constexpr int kTcStagerWarp = kTcIssuerWarp + 1;
 constexpr int kTcQ = kTcConsumers / kTcS;  // threads per sample in the gather (bin quarters)
 constexpr int kTcBPT = 16;         // bins per thread per chunk
 constexpr int kTcMaxBins = kTcQ * kTcBPT;
+// phases B and E give every (sample, detector) item its own consumer thread, whole warps
+// per detector
+static_assert(kTcS * kMaxDet <= kTcConsumers && kTcS % 32 == 0, "one item per consumer thread");
 // R is kept transposed, Rt[column][sample]: the drain (lane = sample, fixed column) and
 // the gather (lane = sample, per-sample column) both touch bank = sample, conflict-free.
 constexpr int kTcPow = 16;
@@ -411,9 +414,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             int i0 = (int)fl;
             i0s[k * kTcS + s] = i0;
             f0s[k * kTcS + s] = (float)(u0 - fl);
-            if (gid[s] != 0xffffffffu) {
-                atomicMin(&lo_s[k], i0);
-                atomicMax(&hi_s[k], i0);
+            // offset range of the tile at detector k: a warp holds 32 samples of one detector
+            // (one item per thread), so reduce over the warp, then one atomic per warp
+            const bool valid = gid[s] != 0xffffffffu;
+            const int wmin = __reduce_min_sync(0xffffffffu, valid ? i0 : INT_MAX);
+            const int wmax = __reduce_max_sync(0xffffffffu, valid ? i0 : INT_MIN);
+            if (lane == 0 && wmin != INT_MAX) {
+                atomicMin(&lo_s[k], wmin);
+                atomicMax(&hi_s[k], wmax);
             }
             const Cx<float> F = response_f(P.Dten_f[k], e5[s], e5[kTcS + s], e5[2 * kTcS + s], e5[3 * kTcS + s],
                                            e5[4 * kTcS + s], par[s], par[kTcS + s]);
