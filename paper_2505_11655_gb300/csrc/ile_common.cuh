@@ -243,6 +243,16 @@ __device__ __forceinline__ uint32_t hilbert_index(uint32_t x, uint32_t y, int or
     return d;
 }
 
+// Cell of the (right ascension, sin declination) grid from the prior coordinates
+// a = alpha / 2 pi and z = (sin delta + 1) / 2, both in [0, 1).
+__device__ __forceinline__ uint32_t sky_cell_v(double a, double z, const SkyGrid &G)
+{
+    const int side = 1 << G.order;
+    const uint32_t x = (uint32_t)min(side - 1, max(0, (int)(a * side)));
+    const uint32_t y = (uint32_t)min(side - 1, max(0, (int)(z * side)));
+    return hilbert_index(x, y, G.order);
+}
+
 __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const SkyGrid &G)
 {
     if (G.mode != kSortSky) {

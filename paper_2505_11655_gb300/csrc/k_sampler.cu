@@ -28,17 +28,20 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
                                                             uint32_t *__restrict__ key)
 {
     const uint32_t iter = *iter_base + iter_off;
-    extern __shared__ double sC[];   // [6][B+1] running sums, then [6][B] masses, [6][B] log densities
+    // [6][B+1] running sums, then [6][B] reciprocal masses, [6][B] log densities (float64
+    // divisions once per block instead of per sample)
+    extern __shared__ double sC[];
     const int B = S.B;
-    double *sP = sC + 6 * (B + 1);
-    double *sL = sP + 6 * B;
+    double *sR = sC + 6 * (B + 1);
+    double *sL = sR + 6 * B;
     for (int e = threadIdx.x; e < 6 * (B + 1); e += blockDim.x)
         sC[e] = S.C[e];
     for (int e = threadIdx.x; e < 6 * B; e += blockDim.x) {
-        sP[e] = S.P[e];
+        sR[e] = 1.0 / S.P[e];
         sL[e] = S.L[e];
     }
     __syncthreads();
+    const double inv_b = 1.0 / B;
     const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
     const double d3lo = S.d_min * S.d_min * S.d_min, d3hi = S.d_max * S.d_max * S.d_max;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -65,13 +68,12 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
                 else
                     hi = mid - 1;
             }
-            const double pb = sP[d * B + lo];
-            double t = (x - Cd[lo]) / pb;
+            double t = (x - Cd[lo]) * sR[d * B + lo];
             if (!(t >= 0.0))
                 t = 0.0;
             if (t >= 1.0)
                 t = 0x1.fffffffffffffp-1;
-            v[d] = (lo + t) / B;
+            v[d] = (lo + t) * inv_b;
             if (!(S.marg && d == 5))
                 lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
             packed |= (uint64_t)lo << (10 * d);
@@ -89,7 +91,9 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
             out[d] = th[d];
         lnpw[i] = lr;
         bins[i] = packed;
-        key[i] = sky_cell(th[0], th[1], G);
+        // on the (right ascension, sin declination) grid the cell follows from the prior
+        // coordinates themselves: alpha / 2 pi = v0 and (sin delta + 1) / 2 = v1
+        key[i] = G.mode == kSortSky ? sky_cell_v(v[0], v[1], G) : sky_cell(th[0], th[1], G);
     }
 }
 
