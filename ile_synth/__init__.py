@@ -56,6 +56,9 @@ DETECTORS = {
     "H1": (46.455144, -119.407656, 142.554, 324.000, 234.000, -6.195e-4, 1.25e-5),
     "L1": (30.562894, -90.774242, -6.574, 252.2835, 162.2835, -3.121e-4, -6.107e-4),
     "V1": (43.631414, 10.504498, 51.884, 19.4326, 289.4326, 0.0, 0.0),
+    # a synthetic fourth site (southern hemisphere, arms at 20 and 110 degrees), used only
+    # for four-detector test problems
+    "X1": (-31.0, 115.0, 0.0, 20.0, 110.0, 0.0, 0.0),
 }
 
 
