@@ -378,7 +378,13 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kernel, "samples_per_cell": plan[1], "kernel_ms": lnl_avg,
                      "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
-                     "flops_per_sample": fps},
+                     "flops_per_sample": fps,
+                     "note": "algorithmic flops of the method against the FP32 FMA peak; the mode contraction "
+                             "(95% of them) runs on tcgen05 as a float16 hi/lo split, so this fraction is not a "
+                             "unit's utilisation: in the ncu capture no unit is saturated (shared-memory "
+                             "wavefronts ~42% of the LSU pipe's bandwidth, issue 53%, tensor pipe 16%); the "
+                             "per-step drain of the accumulators into shared memory and the per-bin gather "
+                             "bound the kernel"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clocks,
         "lnZ_last": r["lnZ"], "n_eff_last": r["n_eff"], "precompute": pre, "distance_marg": dm,
