@@ -30,6 +30,8 @@ constexpr int kBinsPerLane = 5;  // a chunk holds <= 160 bins
 constexpr int kMaxChunkBins = 32 * kBinsPerLane;
 constexpr int kPowStride = 16;   // >= kMaxPow + 1
 static_assert(kPowStride >= kMaxPow + 1, "power table too short");
+// phase B gives every (sample, detector) item its own thread, whole warps per detector
+static_assert(kTS * kMaxDet <= kTThreads && kTS % 32 == 0, "one item per thread");
 
 struct TileLayout {
     size_t cs, qb0, qb1, r, bini, binf, sky, par, pw, fx, i0, f0, quad, qpart, gid, end;
@@ -47,9 +49,11 @@ __host__ __device__ inline TileLayout tile_layout(int K, int M, int n_t, bool db
     L.r = o;   o = al16(o + (size_t)kTS * kNCol * 4);
     L.bini = o; o = al16(o + (size_t)n_t * 4);
     L.binf = o; o = al16(o + (size_t)n_t * 4);
-    L.sky = o; o = al16(o + (size_t)kTS * 4 * 8);     // cos d, sin d, cos h, sin h (float64)
-    L.par = o; o = al16(o + (size_t)kTS * 8 * 4);     // c2psi, s2psi, x, phi, cos(i/2), sin(i/2) (float32)
-    L.pw = o;  o = al16(o + (size_t)kTS * 2 * kPowStride * 4);   // cos(i/2)^p, sin(i/2)^p
+    // per-sample tables are sample-minor ([row][kTS]): the lanes of a warp (consecutive
+    // samples) touch consecutive words
+    L.sky = o; o = al16(o + (size_t)3 * kTS * 8);     // unit vector n to the source (float64)
+    L.par = o; o = al16(o + (size_t)9 * kTS * 4);     // c2psi, s2psi, x, phi, and the sky basis e_a, e_d (float32)
+    L.pw = o;  o = al16(o + (size_t)2 * kPowStride * kTS * 4);   // cos(i/2)^p, sin(i/2)^p
     L.fx = o;  o = al16(o + (size_t)K * kTS * 8);     // x F_k (float2)
     L.i0 = o;  o = al16(o + (size_t)K * kTS * 4);
     L.f0 = o;  o = al16(o + (size_t)K * kTS * 4);
@@ -87,14 +91,14 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
     float *Rs = reinterpret_cast<float *>(smraw + L.r);         // [kTS][kNCol]
     int *bini = reinterpret_cast<int *>(smraw + L.bini);
     float *binf = reinterpret_cast<float *>(smraw + L.binf);
-    double *sky = reinterpret_cast<double *>(smraw + L.sky);    // [kTS][4]
-    float *par = reinterpret_cast<float *>(smraw + L.par);      // [kTS][8]
+    double *sky = reinterpret_cast<double *>(smraw + L.sky);    // [3][kTS]
+    float *par = reinterpret_cast<float *>(smraw + L.par);      // [9][kTS]
     float2 *fx = reinterpret_cast<float2 *>(smraw + L.fx);      // [K][kTS]
     int *i0s = reinterpret_cast<int *>(smraw + L.i0);           // [K][kTS]
     float *f0s = reinterpret_cast<float *>(smraw + L.f0);       // [K][kTS]
     float *qds = reinterpret_cast<float *>(smraw + L.quad);     // [kTS]
     float *qpart = reinterpret_cast<float *>(smraw + L.qpart);  // [4][kTS]
-    float *pw = reinterpret_cast<float *>(smraw + L.pw);        // [kTS][2][kPowStride]
+    float *pw = reinterpret_cast<float *>(smraw + L.pw);        // [2 kPowStride][kTS]
     uint32_t *gid = reinterpret_cast<uint32_t *>(smraw + L.gid);
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];
     __shared__ int tile_s;
@@ -131,60 +135,67 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                 for (int d = 0; d < 6; ++d)
                     th[d] = theta[6 * (int64_t)g + d];
             Sky sk = sky_of(th[0], th[1], P.gmst);
-            double *sp = sky + 4 * tid;
-            sp[0] = sk.cd;
-            sp[1] = sk.sd;
-            sp[2] = sk.ch;
-            sp[3] = sk.sh;
+            // unit vector to the source in float64 (delays); the sky basis of the response
+            // e_a = (-sin h, cos h, 0), e_d = (-sin d cos h, -sin d sin h, cos d) rounded once
+            sky[tid] = sk.cd * sk.ch;
+            sky[kTS + tid] = sk.cd * sk.sh;
+            sky[2 * kTS + tid] = sk.sd;
             float s2p, c2p, shalf, chalf;
             sincosf((float)(2.0 * th[2]), &s2p, &c2p);
             sincosf((float)(0.5 * th[4]), &shalf, &chalf);
-            float *pp = par + 8 * tid;
-            pp[0] = c2p;
-            pp[1] = s2p;
-            pp[2] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
-            pp[3] = (float)th[3];
-            pp[4] = chalf;
-            pp[5] = shalf;
-            float *pc = pw + tid * 2 * kPowStride, *ps = pc + kPowStride;
-            pc[0] = 1.f;
-            ps[0] = 1.f;
+            par[tid] = c2p;
+            par[kTS + tid] = s2p;
+            par[2 * kTS + tid] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
+            par[3 * kTS + tid] = (float)th[3];
+            par[4 * kTS + tid] = (float)(-sk.sh);
+            par[5 * kTS + tid] = (float)sk.ch;
+            par[6 * kTS + tid] = (float)(-sk.sd * sk.ch);
+            par[7 * kTS + tid] = (float)(-sk.sd * sk.sh);
+            par[8 * kTS + tid] = (float)sk.cd;
+            float pc = 1.f, ps = 1.f;
+            pw[tid] = 1.f;
+            pw[kPowStride * kTS + tid] = 1.f;
             for (int q = 1; q <= kMaxPow; ++q) {
-                pc[q] = pc[q - 1] * chalf;
-                ps[q] = ps[q - 1] * shalf;
+                pc *= chalf;
+                ps *= shalf;
+                pw[q * kTS + tid] = pc;
+                pw[(kPowStride + q) * kTS + tid] = ps;
             }
         }
         __syncthreads();
         // ---------------- phase B: per (sample, detector), delays and x F_k
         for (int it = tid; it < kTS * K; it += kTThreads) {
             const int s = it % kTS, k = it / kTS;
-            const double *sp = sky + 4 * s;
-            Sky sk{sp[0], sp[1], sp[2], sp[3]};
-            const float *pp = par + 8 * s;
-            double dt = arrival_delay(P, k, sk);
-            double u0 = (P.t_lo + dt - P.q_t0[k]) * P.fs;
+            // Q-sample position of the first bin, (t_lo + dt_k - q_t0_k) fs
+            const double u0 =
+                fma(P.xfs[k][0], sky[s], fma(P.xfs[k][1], sky[kTS + s], fma(P.xfs[k][2], sky[2 * kTS + s], P.ufs0[k])));
             double fl = floor(u0);
             int i0 = (int)fl;
             i0s[k * kTS + s] = i0;
             f0s[k * kTS + s] = (float)(u0 - fl);
-            if (gid[s] != 0xffffffffu) {
-                atomicMin(&lo_s[k], i0);
-                atomicMax(&hi_s[k], i0);
+            // offset range at detector k: a warp holds 32 samples of one detector (one item
+            // per thread), so reduce over the warp, then one atomic per warp
+            const bool valid = gid[s] != 0xffffffffu;
+            const int wmin = __reduce_min_sync(0xffffffffu, valid ? i0 : INT_MAX);
+            const int wmax = __reduce_max_sync(0xffffffffu, valid ? i0 : INT_MIN);
+            if (lane == 0 && wmin != INT_MAX) {
+                atomicMin(&lo_s[k], wmin);
+                atomicMax(&hi_s[k], wmax);
             }
-            Cx<float> F = response<float>(P, k, sk, pp[0], pp[1]);
-            fx[k * kTS + s] = make_float2(pp[2] * F.re, pp[2] * F.im);
+            const Cx<float> F = response_f(P.Dten_f[k], par[4 * kTS + s], par[5 * kTS + s], par[6 * kTS + s],
+                                           par[7 * kTS + s], par[8 * kTS + s], par[s], par[kTS + s]);
+            const float amp = par[2 * kTS + s];
+            fx[k * kTS + s] = make_float2(amp * F.re, amp * F.im);
         }
         __syncthreads();
         // ---------------- phase C: per (sample, mode), harmonic and coefficients
         for (int it = tid; it < kTS * M; it += kTThreads) {
             const int s = it % kTS, m = it / kTS;
-            const float *pp = par + 8 * s;
-            const float *pc = pw + s * 2 * kPowStride, *ps = pc + kPowStride;
             float d = 0.f;
             for (int t = 0; t < P.wn[m]; ++t)
-                d += (float)P.wcoef[m][t] * pc[P.wpc[m][t]] * ps[P.wps[m][t]];
+                d += P.wcoef_f[m][t] * pw[P.wpc[m][t] * kTS + s] * pw[(kPowStride + P.wps[m][t]) * kTS + s];
             float sy, cy;
-            sincosf(-(float)P.mode_m[m] * pp[3], &sy, &cy);
+            sincosf(-(float)P.mode_m[m] * par[3 * kTS + s], &sy, &cy);
             const float yr = d * cy, yi = d * sy;
             for (int k = 0; k < K; ++k) {
                 float2 f = fx[k * kTS + s];
