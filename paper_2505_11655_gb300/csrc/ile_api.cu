@@ -296,8 +296,20 @@ int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmar
     CK(launch_reduce(key, lnL_tmarg, n, h->red_partial, h->stats, kScratchSlot, h->pooled_scratch, 1, h->err,
                      h->stream));
     CK(launch_select(key, n, h->stats, kScratchSlot, kMixedMargin, h->sel_idx, h->sel_count, h->stream));
-    CK(launch_refine(h->prob, theta, h->sel_idx, h->sel_count, n, lnL_tmarg, lnpw, lnw, h->err, h->stream));
-    h->launches += 4;
+    // the tensor-core kernel recomputes the float32 per-bin ln L of the first refine_rows
+    // selected samples (a few tiles), so the refinement itself evaluates only the bins
+    // within its margin in float64
+    int64_t rows = 0;
+    if (h->refine_bins && use_tc(h, n)) {
+        const BinTable bt{h->bin_i, h->bin_f};
+        rows = std::min<int64_t>(h->refine_rows, n);
+        CK(launch_lnl_tc(h->prob, bt, theta, h->sel_idx, rows, lnL_tmarg, h->refine_bins, lnpw, lnw, h->err,
+                         h->tile_counter, h->stream, h->sel_count, 1, n));
+        h->launches += 1;
+    }
+    CK(launch_refine(h->prob, theta, h->sel_idx, h->sel_count, n, lnL_tmarg, lnpw, lnw, h->err, h->stream,
+                     h->refine_bins, rows));
+    h->launches += 6;
     return RIFT_OK;
 }
 
@@ -630,12 +642,19 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         (rc = dalloc(h, &h->hist_partial, (size_t)152 * 12 * B)) ||
         (rc = dalloc(h, &h->stats, (size_t)8 * (RIFT_MAX_ITER + 1))) || (rc = dalloc(h, &h->pooled, (size_t)8)) ||
         (rc = dalloc(h, &h->pooled_scratch, (size_t)8)) || (rc = dalloc(h, &h->sel_idx, (size_t)N)) ||
-        (rc = dalloc(h, &h->sel_count, (size_t)4)) ||
+        (rc = dalloc(h, &h->sel_count, (size_t)kSelectWords)) ||
         (rc = dalloc(h, &h->final_out, (size_t)8)) || (rc = dalloc(h, &h->P, (size_t)6 * B)) ||
         (rc = dalloc(h, &h->C, (size_t)6 * (B + 1))) || (rc = dalloc(h, &h->Lg, (size_t)6 * B)) || (rc = dalloc(h, &h->err, (size_t)4)) ||
         (rc = dalloc(h, &h->iter_dev, (size_t)4))) {
         release(h);
         return rc;
+    }
+    if (cfg->precision == RIFT_MIXED) {
+        h->refine_rows = std::min<int64_t>(N, kRefineRows);
+        if ((rc = dalloc(h, &h->refine_bins, (size_t)h->refine_rows * cfg->n_t))) {
+            release(h);
+            return rc;
+        }
     }
     h->host_out.assign(8 + 8 * (RIFT_MAX_ITER + 1) + 8, 0.0);
 
@@ -722,7 +741,8 @@ int64_t rift_ile_footprint(const rift_ile_config *cfg)
         2 * nt * 4,
         N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, (int64_t)sort_scratch_words(N) * 4, 16, 16,
         K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 12 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
-        N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16};
+        N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16, (int64_t)kSelectWords * 4,
+        cfg->precision == RIFT_MIXED ? std::min<int64_t>(N, kRefineRows) * nt * 8 : 0};
     int64_t total = 0;
     for (int64_t b : sizes)
         total += b + 16;

@@ -55,6 +55,8 @@ struct rift_ile {
     uint64_t *hist_partial = nullptr;   // [152][6][B][2] exact fixed-point block histograms
     double *pooled_scratch = nullptr;
     uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
+    double *refine_bins = nullptr;   // RIFT_MIXED: float32 per-bin ln L of the first selected samples
+    int64_t refine_rows = 0;
     double *P = nullptr, *C = nullptr, *Lg = nullptr;
     int *err = nullptr;
     uint32_t *iter_dev = nullptr;   // sampler iteration counter read by the draw kernel

@@ -90,20 +90,32 @@ bool lnl_tc_fits(const Problem &P, int max_smem);
 // Template matrices T_k of the tensor-core kernel from the float64 Gram matrices.
 cudaError_t launch_prep_tt(const double2 *U64, const double2 *V64, int K, int M, __half *Ttc, int *tt_exp,
                            cudaStream_t st);
+// n_dev (optional): perm holds min(n, *n_dev) entries (a count written on the device);
+// n_theta: theta's sample count when perm indexes a larger batch (default n);
+// lnl_t_compact: the per-bin output of the sample at position i of perm is row i of lnL_t
+// (instead of its sample index's row).
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
-                          int *tile_counter, cudaStream_t st);
+                          int *tile_counter, cudaStream_t st, const uint32_t *n_dev = nullptr,
+                          int lnl_t_compact = 0, int64_t n_theta = 0);
 // Builds the float16 hi/lo copy of Q for the tensor-core path.
 cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups, unsigned int *qmax_bits,
                            __half *Qtc, cudaStream_t st);
 
 // Precision mode RIFT_MIXED: indices of the samples with key[i] >= stats[slot].max - margin
-// (idx[*count]), then their float64 re-evaluation in place (lnL_tmarg, and lnw when given).
+// (idx[*count], ascending), then their float64 re-evaluation in place (lnL_tmarg, and lnw
+// when given).  count points to kSelectWords words (the count, then block scratch).
+constexpr int kSelectWords = 1 + 1024;
+// selected samples whose float32 per-bin values the tiled kernel recomputes for the
+// refinement (the rest are recomputed by the refinement itself)
+constexpr int64_t kRefineRows = 16384;
 cudaError_t launch_select(const double *key, int64_t n, const double *stats, int slot, double margin, uint32_t *idx,
                           uint32_t *count, cudaStream_t st);
+// v32 (optional): float32 per-bin ln L of the selected samples, row w for the w-th selected
+// sample, for w < v32_rows; the others get their float32 bins recomputed.
 cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t *idx, const uint32_t *count,
                           int64_t max_count, double *lnL_tmarg, const double *lnpw, double *lnw, int *err,
-                          cudaStream_t st);
+                          cudaStream_t st, const double *v32 = nullptr, int64_t v32_rows = 0);
 
 // Per-sample coefficients: c[n][K][M] (complex), dt[n][K], quad[n]; any may be null.
 cudaError_t launch_coeffs(const Problem &P, bool fp64, const double *theta, int64_t n, double2 *c, double *dt,

@@ -22,23 +22,79 @@ namespace rift {
 constexpr int kRefThreads = 128;   // 4 warps, one sample each
 constexpr double kRefineBins = 40.0;
 
-__global__ void select_kernel(const double *__restrict__ key, int64_t n, const double *__restrict__ stats, int slot,
-                              double margin, uint32_t *__restrict__ idx, uint32_t *__restrict__ count)
+// Selection of the samples with key[i] >= max - margin, in ascending index order (so the
+// list, and everything computed from it, is the same from run to run): block b of the
+// grid owns the contiguous range [b per, (b + 1) per); pass 1 counts per block, a single
+// block scans the counts, pass 2 writes each block's matches at its offset in order.
+constexpr int kSelThreads = 256;
+constexpr int kSelMaxBlocks = kSelectWords - 1;
+
+__device__ __forceinline__ bool sel_take(const double *key, int64_t i, double cut) { return key[i] >= cut; }
+
+__global__ void __launch_bounds__(kSelThreads) select_count_kernel(const double *__restrict__ key, int64_t n,
+                                                                    const double *__restrict__ stats, int slot,
+                                                                    double margin, uint32_t *__restrict__ blk)
 {
     const double cut = stats[8 * slot + 4] - margin;   // max ln w (or max ln L) of the batch
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const bool take = key[i] >= cut;
-        const unsigned active = __activemask();
-        const unsigned mask = __ballot_sync(active, take);
-        if (!mask)
-            continue;
-        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
-        uint32_t base = 0;
-        if (lane == leader)
-            base = atomicAdd(count, (uint32_t)__popc(mask));
-        base = __shfl_sync(active, base, leader);
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(n, b0 + per);
+    uint32_t c = 0;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kSelThreads)
+        c += sel_take(key, i, cut) ? 1u : 0u;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ uint32_t ws[kSelThreads / 32];
+    if ((threadIdx.x & 31) == 0)
+        ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w)
+            t += ws[w];
+        blk[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of the nb block counts in place; the total goes to *count
+__global__ void select_scan_kernel(uint32_t *__restrict__ blk, int nb, uint32_t *__restrict__ count)
+{
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int b = 0; b < nb; ++b) {
+            const uint32_t c = blk[b];
+            blk[b] = run;
+            run += c;
+        }
+        *count = run;
+    }
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_write_kernel(const double *__restrict__ key, int64_t n,
+                                                                    const double *__restrict__ stats, int slot,
+                                                                    double margin, const uint32_t *__restrict__ blk,
+                                                                    uint32_t *__restrict__ idx)
+{
+    const double cut = stats[8 * slot + 4] - margin;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * per, b1 = min(n, b0 + per);
+    __shared__ uint32_t ws[kSelThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t base = blk[blockIdx.x];
+    for (int64_t c0 = b0; c0 < b1; c0 += kSelThreads) {
+        const int64_t i = c0 + threadIdx.x;
+        const bool take = i < b1 && sel_take(key, i, cut);
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        if (lane == 0)
+            ws[warp] = (uint32_t)__popc(mask);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w) {
+            before += w < warp ? ws[w] : 0u;
+            total += ws[w];
+        }
         if (take)
-            idx[base + __popc(mask & ((1u << lane) - 1))] = (uint32_t)i;
+            idx[base + before + (uint32_t)__popc(mask & ((1u << lane) - 1))] = (uint32_t)i;
+        base += total;
+        __syncthreads();
     }
 }
 
@@ -46,7 +102,8 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
                                                               const uint32_t *__restrict__ idx,
                                                               const uint32_t *__restrict__ count,
                                                               double *__restrict__ lnL_tmarg, const double *__restrict__ lnpw,
-                                                              double *__restrict__ lnw, int *err)
+                                                              double *__restrict__ lnw, int *err,
+                                                              const double *__restrict__ v32, int64_t v32_rows)
 {
     extern __shared__ double rsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -88,6 +145,7 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
             const double2 *Ur = P.U64 + ((size_t)k * M + a) * M;
             const double2 *Vr = P.V64 + ((size_t)k * M + a) * M;
             double ur = 0, ui = 0, vr = 0, vi = 0;
+#pragma unroll 7
             for (int b = 0; b < M; ++b) {
                 const double2 cb = c64[k * M + b], u = Ur[b], v = Vr[b];
                 ur += u.x * cb.x - u.y * cb.y;
@@ -102,8 +160,17 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
         for (int o = 16; o; o >>= 1)
             part += __shfl_xor_sync(0xffffffffu, part, o);
         const double quad = P.kappa * part;
-        // float32 data term at every bin
+        // float32 ln L at every bin: from the tiled kernel's second pass over the selected
+        // samples when it ran for this one, else recomputed here
         float mx32 = -INFINITY;
+        if ((int64_t)w < v32_rows) {
+            const double *row = v32 + (size_t)w * NT;
+            for (int j = lane; j < NT; j += 32) {
+                const double v = row[j];
+                vals[j] = v;
+                mx32 = fmaxf(mx32, (float)v);
+            }
+        } else
         for (int j = lane; j < NT; j += 32) {
             const double tj = P.t_lo + j * P.t_step;
             float lin = 0.f;
@@ -117,6 +184,8 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
                 const int i = (int)fl;
                 const float f = (float)(u - fl);
                 const float *Qk = P.Qr32 + (size_t)k * 2 * M * P.n_q_pad + i;
+                // the loads of several modes in flight at once (the Q planes live in L2)
+#pragma unroll 7
                 for (int m = 0; m < M; ++m) {
                     const double2 c = c64[k * M + m];
                     const float *qr = Qk + (size_t)(2 * m) * P.n_q_pad, *qi = qr + P.n_q_pad;
@@ -147,6 +216,7 @@ __global__ void __launch_bounds__(kRefThreads) refine_kernel(Problem P, const do
                     const int i = (int)fl;
                     const double f = u - fl;
                     const double2 *Qk = P.Q64 + (size_t)k * M * P.n_q + i;
+#pragma unroll 7
                     for (int m = 0; m < M; ++m) {
                         const double2 q0 = Qk[(size_t)m * P.n_q], q1 = Qk[(size_t)m * P.n_q + 1];
                         const double2 c = c64[k * M + m];
@@ -184,21 +254,19 @@ cudaError_t launch_select(const double *key, int64_t n, const double *stats, int
 {
     if (n <= 0)
         return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess)
-        return e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (n + 255) / 256;
-    const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-    select_kernel<<<grid, 256, 0, st>>>(key, n, stats, slot, margin, idx, count);
+    // block counts live after the count word
+    uint32_t *blk = count + 1;
+    const int64_t want = (n + 4 * kSelThreads - 1) / (4 * kSelThreads);
+    const int grid = (int)(want < kSelMaxBlocks ? (want > 0 ? want : 1) : kSelMaxBlocks);
+    select_count_kernel<<<grid, kSelThreads, 0, st>>>(key, n, stats, slot, margin, blk);
+    select_scan_kernel<<<1, 32, 0, st>>>(blk, grid, count);
+    select_write_kernel<<<grid, kSelThreads, 0, st>>>(key, n, stats, slot, margin, blk, idx);
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t *idx, const uint32_t *count,
                           int64_t max_count, double *lnL_tmarg, const double *lnpw, double *lnw, int *err,
-                          cudaStream_t st)
+                          cudaStream_t st, const double *v32, int64_t v32_rows)
 {
     if (max_count <= 0)
         return cudaSuccess;
@@ -214,7 +282,8 @@ cudaError_t launch_refine(const Problem &P, const double *theta, const uint32_t 
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t want = (max_count + wpb - 1) / wpb;
     const int grid = (int)(want < (int64_t)sms * 8 ? want : (int64_t)sms * 8);
-    refine_kernel<<<grid, kRefThreads, smem, st>>>(P, theta, idx, count, lnL_tmarg, lnpw, lnw, err);
+    refine_kernel<<<grid, kRefThreads, smem, st>>>(P, theta, idx, count, lnL_tmarg, lnpw, lnw, err, v32,
+                                                   v32 ? v32_rows : 0);
     return cudaGetLastError();
 }
 

@@ -253,8 +253,11 @@ template <bool kDM>
 __global__ void __launch_bounds__(kTcThreads, 1)
 lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const uint32_t *__restrict__ perm, int64_t n,
               double *__restrict__ lnL_tmarg, double *__restrict__ lnL_t, const double *__restrict__ lnpw,
-              double *__restrict__ lnw, int *err, int *tile_counter)
+              double *__restrict__ lnw, int *err, int *tile_counter, const uint32_t *__restrict__ n_dev,
+              int64_t n_theta, int lnl_t_compact)
 {
+    // n entries of perm (fewer when a device count is given, read where needed so that no
+    // register holds it); every sample index in perm is below n_theta
     extern __shared__ __align__(128) unsigned char sm[];
     const int K = P.K, M = P.M, NT = P.n_t;
     const TcLayout L = tc_layout(K, M, NT);
@@ -289,7 +292,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double beta = P.t_step * P.fs;
-    const int64_t n_tiles = (n + kTcS - 1) / kTcS;
+    const int64_t n_tiles = ((n_dev ? min(n, (int64_t)*n_dev) : n) + kTcS - 1) / kTcS;
     const uint32_t idesc = tc::idesc_f16_f32(kTcS, kTcW);
     const uint32_t sbo = (uint32_t)kcores * 128u;
     const size_t part_halves = (size_t)kTcW * kp;                 // one B part
@@ -361,8 +364,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         // ---------------- prologue A: sky trigonometry (float64) and per-sample scalars
         if (tid < kTcS) {
             const int64_t si = tile * kTcS + tid;
-            uint32_t g = si < n ? perm[si] : 0xffffffffu;
-            const bool valid = (int64_t)g < n;
+            const int64_t n_use = n_dev ? min(n, (int64_t)*n_dev) : n;
+            uint32_t g = si < n_use ? perm[si] : 0xffffffffu;
+            const bool valid = (int64_t)g < n_theta;
             gid[tid] = valid ? g : 0xffffffffu;
             double th[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
             if (valid)
@@ -823,7 +827,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 #pragma unroll
                                 for (int u = 0; u < kTcBPT; ++u)
                                     if (u == i)
-                                        lnL_t[(int64_t)gid[gs] * NT + jb + i] = (double)(kDM ? lin[u] : lin[u] - gqd);
+                                        lnL_t[(lnl_t_compact ? (int64_t)tile_s * kTcS + gs : (int64_t)gid[gs]) * NT + jb + i] =
+                                            (double)(kDM ? lin[u] : lin[u] - gqd);
                         }
                         if (jn > 0 && in_grp) {
                             const float nm = fmaxf(run_mx, cmx);
@@ -914,8 +919,11 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
-                          int *tile_counter, cudaStream_t st)
+                          int *tile_counter, cudaStream_t st, const uint32_t *n_dev, int lnl_t_compact,
+                          int64_t n_theta)
 {
+    if (n_theta <= 0)
+        n_theta = n;
     if (n <= 0)
         return cudaSuccess;
     int dev = 0, sms = 0, max_smem = 0;
@@ -934,8 +942,8 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
         return e;
     const int64_t tiles = (n + kTcS - 1) / kTcS;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    kern<<<grid, kTcThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err,
-                                                  tile_counter);
+    kern<<<grid, kTcThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err, tile_counter,
+                                          n_dev, n_theta, lnl_t_compact);
     return cudaGetLastError();
 }
 

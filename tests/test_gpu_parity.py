@@ -322,6 +322,23 @@ def test_mixed_precision_high_snr(G, orc):
     assert np.max(np.abs(got32[top] - exp[top])) > np.max(np.abs(got[top] - exp[top]))
 
 
+def test_mixed_precision_reproducible(G, orc):
+    """RIFT_MIXED twice on the same seed: the selection of the samples to re-evaluate is
+    in index order and the float32 bins come from fixed tiles, so every value repeats
+    exactly."""
+    p, _ = high_snr_realisable(orc)
+    n = 20000
+    out = []
+    for _ in range(2):
+        with G.ILE(p, precision=G.RIFT_MIXED, max_samples=n, n_bins=32, seed=11) as s:
+            r = s.adapt(2, n)
+            out.append((r, s.last_batch(n)))
+    (r0, b0), (r1, b1) = out
+    assert r0["lnZ_iter"] == r1["lnZ_iter"] and r0["lnZ"] == r1["lnZ"]
+    for a, b in zip(b0, b1):
+        assert np.array_equal(a, b)
+
+
 def test_mixed_precision_adapt_lnZ(G, orc):
     """Adaptive iterations in RIFT_MIXED at SNR 150: ln Z of the device's own
     sample stream within 1e-3 of the oracle's."""
