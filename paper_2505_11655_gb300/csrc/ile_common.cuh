@@ -301,10 +301,17 @@ __device__ __forceinline__ double fn_log(double x) { return log(x); }
 // phi_m at x_m: [x_m - d, x_m + d] with d = 2 thr / (g + sqrt(g^2 + 4 b thr)), g the slope
 // at x_m (0 for an interior maximum).  The exponent is taken relative to phi_m through
 // phi(x) - phi_m = phi'(x_m) (x - x_m) - b (x - x_m)^2, free of cancellation.
+// Division where only a placement (a peak, an integration support) depends on it: the
+// fast reciprocal-based quotient in float32, the IEEE one in float64.
+__device__ __forceinline__ float fn_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double fn_div(double x, double y) { return x / y; }
+
 template <typename T, int N, int NP>
 __device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi, T lnC, T a, T b, T thr)
 {
-    T xm = b > (T)0 ? a / ((T)2 * b) : (a > (T)0 ? xhi : xlo);
+    // the integral is taken relative to the exponent at xm, so xm only has to be close to
+    // the maximum
+    T xm = b > (T)0 ? fn_div(a, (T)2 * b) : (a > (T)0 ? xhi : xlo);
     xm = xm < xlo ? xlo : (xm > xhi ? xhi : xm);
     const T slope = a - (T)2 * b * xm;
     const T phim = xm * (a - b * xm);
@@ -312,19 +319,26 @@ __device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi
     const T den = g + sqrt(g * g + (T)4 * b * thr);
     T L = xlo, R = xhi;
     if (den > (T)0) {
-        const T d = (T)2 * thr / den;
+        const T d = fn_div((T)2 * thr, den);
         L = xm - d > xlo ? xm - d : xlo;
         R = xm + d < xhi ? xm + d : xhi;
     }
-    const T ul = fn_log(L), h = (fn_log(R) - ul) / (T)NP;
+    const T ul = fn_log(L), h = (fn_log(R) - ul) * ((T)1 / (T)NP);
+    // node x = exp(c0 + h t / 2) = exp(c0) exp(h t / 2): the second factor is the same in
+    // every panel
+    T en[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        en[i] = fn_exp((T)0.5 * h * gt[i]);
     T s = (T)0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const T c0 = ul + ((T)p + (T)0.5) * h;
+        const T ec = fn_exp(c0);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const T u = c0 + (T)0.5 * h * gt[i];
-            const T dx = fn_exp(u) - xm;
+            const T dx = ec * en[i] - xm;
             s += gw[i] * fn_exp(slope * dx - b * dx * dx - (T)3 * u);
         }
     }
@@ -336,7 +350,7 @@ __device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi
 __device__ __forceinline__ float dm_bound32(const Problem &P, float a, float b)
 {
     const float xlo = P.dm_xlo_f, xhi = P.dm_xhi_f;
-    float xm = b > 0.f ? a / (2.f * b) : (a > 0.f ? xhi : xlo);
+    float xm = b > 0.f ? __fdividef(a, 2.f * b) : (a > 0.f ? xhi : xlo);
     xm = fminf(fmaxf(xm, xlo), xhi);
     return P.dm_lnub_f + xm * (a - b * xm);
 }

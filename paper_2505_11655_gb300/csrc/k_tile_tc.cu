@@ -795,12 +795,14 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             // with the highest bound is evaluated, and a bin whose bound lies
                             // more than 40 below the larger of that value and the running
                             // maximum cannot move the marginal (< e^-40): left out
-                            float bnd[kTcBPT], bmax = -INFINITY, abest = 0.f;
+                            // (the bound is recomputed in the second loop rather than kept: it is
+                            // a handful of operations, a register array of it is not)
+                            float bmax = -INFINITY, abest = 0.f;
 #pragma unroll
                             for (int i = 0; i < kTcBPT; ++i) {
-                                bnd[i] = i < jn ? dm_bound32(P, lin[i], gqd) : -INFINITY;
-                                if (bnd[i] > bmax) {
-                                    bmax = bnd[i];
+                                const float bd = i < jn ? dm_bound32(P, lin[i], gqd) : -INFINITY;
+                                if (bd > bmax) {
+                                    bmax = bd;
                                     abest = lin[i];
                                 }
                             }
@@ -809,7 +811,8 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             const float thr = lnL_t ? -INFINITY : fmaxf(run_mx, vbest) - 40.f;
 #pragma unroll
                             for (int i = 0; i < kTcBPT; ++i) {
-                                lin[i] = (i < jn && bnd[i] >= thr) ? ln_dist_marg32(P, lin[i], gqd) : -INFINITY;
+                                lin[i] = (i < jn && dm_bound32(P, lin[i], gqd) >= thr) ? ln_dist_marg32(P, lin[i], gqd)
+                                                                                      : -INFINITY;
                                 if (i < jn)
                                     cmx = fmaxf(cmx, lin[i]);
                             }
