@@ -71,12 +71,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Named barrier over `count` threads (a multiple of 32).
-__device__ __forceinline__ void named_bar(int id, int count)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 // Named barrier that also ORs a predicate over the participating threads.
 __device__ __forceinline__ int named_bar_or(int id, int count, int pred)
 {
@@ -112,35 +106,15 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, no swizzle (canonical K-major core-matrix layout):
-// start address, leading-dimension byte offset (next core matrix along K), stride
-// byte offset (next 8-row group), version bits 46-48 = 0b001.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
+// Shared-memory matrix descriptors (no swizzle, canonical K-major core-matrix layout) are
+// built by the kernels: bits 0-13 start address >> 4, 16-29 leading-dimension byte offset
+// >> 4 (next core matrix along K), 32-45 stride byte offset >> 4 (next 8-row group), bit 46
+// set (descriptor version).
 
 // Instruction descriptor of kind::f16: F32 accumulator, F16 A and B, both K-major.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(uint32_t M, uint32_t N)
 {
     return (1u << 4) | ((N >> 3) << 17) | ((M >> 4) << 24);
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
 }
 
 // D[tmem] (+)= A[tmem] * B[smem]^T: A (M = 128 rows, one per lane) in tensor memory, two
@@ -163,22 +137,8 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-// 32 lanes x 32 consecutive 32-bit columns: thread i of the warp receives lane
-// (warp quarter base + i), columns taddr.col .. +31.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *v)
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-}
-
-// 32 lanes x 16 consecutive 32-bit columns (as tmem_ld32, half the columns).
+// 32 lanes x 16 consecutive 32-bit columns: thread i of the warp receives lane
+// (warp quarter base + i), columns taddr.col .. +15.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *v)
 {
     asm volatile(
