@@ -278,7 +278,7 @@ bool use_tc(const rift_ile_t *h, int64_t n)
 cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
                          const double *lnpw, double *lnw)
 {
-    const BinTable bt{h->bin_i, h->bin_f};
+    const BinTable bt{h->bin_i, h->bin_f, std::log((double)h->prob.n_t)};
     if (use_tc(h, n))
         return launch_lnl_tc(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->tile_counter,
                              h->stream);
@@ -301,7 +301,7 @@ int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmar
     // within its margin in float64
     int64_t rows = 0;
     if (h->refine_bins && use_tc(h, n)) {
-        const BinTable bt{h->bin_i, h->bin_f};
+        const BinTable bt{h->bin_i, h->bin_f, std::log((double)h->prob.n_t)};
         rows = std::min<int64_t>(h->refine_rows, n);
         CK(launch_lnl_tc(h->prob, bt, theta, h->sel_idx, rows, lnL_tmarg, h->refine_bins, lnpw, lnw, h->err,
                          h->tile_counter, h->stream, h->sel_count, 1, n));

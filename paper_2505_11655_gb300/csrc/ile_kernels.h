@@ -71,6 +71,7 @@ cudaError_t prepare_tc_kernels();
 struct BinTable {
     const int *bin_i;
     const float *bin_f;
+    double ln_nt;   // ln of the number of bins (the uniform time prior's normalisation)
 };
 
 // ln L over the time grid for n samples theta[n][6] (float64 everywhere).

@@ -59,11 +59,15 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
             const double *Cd = sC + d * (B + 1);
             const double tot = Cd[B];
             const double x = u[d] * tot;
-            // last b in [0, B-1] with C[b] <= x (C[0] = 0 <= x always)
+            // last b in [0, B-1] with C[b] <= x (C[0] = 0 <= x always).  Non-negative doubles
+            // order like their bit patterns read as integers, so the search compares integers
+            // (float64 comparisons run on the slow float64 pipe of this part)
+            const long long xb = __double_as_longlong(x);
+            const long long *Cb = reinterpret_cast<const long long *>(Cd);
             int lo = 0, hi = B - 1;
             while (lo < hi) {
                 int mid = (lo + hi + 1) >> 1;
-                if (Cd[mid] <= x)
+                if (Cb[mid] <= xb)
                     lo = mid;
                 else
                     hi = mid - 1;

@@ -102,6 +102,9 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
     uint32_t *gid = reinterpret_cast<uint32_t *>(smraw + L.gid);
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];
     __shared__ int tile_s;
+    // bins per chunk for each offset spread that uses the shared window (the float64
+    // division once per block: float64 is slow on this part)
+    __shared__ int jmax_s[kNCol - 15];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double beta = P.t_step * P.fs;
@@ -110,6 +113,10 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
     for (int j = tid; j < NT; j += kTThreads) {
         bini[j] = bt.bin_i[j];
         binf[j] = bt.bin_f[j];
+    }
+    for (int sp = tid; sp <= kNCol - 16; sp += kTThreads) {
+        const int jm = !(beta > 0.0) ? kMaxChunkBins : (int)floor((double)(kNCol - 8 - sp - 1) / beta) + 1;
+        jmax_s[sp] = max(1, min(jm, kMaxChunkBins));
     }
 
     for (;;) {
@@ -145,7 +152,7 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             sincosf((float)(0.5 * th[4]), &shalf, &chalf);
             par[tid] = c2p;
             par[kTS + tid] = s2p;
-            par[2 * kTS + tid] = valid ? (P.dist_marg ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
+            par[2 * kTS + tid] = valid ? (P.dist_marg ? 1.f : (float)P.d_ref / (float)th[5]) : 0.f;
             par[3 * kTS + tid] = (float)th[3];
             par[4 * kTS + tid] = (float)(-sk.sh);
             par[5 * kTS + tid] = (float)sk.ch;
@@ -244,8 +251,7 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
         for (int k = 0; k < K; ++k)
             spread = max(spread, hi_s[k] - lo_s[k]);
         const bool direct = spread > kNCol - 16;   // no shared window: evaluate from global memory
-        int jmax = (direct || !(beta > 0.0)) ? kMaxChunkBins : (int)floor((double)(kNCol - 8 - spread - 1) / beta) + 1;
-        jmax = max(1, min(jmax, kMaxChunkBins));
+        const int jmax = direct ? kMaxChunkBins : jmax_s[spread];
         const int n_chunks = (NT + jmax - 1) / jmax;
         const int jnom = (NT + n_chunks - 1) / n_chunks;
         const int n_steps = n_chunks * K;
@@ -493,7 +499,8 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             const int s = warp + 8 * lane;
             const uint32_t g = gid[s];
             if (g != 0xffffffffu) {
-                double r = (double)mxv + log((double)smv) - log((double)NT);
+                // float32 like the partials (float64 is slow on this part); smv >= 1
+                const double r = (double)mxv + (double)__logf(smv) - bt.ln_nt;
                 if (!isfinite(r))
                     atomicOr(err, kErrNonFinite);
                 lnL_tmarg[g] = r;

@@ -289,6 +289,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
     __shared__ int glo[kTcS][kMaxDet], ghi[kTcS][kMaxDet], gstart[kTcS + 1];
     __shared__ int tile_s, abort_s, ngroups_s;
+    // bins per chunk for each sub-group offset spread (the float64 division once per block:
+    // float64 is slow on this part)
+    __shared__ int jmax_s[kTcSpreadLimit + 1];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double beta = P.t_step * P.fs;
@@ -312,6 +315,13 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 
     for (int j = tid; j < NT; j += blockDim.x) {
         bins[j] = make_int2(bt.bin_i[j], __float_as_int(bt.bin_f[j]));
+    }
+    // the nodes read for the bins j0 .. j0 + jmax - 1 lie within (jmax - 1) beta + 3 columns of
+    // a sample's first node; with the spread of the sub-group's offsets and up to 7 columns of
+    // window alignment that is at most kTcW - 1
+    for (int sp = tid; sp <= kTcSpreadLimit; sp += blockDim.x) {
+        const int jm = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - sp) / beta) + 1;
+        jmax_s[sp] = max(1, min(jm, kTcMaxBins));
     }
     if (warp == 0)
         tc::tmem_alloc(tptr, 512);
@@ -389,7 +399,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             sincosf((float)th[3], &sphi, &cphi);
             par[tid] = c2p;
             par[kTcS + tid] = s2p;
-            par[2 * kTcS + tid] = valid ? (kDM ? 1.f : (float)(P.d_ref / th[5])) : 0.f;
+            par[2 * kTcS + tid] = valid ? (kDM ? 1.f : (float)P.d_ref / (float)th[5]) : 0.f;
             float pc = 1.f, ps = 1.f;
             pw[tid] = 1.f;
             pw[kTcPow * kTcS + tid] = 1.f;
@@ -627,7 +637,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             for (int k = 0; k < K; ++k)
                 spread = max(spread, ghi[grp][k] - glo[grp][k]);
             const bool in_grp = gs >= gstart[grp] && gs < gstart[grp + 1];
-            int jmax = !(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1;
+            // a sub-group's spread never exceeds kTcSpreadLimit (the cut above); the float64
+            // expression is kept for the case that cannot occur
+            int jmax = spread <= kTcSpreadLimit ? jmax_s[spread]
+                                                : (!(beta > 0.0) ? kTcMaxBins : (int)floor((double)(kTcW - 11 - spread) / beta) + 1);
             jmax = max(1, min(jmax, kTcMaxBins));
             const int n_chunks = (NT + jmax - 1) / jmax;
             const int jnom = (NT + n_chunks - 1) / n_chunks;
@@ -887,17 +900,19 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
         if (tid < kTcS && gid[tid] != 0xffffffffu) {
+            // float32 like the partials (float64 is slow on this part): the largest partial
+            // contributes a sum >= 1, so the logarithm is well conditioned
             float mx = -INFINITY;
             for (int h = 0; h < kTcQ; ++h)
                 mx = fmaxf(mx, lse[h * kTcS + tid]);
-            double sum = 0.0;
+            float sum = 0.f;
             for (int h = 0; h < kTcQ; ++h) {
                 const float m = lse[h * kTcS + tid];
                 if (m != -INFINITY)
-                    sum += (double)lse[(kTcQ + h) * kTcS + tid] * exp((double)m - (double)mx);
+                    sum += lse[(kTcQ + h) * kTcS + tid] * __expf(m - mx);
             }
             const uint32_t g = gid[tid];
-            double r = (double)mx + log(sum) - log((double)NT);
+            const double r = (double)mx + (double)__logf(sum) - bt.ln_nt;
             if (!isfinite(r))
                 atomicOr(err, kErrNonFinite);
             lnL_tmarg[g] = r;
