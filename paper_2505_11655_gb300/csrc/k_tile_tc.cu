@@ -594,10 +594,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         } else if (!producer) {
             // warp (q, cb) drains 16-column chunks cb, cb + 4, ... of the K W tiles for the
             // 32 samples of its lane quarter q
-            int ok = 1;
-            if (lane == 0)
-                ok = tc::mbar_wait(wbar, phbit(kPhTile, 0), kWaitNs) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+            const int ok = tc::mbar_wait(wbar, phbit(kPhTile, 0), kWaitNs) ? 1 : 0;
             tc::tc_fence_after();
             const int q = warp & 3, cb = warp >> 2, s = 32 * q + lane;
             float qp = 0.f;
@@ -731,12 +728,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     const int b = t & 1, J = min(jnom, NT - j0);
                     const int jq = (J + kTcQ - 1) / kTcQ;                 // bins per quarter
                     const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins
-                    // one lane per warp waits for the MMAs of step t
-                    int ok = 1;
-                    if (lane == 0)
-                        ok = tc::mbar_wait(fullb + b, phbit(kPhFull, b), kWaitNs) ? 1 : 0;
+                    // every lane waits for the MMAs of step t (the same barrier word: no
+                    // divergent branch, no broadcast of the result)
+                    const int ok = tc::mbar_wait(fullb + b, phbit(kPhFull, b), kWaitNs) ? 1 : 0;
                     ph ^= 1u << (kPhFull + b);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
                     tc::tc_fence_after();
                     // The rows of sample quarter q (TMEM lanes 32q..) are drained and gathered by
                     // the same four warps (warp & 3 == q), which synchronise on their own barrier
@@ -762,8 +757,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     }
                     tc::tc_fence_before();
                     __syncwarp();
-                    if (lane == 0)
-                        tc::mbar_arrive(emptyb + b);
+                    tc::mbar_arrive_if(emptyb + b, lane == 0);
                     // this quarter's rows of R complete; agree on failure
                     if (tc::named_bar_or(qbar, kTcConsumers / 4, !ok || abort_s)) {
                         failed = 1;

@@ -71,6 +71,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Arrive only where `pred` holds, as a predicated instruction (no branch around it).
+__device__ __forceinline__ void mbar_arrive_if(uint64_t *bar, bool pred)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(smem_u32(bar)),
+        "r"((uint32_t)pred)
+        : "memory");
+}
+
 // Named barrier that also ORs a predicate over the participating threads.
 __device__ __forceinline__ int named_bar_or(int id, int count, int pred)
 {
