@@ -442,6 +442,18 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             const float amp = par[2 * kTcS + s];
             fx[k * kTcS + s] = make_float2(amp * F.re, amp * F.im);
         }
+        // ---------------- C: harmonics Y_m = -2Y_lm(iota, -phi) [M][kTcS] (float32); the mode
+        // coefficient of detector k is c_k,m = fx_k Y_m.  C reads only what A wrote, so it
+        // follows B without a barrier (the float64 delays of B overlap the float32 work of C).
+        for (int it = tid; tid < kTcConsumers && it < kTcS * M; it += kTcConsumers) {
+            const int s = it % kTcS, m = it / kTcS;
+            float d = 0.f;
+            for (int t = 0; t < P.wn[m]; ++t)
+                d += P.wcoef_f[m][t] * pw[P.wpc[m][t] * kTcS + s] * pw[(kTcPow + P.wps[m][t]) * kTcS + s];
+            const int mm = P.mode_m[m];
+            const float2 e = pe[(mm < 0 ? -mm : mm) * kTcS + s];   // exp(-i |m| phi)
+            Ys[m * kTcS + s] = make_float2(d * e.x, d * (mm < 0 ? -e.y : e.y));
+        }
         __syncthreads();
         // sub-groups: the whole tile when it is compact, else a greedy cut along the sort order
         if (tid == 0) {
@@ -495,18 +507,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             gstart[ng] = kTcS;
             ngroups_s = ng;
         }
-        // ---------------- C: harmonics Y_m = -2Y_lm(iota, -phi) [M][kTcS] (float32); the mode
-        // coefficient of detector k is c_k,m = fx_k Y_m
-        for (int it = tid; tid < kTcConsumers && it < kTcS * M; it += kTcConsumers) {
-            const int s = it % kTcS, m = it / kTcS;
-            float d = 0.f;
-            for (int t = 0; t < P.wn[m]; ++t)
-                d += P.wcoef_f[m][t] * pw[P.wpc[m][t] * kTcS + s] * pw[(kTcPow + P.wps[m][t]) * kTcS + s];
-            const int mm = P.mode_m[m];
-            const float2 e = pe[(mm < 0 ? -mm : mm) * kTcS + s];   // exp(-i |m| phi)
-            Ys[m * kTcS + s] = make_float2(d * e.x, d * (mm < 0 ? -e.y : e.y));
-        }
-        __syncthreads();
         // ---------------- E: A operand, float16 hi/lo with a power-of-two scale per (sample,
         // detector), written into tensor memory: the thread of sample s writes lane s (its
         // warp's lane quarter), 16 components (8 columns) per store.  The previous tile's MMAs,
