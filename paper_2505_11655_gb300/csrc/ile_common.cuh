@@ -330,17 +330,21 @@ __device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi
 #pragma unroll
     for (int i = 0; i < N; ++i)
         en[i] = fn_exp((T)0.5 * h * gt[i]);
+    // panel centre c0 = ln L + (p + 1/2) h: exp(c0) = L e^(h/2) e^(p h), one exponential for
+    // all panels
+    const T eh = fn_exp((T)0.5 * h), eh2 = eh * eh;
+    T ec = L * eh;
     T s = (T)0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const T c0 = ul + ((T)p + (T)0.5) * h;
-        const T ec = fn_exp(c0);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             const T u = c0 + (T)0.5 * h * gt[i];
             const T dx = ec * en[i] - xm;
             s += gw[i] * fn_exp(slope * dx - b * dx * dx - (T)3 * u);
         }
+        ec *= eh2;
     }
     return lnC + phim + fn_log((T)0.5 * h * s);
 }
