@@ -391,10 +391,11 @@ int run_iteration(rift_ile_t *h, int64_t n, int slot, bool adapt, bool reset_poo
             RK(refine_batch(h, h->theta, n, h->lnL, h->lnpw, h->lnw));
     }
     CK(mark(h, slot, 2));
+    const bool f32_terms = h->cfg.precision == RIFT_FP32;
     CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, slot, h->pooled, reset_pooled ? 1 : 0, h->err,
-                     h->stream));
+                     h->stream, f32_terms));
     if (adapt)
-        CK(launch_adapt(S, h->bins, h->lnw, n, h->stats, slot, h->hist_partial, h->stream));
+        CK(launch_adapt(S, h->bins, h->lnw, n, h->stats, slot, h->hist_partial, h->stream, f32_terms));
     CK(mark(h, slot, 3));
     h->launches += 1 + sorted + 1 + 2 + (adapt ? 2 : 0);
     return RIFT_OK;

@@ -299,7 +299,7 @@ int av_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, double p
     }
     CK(mark(h, slot, 2));
     CK(launch_reduce(h->lnw, h->lnL, n, h->red_partial, h->stats, slot, h->pooled, reset_pooled ? 1 : 0, h->err,
-                     st));
+                     st, h->cfg.precision == RIFT_FP32));
     CK(mark(h, slot, 3));
     h->launches += 1 + sorted + 1 + 2;
     // 3. live set

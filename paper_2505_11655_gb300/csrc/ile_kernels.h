@@ -164,12 +164,15 @@ SkyGrid sky_grid_for(int64_t n, int per_cell = 4);
 // Reduction of ln w and ln L_tmarg for iteration slot `slot`:
 //   stats[slot*8 + 0..7] = lnZ, sigma, n_eff, n_ess, max lnw, max lnL, N, (unused)
 //   pooled[0..4] = running max lnw, s1, s2 (relative to the max), N, max lnL over all slots.
+// f32_terms: the terms exp(lnw - max) in float32 (relative error ~1e-7, for ln w that carry
+// float32 errors themselves: the float32 path); sums, maxima and everything else in float64.
 constexpr int kRedBlocks = 304;
 cudaError_t launch_reduce(const double *lnw, const double *lnL, int64_t n, double *partial, double *stats, int slot,
-                          double *pooled, int reset_pooled, int *err, cudaStream_t st);
-// Histogram adaptation of the sampler from weights exp(beta (lnw - max lnw)) (max from stats[slot]).
+                          double *pooled, int reset_pooled, int *err, cudaStream_t st, bool f32_terms = false);
+// Histogram adaptation of the sampler from weights exp(beta (lnw - max lnw)) (max from stats[slot]);
+// f32_terms as for launch_reduce (the weights stay deterministic: summed exactly in fixed point).
 cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
-                         int slot, uint64_t *hist_partial, cudaStream_t st);
+                         int slot, uint64_t *hist_partial, cudaStream_t st, bool f32_terms = false);
 cudaError_t launch_build_cdf(const SamplerDev &S, cudaStream_t st);
 // Final pooled statistics into out[0..7] = lnZ, sigma, n_eff, n_ess, max lnL, N; the
 // device iteration counter moves on by `advance`.

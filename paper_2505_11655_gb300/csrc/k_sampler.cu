@@ -529,9 +529,16 @@ __device__ Acc block_merge(Acc a)
 }
 
 // Pass 1: per block, over a contiguous stripe (deterministic for a fixed n).
+// exp(t) for t <= 0: float64, or float32 for terms that carry float32 errors already
+// (float64 exponentials run on this part's slow float64 pipe)
+__device__ __forceinline__ double term_exp(double t, bool f32)
+{
+    return f32 ? (double)expf((float)t) : exp(t);
+}
+
 __global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const double *__restrict__ lnw,
                                                                      const double *__restrict__ lnL, int64_t n,
-                                                                     double *__restrict__ partial)
+                                                                     double *__restrict__ partial, bool f32)
 {
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b0 = (int64_t)blockIdx.x * per;
@@ -545,12 +552,12 @@ __global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const doubl
             continue;
         }
         if (x > a.mx) {
-            double f = (a.mx == -INFINITY) ? 0.0 : exp(a.mx - x);
+            double f = (a.mx == -INFINITY) ? 0.0 : term_exp(a.mx - x, f32);
             a.s1 = a.s1 * f + 1.0;
             a.s2 = a.s2 * f * f + 1.0;
             a.mx = x;
         } else {
-            double e = exp(x - a.mx);
+            double e = term_exp(x - a.mx, f32);
             a.s1 += e;
             a.s2 += e * e;
         }
@@ -605,14 +612,14 @@ __global__ void __launch_bounds__(kRedThreads) reduce_final_kernel(const double 
 }
 
 cudaError_t launch_reduce(const double *lnw, const double *lnL, int64_t n, double *partial, double *stats, int slot,
-                          double *pooled, int reset_pooled, int *err, cudaStream_t st)
+                          double *pooled, int reset_pooled, int *err, cudaStream_t st, bool f32_terms)
 {
     int nb = kRedBlocks;
     if ((int64_t)nb * 64 > n)
         nb = (int)((n + 63) / 64);
     if (nb < 1)
         nb = 1;
-    reduce_partial_kernel<<<nb, kRedThreads, 0, st>>>(lnw, lnL, n, partial);
+    reduce_partial_kernel<<<nb, kRedThreads, 0, st>>>(lnw, lnL, n, partial, f32_terms);
     reduce_final_kernel<<<1, kRedThreads, 0, st>>>(partial, nb, n, stats, slot, pooled, reset_pooled, err);
     return cudaGetLastError();
 }
@@ -686,7 +693,7 @@ __device__ __forceinline__ void add_fixed(unsigned long long *lo, unsigned long 
 __global__ void __launch_bounds__(256) hist_partial_kernel(SamplerDev S, const uint64_t *__restrict__ bins,
                                                            const double *__restrict__ lnw, int64_t n,
                                                            const double *__restrict__ stats, int slot,
-                                                           uint64_t *__restrict__ partial)
+                                                           uint64_t *__restrict__ partial, bool f32)
 {
     extern __shared__ unsigned long long sF[];   // [6][B][2] = (lo, hi) per bin
     const int B = S.B;
@@ -701,7 +708,7 @@ __global__ void __launch_bounds__(256) hist_partial_kernel(SamplerDev S, const u
         if (!isfinite(x))
             continue;
         uint64_t lo, hi;
-        to_fixed(exp(S.temper * (x - mx)), lo, hi);
+        to_fixed(term_exp(S.temper * (x - mx), f32), lo, hi);
         if (!(lo | hi))
             continue;
         uint64_t pk = bins[i];
@@ -766,7 +773,7 @@ __global__ void adapt_final_kernel(SamplerDev S, const uint64_t *__restrict__ pa
 }
 
 cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double *lnw, int64_t n, const double *stats,
-                         int slot, uint64_t *hist_partial, cudaStream_t st)
+                         int slot, uint64_t *hist_partial, cudaStream_t st, bool f32_terms)
 {
     int nb = kHistBlocks;
     if ((int64_t)nb * 256 > n)
@@ -779,7 +786,7 @@ cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double
         if (e != cudaSuccess)
             return e;
     }
-    hist_partial_kernel<<<nb, 256, smem, st>>>(S, bins, lnw, n, stats, slot, hist_partial);
+    hist_partial_kernel<<<nb, 256, smem, st>>>(S, bins, lnw, n, stats, slot, hist_partial, f32_terms);
     adapt_final_kernel<<<1, 6 * 32, 0, st>>>(S, hist_partial, nb);
     return cudaGetLastError();
 }
