@@ -528,7 +528,6 @@ __device__ Acc block_merge(Acc a)
     return a;   // valid in warp 0
 }
 
-// Pass 1: per block, over a contiguous stripe (deterministic for a fixed n).
 // exp(t) for t <= 0: float64, or float32 for terms that carry float32 errors already
 // (float64 exponentials run on this part's slow float64 pipe)
 __device__ __forceinline__ double term_exp(double t, bool f32)
@@ -536,6 +535,7 @@ __device__ __forceinline__ double term_exp(double t, bool f32)
     return f32 ? (double)expf((float)t) : exp(t);
 }
 
+// Pass 1: per block, over a contiguous stripe (deterministic for a fixed n).
 __global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const double *__restrict__ lnw,
                                                                      const double *__restrict__ lnL, int64_t n,
                                                                      double *__restrict__ partial, bool f32)
