@@ -195,10 +195,15 @@ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
 }
 
 // 53-bit uniform in [0, 1) from two words (27 high bits of a, 26 of b).
+// the 53-bit integer m of the uniform u = m 2^-53 built from two 32-bit Philox words
+__device__ __forceinline__ unsigned long long bits53(uint32_t a, uint32_t b)
+{
+    return ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
+}
+
 __device__ __forceinline__ double unit53(uint32_t a, uint32_t b)
 {
-    unsigned long long v = ((unsigned long long)(a >> 5) << 26) | (unsigned long long)(b >> 6);
-    return (double)v * 0x1.0p-53;
+    return (double)bits53(a, b) * 0x1.0p-53;
 }
 
 // ---------------------------------------------------------------- sort key

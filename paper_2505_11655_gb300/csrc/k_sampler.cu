@@ -45,20 +45,22 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
     const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
     const double d3lo = S.d_min * S.d_min * S.d_min, d3hi = S.d_max * S.d_max * S.d_max;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double u[6];
+        // the 53-bit integers m of the uniforms u = m 2^-53
+        double m53[6];
 #pragma unroll
         for (uint32_t p = 0; p < 3; ++p) {
             U4 r = philox10(U4{(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p}, k0, k1);
-            u[2 * p] = unit53(r.x, r.y);
-            u[2 * p + 1] = unit53(r.z, r.w);
+            m53[2 * p] = (double)bits53(r.x, r.y);
+            m53[2 * p + 1] = (double)bits53(r.z, r.w);
         }
         double v[6], lr = 0.0;
         uint64_t packed = 0;
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
             const double *Cd = sC + d * (B + 1);
-            const double tot = Cd[B];
-            const double x = u[d] * tot;
+            // x = u tot = m (2^-53 tot): both scalings by 2^-53 are exact, so this is the
+            // same single rounding as (m 2^-53) tot
+            const double x = m53[d] * (Cd[B] * 0x1.0p-53);
             // last b in [0, B-1] with C[b] <= x (C[0] = 0 <= x always).  Non-negative doubles
             // order like their bit patterns read as integers, so the search compares integers
             // (float64 comparisons run on the slow float64 pipe of this part)
@@ -72,11 +74,14 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
                 else
                     hi = mid - 1;
             }
-            double t = (x - Cd[lo]) * sR[d * B + lo];
-            if (!(t >= 0.0))
-                t = 0.0;
-            if (t >= 1.0)
-                t = 0x1.fffffffffffffp-1;
+            // t in [0, 1): negative or NaN -> 0, [1, inf] -> the largest double below 1,
+            // decided on the bit pattern (integer comparisons)
+            long long tb = __double_as_longlong((x - Cd[lo]) * sR[d * B + lo]);
+            if (tb < 0 || (tb & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL)
+                tb = 0;
+            else if (tb >= 0x3ff0000000000000LL)
+                tb = 0x3fefffffffffffffLL;
+            const double t = __longlong_as_double(tb);
             v[d] = (lo + t) * inv_b;
             if (!(S.marg && d == 5))
                 lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
