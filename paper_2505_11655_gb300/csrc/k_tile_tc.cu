@@ -553,6 +553,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             }
             tc::tc_fence_before();
         }
+        // the prologue scratch (generic accesses above) shares its bytes with the B buffers,
+        // which the stager refills by bulk copies (async proxy) once the steps begin
+        tc::fence_proxy_async_smem();
         __syncthreads();
 
         // gather / fold ownership: thread -> sample s, bin quarter h of every chunk
