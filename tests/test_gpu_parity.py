@@ -213,6 +213,21 @@ def test_fp32_marginalize_against_oracle_on_device_stream(G, orc):
     assert abs(r["n_eff"] - red["n_eff"]) <= 1e-2 * red["n_eff"]
 
 
+def test_fp32_reduction_against_float64_reduction_of_same_weights(G, orc):
+    """The float32 path sums float32 exponentials of ln w - max.  The oracle's float64
+    reduction of the device's own ln w pins that reduction alone: the terms' ~1e-7
+    relative error moves ln Z and n_eff by far less than the float32 bars."""
+    p = S.single_large_problem()
+    n = 50000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=12) as s:
+        r = s.marginalize(n)
+        th, lr, ll, lw = s.last_batch(n)
+    red = orc.reduce(lw)
+    assert abs(r["lnZ"] - red["lnZ"]) <= 1e-6
+    assert abs(r["n_eff"] - red["n_eff"]) <= 1e-6 * red["n_eff"]
+    assert abs(r["n_ess"] - red["n_ess"]) <= 1e-6 * red["n_ess"]
+
+
 @pytest.mark.parametrize("tc", ["0", "1"])
 def test_fp32_adapt_two_iterations(G, orc, monkeypatch, tc):
     """Adaptive iterations through the CUDA-core and the tensor-core kernels.  The
