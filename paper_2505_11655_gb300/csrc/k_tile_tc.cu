@@ -743,6 +743,26 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     // every warp of the quarter finished before the barrier of step t - 1.
                     const int qbar = 2 + (warp & 3);
                     float *Rt = (t & 1) ? Rs2 : Rs;
+                    // The gather's own loads do not depend on the drain: issued before it, their
+                    // shared-memory latency overlaps the drain.  Padding samples and samples of
+                    // other sub-groups read at the group's lowest offset, which keeps every read
+                    // in the row; their sums are discarded.
+                    const int iw0 = win0(k, j0);
+                    const bool mine = gok && in_grp;
+                    const float *Rcol = Rt + ((mine ? i0s[k * kTcS + gs] : glo[grp][k]) - iw0) * kTcS + gs;
+                    const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
+                    const float sc = invs[k * kTcS + gs];
+                    if (k == 0) {
+                        // this thread's bins of the chunk, shared by every detector (idle slots
+                        // re-read the chunk's last bin; one 8-byte broadcast load each)
+#pragma unroll
+                        for (int i = 0; i < kTcBPT; ++i) {
+                            const int j = min(jb + i, j0 + J - 1);
+                            const int2 bv = bins[j];
+                            bj[i] = bv.x;
+                            bfj[i] = __int_as_float(bv.y);
+                        }
+                    }
                     {
                         // drain accumulator b: warp quarter q = rows 32q.., column block w / 4 of 32
                         const int q = warp & 3, cb = warp >> 2;
@@ -765,24 +785,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     if (tc::named_bar_or(qbar, kTcConsumers / 4, !ok || abort_s)) {
                         failed = 1;
                         break;
-                    }
-                    const int iw0 = win0(k, j0);
-                    // padding samples and samples of other sub-groups read at the group's lowest
-                    // offset, which keeps every read in the row; their sums are discarded
-                    const bool mine = gok && in_grp;
-                    const float *Rcol = Rt + ((mine ? i0s[k * kTcS + gs] : glo[grp][k]) - iw0) * kTcS + gs;
-                    const float ff = mine ? f0s[k * kTcS + gs] : 0.f;
-                    const float sc = invs[k * kTcS + gs];
-                    if (k == 0) {
-                        // this thread's bins of the chunk, shared by every detector (idle slots
-                        // re-read the chunk's last bin)
-#pragma unroll
-                        for (int i = 0; i < kTcBPT; ++i) {
-                            const int j = min(jb + i, j0 + J - 1);
-                            const int2 bv = bins[j];   // one 8-byte broadcast load
-                            bj[i] = bv.x;
-                            bfj[i] = __int_as_float(bv.y);
-                        }
                     }
                     // two bins per packed float32 operation (the same roundings as one at a time)
 #pragma unroll
