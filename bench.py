@@ -382,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
                      "note": "algorithmic flops of the method against the FP32 FMA peak; the mode contraction "
                              "(95% of them) runs on tcgen05 as a float16 hi/lo split, so this fraction is not a "
                              "unit's utilisation: in the ncu capture no unit is saturated (shared-memory "
-                             "wavefronts ~42% of the LSU pipe's bandwidth, issue 53%, tensor pipe 16%); the "
+                             "wavefronts ~46% of the LSU pipe's bandwidth, issue 57%, tensor pipe 18%); the "
                              "per-step drain of the accumulators into shared memory and the per-bin gather "
                              "bound the kernel"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
