@@ -295,6 +295,13 @@ __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const S
 __device__ __forceinline__ float fn_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double fn_exp(double x) { return exp(x); }
 __device__ __forceinline__ float fn_log(float x) { return __logf(x); }
+// 2^x in float32: one ex2.approx
+__device__ __forceinline__ float fn_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double fn_log(double x) { return log(x); }
 
 // ln of the distance-marginal likelihood of one bin.  ln L is exactly a x - b x^2 in
@@ -339,15 +346,31 @@ __device__ __forceinline__ T ln_dist_marg(const T *gt, const T *gw, T xlo, T xhi
     // all panels
     const T eh = fn_exp((T)0.5 * h), eh2 = eh * eh;
     T ec = L * eh;
+    // exponent at node x = ec en_i, u = ln x = c0 + h t_i / 2, dx = x - xm:
+    //   slope dx - b dx^2 - 3 u = dx (slope - b dx) + (-3 c0) + (-3 h t_i / 2),
+    // the last term once per bin; float32 takes it in base 2 (e^E = 2^(E log2 e)) with log2 e
+    // in the coefficients, so that each node costs one ex2
+    constexpr bool kF32 = sizeof(T) == 4;
+    const T ks = kF32 ? (T)1.4426950408889634 : (T)1;
+    const T sl = slope * ks, bs = b * ks;
+    T m3h[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        m3h[i] = (T)-1.5 * ks * h * gt[i];
     T s = (T)0;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-        const T c0 = ul + ((T)p + (T)0.5) * h;
+        const T m3c = (T)-3 * ks * (ul + ((T)p + (T)0.5) * h);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const T u = c0 + (T)0.5 * h * gt[i];
             const T dx = ec * en[i] - xm;
-            s += gw[i] * fn_exp(slope * dx - b * dx * dx - (T)3 * u);
+            const T E = dx * (sl - bs * dx) + (m3c + m3h[i]);
+            T e;
+            if constexpr (kF32)
+                e = fn_exp2(E);
+            else
+                e = fn_exp(E);
+            s += gw[i] * e;
         }
         ec *= eh2;
     }
