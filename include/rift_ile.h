@@ -235,11 +235,13 @@ int rift_ile_last_batch(rift_ile_t *h, int mem, double *theta, double *lnp_minus
  *   3. the draws passing the current threshold join the live set (draw order, at most
  *      `capacity` live points);
  *   4. the threshold keeps the fewest top 1/64-wide ln L bins (below the live maximum)
- *      holding the fraction p_thr of the live mass or n_min_star points, whichever comes
- *      first; masses are exact fixed-point integers;
- *   5. refinement: V' = V N_min / N_live, dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6)
- *      (Eq. nbins_V) rounded down to a power of two and never coarser; the new active
- *      cells are the cells holding a kept live point.
+ *      holding both the fraction p_thr of the live mass and at least n_min_star points
+ *      (n_min_star is a floor: while a few points carry p_thr of the mass, the top
+ *      n_min_star set the threshold); masses are exact fixed-point integers;
+ *   5. refinement: with V_thr the estimated volume above the current threshold (1 at the
+ *      start), V' = V_thr N_min / N_live, dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6)
+ *      (Eq. nbins_V) rounded down to a power of two and never coarser, V_thr <- V'; the
+ *      new active cells are the cells holding a kept live point.
  * Draw i of AV iteration g uses Philox4x32-10 with key = seed and counter
  * (i low, i high, g, p), p = 0..3: the first word pair chooses the cell (first of the
  * sorted active cells at floor(U n_cells / 2^53)), the next six the in-cell uniforms.

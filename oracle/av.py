@@ -15,10 +15,11 @@ prior is uniform there, so the evidence is Z = int L dv).  Each iteration g:
 4. threshold: histogram the live ln L in bins of 1/64 below the live maximum m (4096
    bins; bin b = floor((m - ln L) 64)) with exact fixed-point masses
    floor(exp(ln L - m) 2^S), S = 62 - ceil(log2 N_live), and counts; the kept bins are
-   the fewest from the top that hold the fraction P_thr of the mass
-   (floor(P_thr 2^20) / 2^20, compared exactly) or N_min* points, whichever is reached
-   first (early on the top N_min* points hold less than P_thr of the mass and set the
-   threshold; later the P_thr rule does); N_min = the points kept;
+   the fewest from the top that hold both the fraction P_thr of the mass
+   (floor(P_thr 2^20) / 2^20, compared exactly) and at least N_min* points: N_min* is a
+   floor (while the likelihood is poorly resolved a handful of points carry P_thr of the
+   mass and the top N_min* points set the threshold; once the mass is spread over more
+   points, the P_thr rule does); N_min = the points kept;
 5. refine: V' = V_g N_min / N_live, dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6);
    the new level is floor(log2 n_bins), at least the current one and at most 10, so
    that a cell holds of order sqrt(N_min) points (Eq. nbins_V: cells no smaller than the
@@ -72,7 +73,7 @@ def threshold(lnL, p_thr, n_min_star):
         count[k] += 1
     total = sum(mass)
     p_num = int(math.floor(p_thr * (1 << P_SHIFT)))
-    need = min(n_min_star, int(valid.sum()))
+    need = min(n_min_star, lnL.size)
     run_m = run_c = 0
     b_mass = b_count = None
     for k in range(N_HIST):
@@ -84,10 +85,14 @@ def threshold(lnL, p_thr, n_min_star):
             b_count = k
         if b_mass is not None and b_count is not None:
             break
-    # early iterations keep the top N_min* points while they hold less than P_thr of the
-    # mass; once they hold more, the P_thr rule takes over (fewer points)
-    b_thr = min(b_mass if b_mass is not None else N_HIST - 1, b_count if b_count is not None else N_HIST - 1)
-    kept = valid & (b <= b_thr)
+    # N_min* is a floor: while a few points carry P_thr of the mass (a poorly resolved
+    # likelihood) the top N_min* points are kept; once the mass is spread over more
+    # points the P_thr rule keeps them
+    if b_count is None:
+        # the N_min*-th largest value lies beyond the histogram's range: its bin, exactly
+        b_count = int(np.floor((m - np.sort(lnL)[::-1][need - 1]) * LN_BINS_PER_UNIT))
+    b_thr = max(b_mass if b_mass is not None else N_HIST - 1, b_count)
+    kept = b <= b_thr
     return m, b_thr, kept
 
 
@@ -110,7 +115,8 @@ class AV:
         self.d_min, self.d_max = float(d_min), float(d_max)
         self.level = 0
         self.cells = np.zeros(1, np.uint64)
-        self.V = 1.0
+        self.V = 1.0        # volume of the active cells (the sampling density is 1/V)
+        self.V_thr = 1.0    # estimated volume above the current threshold (V_g of Eq. nbins_V)
         self.live_v = np.zeros((0, 6))
         self.live_lnL = np.zeros(0)
         self.thr = None   # (m, b) of the previous threshold
@@ -146,7 +152,8 @@ class AV:
         m, b_thr, kept = threshold(self.live_lnL, self.p_thr, self.n_min_star)
         n_min = int(kept.sum())
         # 5. refine
-        self.level = next_level(self.level, self.V, n_min, n_live)
+        self.level = next_level(self.level, self.V_thr, n_min, n_live)
+        self.V_thr = self.V_thr * n_min / n_live
         self.live_v = self.live_v[kept]
         self.live_lnL = self.live_lnL[kept]
         self.cells = np.unique(cell_keys(self.live_v, self.level))

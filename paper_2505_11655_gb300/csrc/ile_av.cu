@@ -11,11 +11,17 @@
 //      up to its capacity);
 //   4. threshold: a 1/64-wide ln L histogram below the live maximum m with exact
 //      fixed-point masses floor(exp(ln L - m) 2^S), S = 62 - ceil(log2 N_live); the kept
-//      bins are the fewest from the top holding the fraction P_thr of the mass or
-//      N_min* points, whichever comes first (decided on the host in integers);
-//   5. refine: V' = V N_min / N_live, dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6)
-//      (Eq. nbins_V) rounded down to a power of two, never coarser; the new active cells
-//      are those holding a kept live point (64-bit radix sort of the cell keys, unique).
+//      bins are the fewest from the top holding both the fraction P_thr of the mass and
+//      at least N_min* points (decided on the host in integers).  N_min* is a floor: while
+//      the likelihood is poorly resolved a handful of points carry P_thr of the mass, and
+//      the top N_min* points set the threshold, beyond the histogram's range when need be
+//      (the N_min*-th smallest bin index, from a sort of every live point's bin);
+//   5. refine: with V_thr the estimated volume above the current threshold (1 at the
+//      start; the live points are uniform in that region), V' = V_thr N_min / N_live,
+//      dV = V' / sqrt(N_min), n_bins = (1/dV)^(1/6) (Eq. nbins_V) rounded down to a power
+//      of two, never coarser; V_thr <- V'.  The new active cells are those holding a kept
+//      live point (64-bit radix sort of the cell keys, unique); draws are uniform over
+//      them (volume V >= V_thr).
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -73,13 +79,13 @@ __global__ void av_draw_kernel(const uint64_t *__restrict__ cells, int64_t n_cel
     }
 }
 
-__device__ __forceinline__ bool av_passes(double lnL, bool has_thr, double m, int b)
+__device__ __forceinline__ bool av_passes(double lnL, bool has_thr, double m, int64_t b)
 {
     return !has_thr || floor(__dmul_rn(__dsub_rn(m, lnL), (double)kAvBinsPerUnit)) <= (double)b;
 }
 
 // flags[i] = point i passes; flags[n] = 0 (so that the exclusive scan ends in the total)
-__global__ void av_flags_kernel(const double *__restrict__ lnL, int64_t n, bool has_thr, double m, int b,
+__global__ void av_flags_kernel(const double *__restrict__ lnL, int64_t n, bool has_thr, double m, int64_t b,
                                 uint32_t *__restrict__ flags)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
@@ -88,7 +94,7 @@ __global__ void av_flags_kernel(const double *__restrict__ lnL, int64_t n, bool 
 
 // points that pass go to dst[base + rank] while rank < room
 __global__ void av_scatter_kernel(const double *__restrict__ v, const double *__restrict__ lnL, int64_t n,
-                                  bool has_thr, double m, int b, const uint32_t *__restrict__ rank, int64_t base,
+                                  bool has_thr, double m, int64_t b, const uint32_t *__restrict__ rank, int64_t base,
                                   int64_t room, double *__restrict__ v_dst, double *__restrict__ lnL_dst)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -180,6 +186,21 @@ __global__ void av_hist_final_kernel(const uint64_t *__restrict__ mass_part, con
     count[e] = cc;
 }
 
+// bin index floor((m - ln L) 64) of every live point as a sort key (non-finite values and
+// bins beyond 2^40 - 1 take the largest key)
+constexpr int kAvBinKeyBits = 40;
+__global__ void av_bin_keys_kernel(const double *__restrict__ lnL, int64_t n,
+                                   const unsigned long long *__restrict__ maxbits, uint64_t *__restrict__ keys)
+{
+    const double m = from_order_bits(*maxbits);
+    const uint64_t kmax = (1ull << kAvBinKeyBits) - 1ull;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = lnL[i];
+        const double bf = isfinite(x) ? floor(__dmul_rn(__dsub_rn(m, x), (double)kAvBinsPerUnit)) : (double)kmax;
+        keys[i] = bf < (double)kmax ? (uint64_t)bf : kmax;
+    }
+}
+
 __global__ void av_keys_kernel(const double *__restrict__ v, int64_t n, int level, uint64_t *__restrict__ keys)
 {
     const double side = ldexp(1.0, level);
@@ -251,6 +272,7 @@ int av_restart(rift_ile_t *h)
     a.level = 0;
     a.n_cells = 1;
     a.V = 1.0;
+    a.V_thr = 1.0;
     a.n_live = 0;
     a.has_thr = false;
     a.iter = 0;
@@ -333,16 +355,13 @@ int av_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, double p
     double m;
     std::memcpy(&m, &bits, sizeof(m));
     unsigned __int128 total = 0;
-    int64_t valid = 0;
-    for (int e = 0; e < kAvHist; ++e) {
+    for (int e = 0; e < kAvHist; ++e)
         total += mass[e];
-        valid += count[e];
-    }
     const uint64_t p_num = (uint64_t)std::floor(p_thr * (double)(1u << kAvPShift));
-    const int64_t need = std::min<int64_t>(n_min_star, valid);
+    const int64_t need = std::min<int64_t>(n_min_star, n_live);
     unsigned __int128 run_m = 0;
     int64_t run_c = 0;
-    int b_mass = -1, b_count = -1;
+    int64_t b_mass = -1, b_count = -1;
     for (int e = 0; e < kAvHist && (b_mass < 0 || b_count < 0); ++e) {
         run_m += mass[e];
         run_c += count[e];
@@ -351,19 +370,30 @@ int av_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, double p
         if (b_count < 0 && run_c >= need)
             b_count = e;
     }
-    const int b_thr = std::min(b_mass < 0 ? kAvHist - 1 : b_mass, b_count < 0 ? kAvHist - 1 : b_count);
-    int64_t n_min = 0;
-    for (int e = 0; e <= b_thr; ++e)
-        n_min += count[e];
+    if (b_count < 0 && need > 0) {
+        // the need-th largest value lies beyond the histogram's range: its bin, the need-th
+        // smallest bin index of the live points
+        av_bin_keys_kernel<<<grid1(n_live), 256, 0, st>>>(a.lnL, n_live, a.maxbits, a.keys);
+        int ks = 0;
+        CK(launch_sort64(a.keys, a.keys_tmp, n_live, kAvBinKeyBits, a.sort, st, &ks));
+        uint64_t kb = 0;
+        CK(cudaMemcpyAsync(&kb, a.keys + (need - 1), sizeof(kb), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        b_count = (int64_t)kb;
+        h->launches += 1 + ks;
+    }
+    const int64_t b_thr = std::max<int64_t>(b_mass < 0 ? kAvHist - 1 : b_mass, b_count);
+    av_flags_kernel<<<grid1(n_live + 1), 256, 0, st>>>(a.lnL, n_live, true, m, b_thr, a.flags);
+    int64_t kept = 0;
+    RK(scan_total(h, n_live, &kept));
+    const int64_t n_min = kept;
     // 5. refine
-    const double v_next = a.V * (double)n_min / (double)n_live;
+    const double v_next = a.V_thr * (double)n_min / (double)n_live;
     const double dV = v_next / std::sqrt((double)n_min);
     const double nbins = std::pow(1.0 / dV, 1.0 / 6.0);
     const int cand = nbins >= 1.0 ? (int)std::floor(std::log2(nbins)) : 0;
     const int level = std::max(a.level, std::min(kAvMaxLevel, cand));
-    av_flags_kernel<<<grid1(n_live + 1), 256, 0, st>>>(a.lnL, n_live, true, m, b_thr, a.flags);
-    int64_t kept = 0;
-    RK(scan_total(h, n_live, &kept));
+    a.V_thr = v_next;
     av_scatter_kernel<<<grid1(n_live), 256, 0, st>>>(a.v, a.lnL, n_live, true, m, b_thr, a.flags, 0, kept, a.v2,
                                                      a.lnL2);
     std::swap(a.v, a.v2);

@@ -589,8 +589,8 @@ def test_av_draws_are_uniform_in_the_active_cells(orc):
 
 def test_av_threshold_rule_against_sorted_definition(orc):
     """The histogram threshold keeps every point of the exact sort-based rule (the
-    fewest top points holding P_thr of the mass, or N_min* points) and at most the
-    rest of the 1/64-wide bin where that rule stops."""
+    fewest top points holding P_thr of the mass, and at least N_min* of them) and at
+    most the rest of the 1/64-wide bin where that rule stops."""
     from oracle import av as A
     rng = np.random.default_rng(2)
     for p_thr, nstar in ((0.999, 1000), (0.9, 50), (0.99999, 10)):
@@ -600,7 +600,7 @@ def test_av_threshold_rule_against_sorted_definition(orc):
         w = np.exp(lnL[order] - m)
         frac = np.cumsum(w) / w.sum()
         k_mass = int(np.searchsorted(frac, np.floor(p_thr * 2 ** 20) / 2 ** 20 * (1 - 1e-12))) + 1
-        k = min(k_mass, nstar)
+        k = max(k_mass, nstar)
         exact = np.zeros(lnL.size, bool)
         exact[order[:k]] = True
         assert np.all(kept[exact])
@@ -630,7 +630,7 @@ def test_av_box_target_is_exact(orc):
         inside = np.all((v >= lo) & (v < lo + 0.25), 1)
         return np.where(inside, 0.0, -200.0)
 
-    res = A.run(lnL, 3, 200000, seed=6)
+    res = A.run(lnL, 3, 200000, seed=6, n_min_star=30)   # below the ~49 points the box holds
     its = res["iterations"]
     for r in its[1:]:
         assert r["level"] >= 2 and r["n_cells"] == 64 ** (r["level"] - 2)
@@ -662,6 +662,35 @@ def test_av_refinement_formula_and_nesting(orc):
                 coord = (c >> np.uint64(a.level * d)) & np.uint64((1 << a.level) - 1)
                 parent |= (coord >> np.uint64(shift)) << np.uint64(old_level * d)
             assert set(parent.tolist()) <= old_cells
+
+
+def test_av_sharp_gaussian_keeps_n_min_floor_and_converges(orc):
+    """A 6-D Gaussian with sigma = 0.002 (a posterior volume ~1e-16 of the cube): in
+    iteration 0 the few draws nearest the peak hold P_thr of the mass, so the P_thr rule
+    alone would keep a handful of points.  N_min* is a floor (Sec. IV A: while the
+    likelihood is poorly resolved the top N_min* points are kept), so the live set keeps
+    N_min* points, the region shrinks steadily instead of collapsing onto those few, and
+    the late iterations' ln Z meet the analytic integral within 4 sigma + 1e-3."""
+    from oracle import av as A
+    mu = np.array([0.3125, 0.5625, 0.4375, 0.6875, 0.1875, 0.8125]) + 0.0004
+    sig = 0.002
+
+    def lnL(th):
+        return -np.sum((_v_of_theta(th) - mu) ** 2, 1) / (2 * sig ** 2)
+
+    truth = 3 * math.log(2 * math.pi * sig ** 2)
+    a = A.AV(seed=8, n_min_star=1000)
+    ll0 = lnL(A.AV(seed=8).draw(100000, it=0)[0])
+    # the P_thr rule alone (no floor) keeps a handful of points in iteration 0
+    assert int(A.threshold(ll0, a.p_thr, 1)[2].sum()) < 10
+    its = [a.step(lnL, 100000) for _ in range(16)]
+    assert its[0]["n_min"] >= 1000
+    assert all(r["n_min"] >= 1000 for r in its)
+    assert its[-1]["level"] >= 6
+    for r in its[-3:]:
+        red = A.reduce(r["lnw"])
+        assert abs(red["lnZ"] - truth) < 4 * red["sigma_lnZ"] + 1e-3, (red, truth)
+    assert A.reduce(its[-1]["lnw"])["n_eff"] > 20
 
 
 def test_av_gaussian_target(orc):
