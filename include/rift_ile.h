@@ -58,7 +58,9 @@ extern "C" {
 #define RIFT_QUAD_HALF 1    /* kappa = 1/2 (equivalent to QUARTER with U, V doubled)  */
 
 #define RIFT_FP64 0  /* every step in float64: the plain reference GPU path               */
-#define RIFT_FP32 1  /* float32 bulk arithmetic; float64 delays, log-sum-exp and sums      */
+#define RIFT_FP32 1  /* float32 bulk arithmetic; float64 delays, log-sum-exp and sums; the  */
+                     /* samples with large data and template terms corrected in           */
+                     /* double-float, so every ln L is within 1e-3 of the float64 value   */
 #define RIFT_MIXED 2 /* FP32, then float64 re-evaluation of the samples that carry weight  */
 
 #define RIFT_MAX_DET 4

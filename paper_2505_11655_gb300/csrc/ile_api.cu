@@ -279,16 +279,34 @@ cudaError_t launch_tiled(rift_ile_t *h, const double *theta, int64_t n, double *
                          const double *lnpw, double *lnw)
 {
     const BinTable bt{h->bin_i, h->bin_f, std::log((double)h->prob.n_t)};
-    if (use_tc(h, n))
-        return launch_lnl_tc(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->tile_counter,
-                             h->stream);
-    return launch_lnl_fp32(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->tile_counter,
-                           h->stream);
+    PeakOut po;
+    if (h->fix_on) {
+        po.q = h->aux_q;
+        po.m = h->aux_m;
+        po.j = h->aux_j;
+    }
+    const bool tc = use_tc(h, n);
+    cudaError_t e = tc ? launch_lnl_tc(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err,
+                                       h->tile_counter, h->stream, nullptr, 0, 0, po)
+                       : launch_lnl_fp32(h->prob, bt, theta, h->perm, n, lnL_tmarg, lnL_t, lnpw, lnw, h->err,
+                                         h->tile_counter, h->stream, po);
+    if (e != cudaSuccess || !h->fix_on)
+        return e;
+    // the samples whose float32 terms are large enough for their rounding to reach the
+    // parity bar: template term and peak data term again in double-float
+    int k = 0;
+    e = launch_fix(h->prob, bt, h->fix, theta, n, po, tc ? kPeakBlockTc : 1, h->fix_thr, h->fix_idx, h->fix_count,
+                   lnL_tmarg, lnL_t, lnpw, lnw, h->err, h->stream, &k);
+    h->launches += k;
+    return e;
 }
 
 // RIFT_MIXED: samples whose log-weight is within kMixedMargin of the batch maximum
 // are re-evaluated in float64 (their weight relative to the largest is >= e^-40).
 constexpr double kMixedMargin = 40.0;
+// the float32 modes correct every sample whose template term plus largest data term
+// exceeds this (k_fixup.cu)
+constexpr float kFixThreshold = 600.f;
 
 int refine_batch(rift_ile_t *h, const double *theta, int64_t n, double *lnL_tmarg, const double *lnpw, double *lnw)
 {
@@ -650,6 +668,60 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         release(h);
         return rc;
     }
+    // the large-term correction runs in the float32 modes (not with the distance marginal,
+    // whose per-bin values are no difference of two large terms)
+    h->fix_on = cfg->precision != RIFT_FP64 && !cfg->distance_marg;
+    if (h->fix_on) {
+        // mode-pair tables, grouped by m_a - m_b >= 0 (ordered pairs) and by m_a + m_b (a <= b)
+        int mmax = 0;
+        for (int m = 0; m < M; ++m)
+            mmax = std::max(mmax, std::abs(cfg->lm[2 * m + 1]));
+        const int dmax = 2 * mmax;
+        std::vector<uint16_t> aij, bij;
+        std::vector<int> ast, bst;
+        for (int D = 0; D <= dmax; ++D) {
+            ast.push_back((int)aij.size());
+            for (int a = 0; a < M; ++a)
+                for (int b = 0; b < M; ++b)
+                    if (cfg->lm[2 * a + 1] - cfg->lm[2 * b + 1] == D)
+                        aij.push_back((uint16_t)(a | (b << 8)));
+        }
+        ast.push_back((int)aij.size());
+        for (int S = -dmax; S <= dmax; ++S) {
+            bst.push_back((int)bij.size());
+            for (int a = 0; a < M; ++a)
+                for (int b = a; b < M; ++b)
+                    if (cfg->lm[2 * a + 1] + cfg->lm[2 * b + 1] == S)
+                        bij.push_back((uint16_t)(a | (b << 8)));
+        }
+        bst.push_back((int)bij.size());
+        const int nA = (int)aij.size(), nB = (int)bij.size();
+        if ((rc = dalloc(h, &h->aux_q, (size_t)N)) || (rc = dalloc(h, &h->aux_m, (size_t)N)) ||
+            (rc = dalloc(h, &h->aux_j, (size_t)N)) || (rc = dalloc(h, &h->fix_idx, (size_t)N)) ||
+            (rc = dalloc(h, &h->fix_count, (size_t)4)) || (rc = dalloc(h, &h->fix_aij, (size_t)nA)) ||
+            (rc = dalloc(h, &h->fix_bij, (size_t)nB)) || (rc = dalloc(h, &h->fix_astart, ast.size())) ||
+            (rc = dalloc(h, &h->fix_bstart, bst.size())) || (rc = dalloc(h, &h->fix_ua, (size_t)K * nA)) ||
+            (rc = dalloc(h, &h->fix_vb, (size_t)K * nB)) || (rc = dalloc(h, &h->fix_qdf, (size_t)K * M * cfg->n_q))) {
+            release(h);
+            return rc;
+        }
+        if (cudaMemcpyAsync(h->fix_aij, aij.data(), sizeof(uint16_t) * nA, cudaMemcpyHostToDevice, h->stream) ||
+            cudaMemcpyAsync(h->fix_bij, bij.data(), sizeof(uint16_t) * nB, cudaMemcpyHostToDevice, h->stream) ||
+            cudaMemcpyAsync(h->fix_astart, ast.data(), sizeof(int) * ast.size(), cudaMemcpyHostToDevice, h->stream) ||
+            cudaMemcpyAsync(h->fix_bstart, bst.data(), sizeof(int) * bst.size(), cudaMemcpyHostToDevice, h->stream) ||
+            cudaStreamSynchronize(h->stream)) {
+            cudaGetLastError();
+            release(h);
+            return RIFT_ECUDA;
+        }
+        h->fix = FixTables{h->fix_aij, h->fix_astart, h->fix_bij, h->fix_bstart, h->fix_ua, h->fix_vb, h->fix_qdf,
+                           nA, nB, dmax};
+        // samples with quad32 + |max lin32| above this are corrected: below it the float32
+        // rounding stays under 5e-4 (measured, ~3e-7 per unit of the terms at most)
+        h->fix_thr = kFixThreshold;
+        if (const char *env = std::getenv("RIFT_ILE_FIX_T"))
+            h->fix_thr = (float)std::atof(env);
+    }
     if (cfg->precision == RIFT_MIXED) {
         h->refine_rows = std::min<int64_t>(N, kRefineRows);
         if ((rc = dalloc(h, &h->refine_bins, (size_t)h->refine_rows * cfg->n_t))) {
@@ -696,7 +768,8 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
         else if (env && env[0] == '1')
             h->tc_mode = 1;
         if (prepare_sampler_kernels() != cudaSuccess || prepare_refine_kernels() != cudaSuccess ||
-            prepare_tile_kernels() != cudaSuccess || (h->tc_ok && prepare_tc_kernels() != cudaSuccess)) {
+            prepare_tile_kernels() != cudaSuccess || (h->tc_ok && prepare_tc_kernels() != cudaSuccess) ||
+            prepare_fix_kernels() != cudaSuccess) {
             cudaGetLastError();
             release(h);
             return RIFT_ECUDA;
@@ -743,7 +816,12 @@ int64_t rift_ile_footprint(const rift_ile_config *cfg)
         N * 6 * 8, 3 * N * 8, N * 8, 2 * N * 4, (int64_t)sort_scratch_words(N) * 4, 16, 16,
         K * 2 * groups * kp * 8 * 2, 5 * kRedBlocks * 8, 152 * 12 * B * 8, 8 * (RIFT_MAX_ITER + 1) * 8, 3 * 8 * 8,
         N * 4, 16, 6 * B * 8, 6 * (B + 1) * 8, 6 * B * 8, 16, (int64_t)kSelectWords * 4,
-        cfg->precision == RIFT_MIXED ? std::min<int64_t>(N, kRefineRows) * nt * 8 : 0};
+        cfg->precision == RIFT_MIXED ? std::min<int64_t>(N, kRefineRows) * nt * 8 : 0,
+        // large-term correction: per-sample side outputs and list, pair tables, double-float
+        // copies of U, V (at most M^2 pairs each) and Q
+        cfg->precision != RIFT_FP64 && !cfg->distance_marg ? 4 * N * 4 + 16 + 4 * M * M + 8 * 64 +
+                                                                  2 * K * M * M * 16 + K * M * nq * 16
+                                                            : 0};
     int64_t total = 0;
     for (int64_t b : sizes)
         total += b + 16;
@@ -886,6 +964,10 @@ int install_overlaps(rift_ile_t *h)
         CK(launch_prep_tc(h->Q64, K, M, nq, h->prob.tc_groups, h->qmax_bits, h->Qtc, h->stream));
         CK(launch_prep_tt(h->U64, h->V64, K, M, h->Ttc, h->tt_exp, h->stream));
         h->launches += 3;
+    }
+    if (h->fix_on) {
+        CK(launch_fix_prep(h->prob, h->fix, h->fix_ua, h->fix_vb, h->fix_qdf, h->stream));
+        h->launches += 1;
     }
     int rc = sync_and_err(h);
     h->have_overlaps = (rc == RIFT_OK);

@@ -57,6 +57,18 @@ struct rift_ile {
     uint32_t *sel_idx = nullptr, *sel_count = nullptr;   // RIFT_MIXED re-evaluation list
     double *refine_bins = nullptr;   // RIFT_MIXED: float32 per-bin ln L of the first selected samples
     int64_t refine_rows = 0;
+    // large-term correction of the float32 path (k_fixup.cu): the kernels' per-sample
+    // template term, largest data term and its bin block; the list of corrected samples;
+    // mode-pair tables and double-float copies of U, V, Q
+    float *aux_q = nullptr, *aux_m = nullptr;
+    int *aux_j = nullptr;
+    uint32_t *fix_idx = nullptr, *fix_count = nullptr;
+    uint16_t *fix_aij = nullptr, *fix_bij = nullptr;
+    int *fix_astart = nullptr, *fix_bstart = nullptr;
+    float4 *fix_ua = nullptr, *fix_vb = nullptr, *fix_qdf = nullptr;
+    rift::FixTables fix{};
+    bool fix_on = false;
+    float fix_thr = 0.f;
     double *P = nullptr, *C = nullptr, *Lg = nullptr;
     int *err = nullptr;
     uint32_t *iter_dev = nullptr;   // sampler iteration counter read by the draw kernel
@@ -82,10 +94,11 @@ struct rift_ile {
         int level = 0;               // 2^level cells per side
         int64_t n_cells = 1;
         double V = 1.0;              // volume of the active cells
+        double V_thr = 1.0;          // estimated volume above the current threshold
         int64_t n_live = 0;
         bool has_thr = false;        // threshold (m, b): keep floor((m - ln L) 64) <= b
         double m = 0.0;
-        int b = 0;
+        int64_t b = 0;
         uint32_t iter = 0;
         double *v = nullptr, *lnL = nullptr, *v2 = nullptr, *lnL2 = nullptr;   // live set, ping-pong
         double *v_fresh = nullptr;                                               // [max_samples][6]

@@ -66,6 +66,7 @@ cudaError_t prepare_sampler_kernels();
 cudaError_t prepare_refine_kernels();
 cudaError_t prepare_tile_kernels();
 cudaError_t prepare_tc_kernels();
+cudaError_t prepare_fix_kernels();
 
 // Per-bin split of j * beta (beta = bin spacing x fs): j*beta = bin_i[j] + bin_f[j], 0 <= bin_f < 1.
 struct BinTable {
@@ -79,11 +80,44 @@ struct BinTable {
 cudaError_t launch_lnl_fp64(const Problem &P, const double *theta, int64_t n, double *lnL_tmarg, double *lnL_t,
                             const double *lnpw, double *lnw, int *err, cudaStream_t st);
 
+// Per-sample side outputs of the float32 likelihood kernels (all null, or all set), read
+// by the large-term correction: q[i] the float32 template term, m[i] the largest float32
+// data term over the time bins, j[i] the first bin of a block of consecutive bins that
+// holds the bin of that largest value (the block length is a property of the kernel:
+// kPeakBlockTc for the tensor-core tiles, 1 for the CUDA-core tiles).
+struct PeakOut {
+    float *q = nullptr;
+    float *m = nullptr;
+    int *j = nullptr;
+};
+constexpr int kPeakBlockTc = 4;
+
+// Large-term correction of the float32 path (k_fixup.cu).  Mode-pair tables (host-built
+// from the mode list) and double-float copies of U, V, Q (built on the device whenever the
+// overlaps change).  dmax = 2 max|m|.
+struct FixTables {
+    const uint16_t *a_ij;   // ordered pairs (a | b << 8) with m_a - m_b = D >= 0, grouped by D
+    const int *a_start;     // [dmax + 2] group boundaries
+    const uint16_t *b_ij;   // pairs a <= b grouped by S = m_a + m_b
+    const int *b_start;     // [2 dmax + 2] group boundaries, by S + dmax
+    const float4 *ua;       // [K][nA] U_k,ab (re.hi, re.lo, im.hi, im.lo)
+    const float4 *vb;       // [K][nB] (2 - delta_ab) V_k,ab, same layout
+    const float4 *qdf;      // [K][M][n_q] Q, same layout
+    int nA, nB, dmax;
+};
+cudaError_t launch_fix_prep(const Problem &P, FixTables T, float4 *ua, float4 *vb, float4 *qdf, cudaStream_t st);
+// Lists the samples with po.q + |po.m| > thr (idx, *count; count reset here) and corrects
+// their lnL_tmarg (and lnw = lnL_tmarg + lnpw, and the rows of lnL_t, when given) in place.
+// blen: the block length of po.j.  *launched: kernels enqueued.
+cudaError_t launch_fix(const Problem &P, BinTable bt, FixTables T, const double *theta, int64_t n, PeakOut po,
+                       int blen, float thr, uint32_t *idx, uint32_t *count, double *lnL_tmarg, double *lnL_t,
+                       const double *lnpw, double *lnw, int *err, cudaStream_t st, int *launched);
+
 // Float32 tiled path.  perm[n] lists sample indices in sky-cell order; outputs are
 // written at the original index.  tile_counter: one device int (reset by the launcher).
 cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                             double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
-                            int *tile_counter, cudaStream_t st);
+                            int *tile_counter, cudaStream_t st, PeakOut po = PeakOut());
 size_t lnl_fp32_smem_bytes(const Problem &P);
 
 // Tensor-core variant of the float32 tiled path (tiles of 128 samples, tcgen05 MMA).
@@ -98,7 +132,7 @@ cudaError_t launch_prep_tt(const double2 *U64, const double2 *V64, int K, int M,
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
                           int *tile_counter, cudaStream_t st, const uint32_t *n_dev = nullptr,
-                          int lnl_t_compact = 0, int64_t n_theta = 0);
+                          int lnl_t_compact = 0, int64_t n_theta = 0, PeakOut po = PeakOut());
 // Builds the float16 hi/lo copy of Q for the tensor-core path.
 cudaError_t launch_prep_tc(const double2 *Q64, int K, int M, int n_q, int groups, unsigned int *qmax_bits,
                            __half *Qtc, cudaStream_t st);

@@ -81,7 +81,7 @@ template <bool kDbuf>
 __global__ void __launch_bounds__(kTThreads, 1)
 lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const uint32_t *__restrict__ perm, int64_t n,
                 double *__restrict__ lnL_tmarg, double *__restrict__ lnL_t, const double *__restrict__ lnpw,
-                double *__restrict__ lnw, int *err, int *tile_counter)
+                double *__restrict__ lnw, int *err, int *tile_counter, PeakOut po)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = P.K, M = P.M, R2 = 2 * M, NT = P.n_t;
@@ -282,11 +282,15 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
             stage(0, Qb[0]);
         }
 
+        // running log-sum-exp per sample over the bins of the data term alone (the template
+        // term enters once, in the epilogue) and the bin of its maximum
         float run_mx[8], run_sum[8];
+        int run_j[8];
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
             run_mx[p] = -INFINITY;
             run_sum[p] = 0.f;
+            run_j[p] = 0;
         }
         float lin[8][kBinsPerLane];
 #pragma unroll
@@ -442,11 +446,9 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                         }
                     } else {
 #pragma unroll
-                        for (int q = 0; q < kBinsPerLane; ++q) {
-                            lin[p][q] -= qd;
+                        for (int q = 0; q < kBinsPerLane; ++q)
                             if (lane + 32 * q < J)
                                 cmx[p] = fmaxf(cmx[p], lin[p][q]);
-                        }
                     }
                 }
                 if (lnL_t) {
@@ -456,7 +458,8 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
 #pragma unroll
                         for (int q = 0; q < kBinsPerLane; ++q)
                             if (lane + 32 * q < J && g != 0xffffffffu)
-                                lnL_t[(int64_t)g * NT + j0 + lane + 32 * q] = (double)lin[p][q];
+                                lnL_t[(int64_t)g * NT + j0 + lane + 32 * q] =
+                                    P.dist_marg ? (double)lin[p][q] : (double)lin[p][q] - (double)qds[warp + 8 * p];
                     }
                 }
 #pragma unroll
@@ -466,6 +469,15 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
                         cmx[p] = fmaxf(cmx[p], __shfl_xor_sync(0xffffffffu, cmx[p], o));
 #pragma unroll
                 for (int p = 0; p < 8; ++p) {
+                    if (cmx[p] > run_mx[p]) {
+                        // a new running maximum (warp-uniform): its bin, the lowest holding it
+                        int jc = INT_MAX;
+#pragma unroll
+                        for (int q = 0; q < kBinsPerLane; ++q)
+                            if (lane + 32 * q < J && lin[p][q] == cmx[p])
+                                jc = min(jc, j0 + lane + 32 * q);
+                        run_j[p] = __reduce_min_sync(0xffffffffu, jc);
+                    }
                     cmx[p] = fmaxf(run_mx[p], cmx[p]);
                     cs[p] = 0.f;
 #pragma unroll
@@ -490,17 +502,27 @@ lnl_tile_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const 
         // ---------------- epilogue: lane p writes sample warp + 8 p
         if (lane < 8) {
             float mxv = run_mx[0], smv = run_sum[0];
+            int jv = run_j[0];
 #pragma unroll
             for (int p = 1; p < 8; ++p)
                 if (lane == p) {
                     mxv = run_mx[p];
                     smv = run_sum[p];
+                    jv = run_j[p];
                 }
             const int s = warp + 8 * lane;
             const uint32_t g = gid[s];
             if (g != 0xffffffffu) {
-                // float32 like the partials (float64 is slow on this part); smv >= 1
-                const double r = (double)mxv + (double)__logf(smv) - bt.ln_nt;
+                // the log-sum-exp in float32 like the partials (smv >= 1); the template term
+                // subtracted in float64, so that the difference of two large terms is not
+                // rounded to float32
+                const double r =
+                    (double)mxv + (double)__logf(smv) - (P.dist_marg ? 0.0 : (double)qds[s]) - bt.ln_nt;
+                if (!P.dist_marg && po.q) {
+                    po.q[g] = qds[s];
+                    po.m[g] = mxv;
+                    po.j[g] = jv;
+                }
                 if (!isfinite(r))
                     atomicOr(err, kErrNonFinite);
                 lnL_tmarg[g] = r;
@@ -522,7 +544,7 @@ size_t lnl_fp32_smem_bytes(const Problem &P)
 
 cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                             double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
-                            int *tile_counter, cudaStream_t st)
+                            int *tile_counter, cudaStream_t st, PeakOut po)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -543,7 +565,7 @@ cudaError_t launch_lnl_fp32(const Problem &P, BinTable bt, const double *theta, 
         return e;
     const int64_t tiles = (n + kTS - 1) / kTS;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    kern<<<grid, kTThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err, tile_counter);
+    kern<<<grid, kTThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err, tile_counter, po);
     return cudaGetLastError();
 }
 

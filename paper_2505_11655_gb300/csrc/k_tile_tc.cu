@@ -96,7 +96,7 @@ __host__ __device__ inline TcLayout tc_layout(int K, int M, int n_t)
     L.inv = o;  o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.qsc = o;  o = tc_al(o + (size_t)K * kTcS * 4, 16);
     L.gid = o;  o = tc_al(o + (size_t)kTcS * 4, 16);
-    L.lse = o;  o = tc_al(o + (size_t)2 * kTcQ * kTcS * 4, 16);
+    L.lse = o;  o = tc_al(o + (size_t)(2 * kTcQ + 2) * kTcS * 4, 16);
     L.bar = o;  o = tc_al(o + 8 * 8, 16);
     L.tptr = o; o = tc_al(o + 16, 16);
     L.end = o;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const uint32_t *__restrict__ perm, int64_t n,
               double *__restrict__ lnL_tmarg, double *__restrict__ lnL_t, const double *__restrict__ lnpw,
               double *__restrict__ lnw, int *err, int *tile_counter, const uint32_t *__restrict__ n_dev,
-              int64_t n_theta, int lnl_t_compact)
+              int64_t n_theta, int lnl_t_compact, PeakOut po)
 {
     // n entries of perm (fewer when a device count is given, read where needed so that no
     // register holds it); every sample index in perm is below n_theta
@@ -284,6 +284,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     float2 *pe = reinterpret_cast<float2 *>(sm + L.pe);        // [kMaxL + 1][kTcS] exp(-i j phi)
     float2 *fx = reinterpret_cast<float2 *>(sm + L.fx);        // [K][kTcS] (D_ref/D) F_k
     float *lse = reinterpret_cast<float *>(sm + L.lse);         // [2][kTcQ][kTcS] running max, sum
+    // [kTcS] per sample: the largest data term over its bins (order-preserving bits, high
+    // word) and the first bin of the block of bins holding it (NT - bin, low word, so that
+    // the lowest bin wins among equals), by one 64-bit shared atomic max per chunk and thread
+    unsigned long long *peak = reinterpret_cast<unsigned long long *>(lse + 2 * kTcQ * kTcS);
     float *qsum = lse;                                          // [kTcQ][kTcS] template term partials
     float2 *Ys = reinterpret_cast<float2 *>(Rs);               // [M][kTcS] -2Y_lm(iota, -phi)
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
@@ -378,6 +382,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             uint32_t g = si < n_use ? perm[si] : 0xffffffffu;
             const bool valid = (int64_t)g < n_theta;
             gid[tid] = valid ? g : 0xffffffffu;
+            peak[tid] = 0ull;
             double th[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 1.0};
             if (valid)
                 for (int d = 0; d < 6; ++d)
@@ -829,13 +834,28 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                                     cmx = fmaxf(cmx, lin[i]);
                             }
                         } else {
-                            // lin holds the overlap term; ln L = lin - gqd (max commutes with
-                            // the subtraction)
+                            // lin holds the data term; ln L = lin - gqd, the template term
+                            // subtracted once per sample in the epilogue (in float64)
+                            // (the maximum by blocks of kPeakBlockTc bins, the same number of
+                            // operations, so that the block holding it is known)
+                            float qm[kTcBPT / kPeakBlockTc];
 #pragma unroll
-                            for (int i = 0; i < kTcBPT; ++i)
-                                if (i < jn)
-                                    cmx = fmaxf(cmx, lin[i]);
-                            cmx -= gqd;
+                            for (int a = 0; a < kTcBPT / kPeakBlockTc; ++a) {
+                                qm[a] = -INFINITY;
+#pragma unroll
+                                for (int i = kPeakBlockTc * a; i < kPeakBlockTc * (a + 1); ++i)
+                                    if (i < jn)
+                                        qm[a] = fmaxf(qm[a], lin[i]);
+                            }
+                            const float m01 = fmaxf(qm[0], qm[1]), m23 = fmaxf(qm[2], qm[3]);
+                            cmx = fmaxf(m01, m23);
+                            if (jn > 0 && in_grp) {
+                                const int a = m01 >= m23 ? (qm[0] >= qm[1] ? 0 : 1) : (qm[2] >= qm[3] ? 2 : 3);
+                                const uint32_t ob = __float_as_uint(cmx) ^
+                                                    ((uint32_t)((int)__float_as_uint(cmx) >> 31) | 0x80000000u);
+                                atomicMax(peak + gs,
+                                          ((unsigned long long)ob << 32) | (unsigned)(NT - jb - kPeakBlockTc * a));
+                            }
                         }
                         if (lnL_t && gok && in_grp) {
                             for (int i = 0; i < jn; ++i)
@@ -843,7 +863,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                                 for (int u = 0; u < kTcBPT; ++u)
                                     if (u == i)
                                         lnL_t[(lnl_t_compact ? (int64_t)tile_s * kTcS + gs : (int64_t)gid[gs]) * NT + jb + i] =
-                                            (double)(kDM ? lin[u] : lin[u] - gqd);
+                                            kDM ? (double)lin[u] : (double)lin[u] - (double)gqd;
                         }
                         if (jn > 0 && in_grp) {
                             const float nm = fmaxf(run_mx, cmx);
@@ -854,9 +874,9 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                                     if (i < jn)
                                         cs += __expf(lin[i] - nm);
                             } else {
-                                // exp(lin - gqd - nm) = 2^(lin log2(e) - (gqd + nm) log2(e)), two bins
-                                // per packed operation
-                                const float off = (gqd + nm) * kLog2e;
+                                // exp(lin - nm) = 2^(lin log2(e) - nm log2(e)), two bins per packed
+                                // operation
+                                const float off = nm * kLog2e;
                                 float2 cs2 = make_float2(0.f, 0.f);
 #pragma unroll
                                 for (int i = 0; i < kTcBPT; i += 2) {
@@ -899,8 +919,10 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
         }
         __syncthreads();
         if (tid < kTcS && gid[tid] != 0xffffffffu) {
-            // float32 like the partials (float64 is slow on this part): the largest partial
-            // contributes a sum >= 1, so the logarithm is well conditioned
+            // the partials combine in float32 (float64 is slow on this part): the largest
+            // partial contributes a sum >= 1, so the logarithm is well conditioned.  The
+            // template term (thread tid holds sample tid's) is subtracted in float64, so that
+            // the difference of two large terms is not rounded to float32.
             float mx = -INFINITY;
             for (int h = 0; h < kTcQ; ++h)
                 mx = fmaxf(mx, lse[h * kTcS + tid]);
@@ -911,7 +933,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     sum += lse[(kTcQ + h) * kTcS + tid] * __expf(m - mx);
             }
             const uint32_t g = gid[tid];
-            const double r = (double)mx + (double)__logf(sum) - bt.ln_nt;
+            const double r = (double)mx + (double)__logf(sum) - (kDM ? 0.0 : (double)gqd) - bt.ln_nt;
+            if (!kDM && po.q) {
+                po.q[g] = gqd;
+                po.m[g] = mx;
+                po.j[g] = NT - (int)(uint32_t)peak[tid];
+            }
             if (!isfinite(r))
                 atomicOr(err, kErrNonFinite);
             lnL_tmarg[g] = r;
@@ -937,7 +964,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
 cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, const uint32_t *perm, int64_t n,
                           double *lnL_tmarg, double *lnL_t, const double *lnpw, double *lnw, int *err,
                           int *tile_counter, cudaStream_t st, const uint32_t *n_dev, int lnl_t_compact,
-                          int64_t n_theta)
+                          int64_t n_theta, PeakOut po)
 {
     if (n_theta <= 0)
         n_theta = n;
@@ -960,7 +987,7 @@ cudaError_t launch_lnl_tc(const Problem &P, BinTable bt, const double *theta, co
     const int64_t tiles = (n + kTcS - 1) / kTcS;
     const int grid = (int)(tiles < sms ? tiles : sms);
     kern<<<grid, kTcThreads, smem, st>>>(P, bt, theta, perm, n, lnL_tmarg, lnL_t, lnpw, lnw, err, tile_counter,
-                                          n_dev, n_theta, lnl_t_compact);
+                                          n_dev, n_theta, lnl_t_compact, po);
     return cudaGetLastError();
 }
 

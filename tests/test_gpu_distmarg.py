@@ -34,11 +34,12 @@ def oracle_marg(orc, p, th):
     return ll, bins, quad * (p.d_ref / p.d_min) ** 2   # largest template term over the prior range
 
 
-def close32(got, exp, quad):
+def close32(got, exp, quad=None):
+    """Float32 bar: |d ln L| <= 1e-3 on every sample.  With the distance marginal the
+    per-bin value is no difference of two large terms (the integrand peaks where the data
+    and template terms balance), so the float32 path meets it without correction."""
     d = np.abs(got - exp)
-    near = exp >= exp.max() - 100.0
-    assert np.max(d[near]) <= 1e-3, np.max(d[near])
-    assert np.all(d <= 1e-3 + 4e-7 * (np.abs(exp) + 2.0 * quad)), np.max(d)
+    assert np.max(d) <= 1e-3, (np.max(d), int(np.argmax(d)))
 
 
 @pytest.mark.parametrize("problem", ["plain", "large"])

@@ -3,8 +3,7 @@ same seeded inputs.
 
 Tolerances:
   * RIFT_FP64 path: 1e-9 relative on every ln L value and on ln Z.
-  * RIFT_FP32 path: |d ln Z| <= 1e-3; |d ln L| <= 1e-3 on samples within 100 of the
-    batch maximum, 1e-3 + 3e-7 |ln L| on the rest (float32 rounding floor), at SNR 20.
+  * RIFT_FP32 path: |d ln L| <= 1e-3 on every sample (and every time bin), |d ln Z| <= 1e-3.
   * Integer and index work (sample streams, histogram bins) is compared exactly.
 """
 import math
@@ -36,23 +35,15 @@ def rel(a, b):
     return np.max(np.abs(a - b) / np.maximum(1.0, np.abs(b)))
 
 
-def fp32_floor(exp, quad):
-    """Float32 rounding floor of ln L = lin - quad: the data and template terms
-    are each as large as |ln L| + quad, and every float32 operand and product
-    carries ~6e-8 relative error."""
-    return 1e-3 + 4e-7 * (np.abs(exp) + 2.0 * np.abs(quad))
+FP32_TOL = 1e-3   # |d ln L| on every sample, and |d ln Z|, for the float32 path
 
 
-def assert_fp32_close(got, exp, quad):
-    """Float32 bar: |d ln L| <= 1e-3 on every sample within 100 of the batch's
-    largest ln L (all samples that can carry weight); elsewhere the float32
-    rounding floor of terms of the size of the template term (up to ~1e4 for
-    the nearest prior distances)."""
+def assert_fp32_close(got, exp, quad=None):
+    """Float32 bar: |d ln L| <= 1e-3 on every sample.  (quad, the template term, is
+    accepted for the callers' convenience; the bar does not depend on it.)"""
     got, exp = np.asarray(got), np.asarray(exp)
     d = np.abs(got - exp)
-    near = exp >= np.max(exp) - 100.0
-    assert np.max(d[near]) <= 1e-3, np.max(d[near])
-    assert np.all(d <= fp32_floor(exp, quad)), np.max(d - fp32_floor(exp, quad))
+    assert np.max(d) <= FP32_TOL, (np.max(d), int(np.argmax(d)))
 
 
 def olnL(orc, p, th):
@@ -162,7 +153,7 @@ def test_fp32_bins_match(G, orc):
     with G.ILE(p, precision=G.RIFT_FP32, max_samples=4096) as s:
         got, gbins = s.eval(th, want_bins=True)
     exp, ebins, quad = orc.lnL(p, th, want_bins=True)
-    assert np.all(np.abs(gbins - ebins) <= fp32_floor(ebins, quad[:, None]))
+    assert np.max(np.abs(gbins - ebins)) <= FP32_TOL, np.max(np.abs(gbins - ebins))
     assert_fp32_close(got, exp, quad)
 
 
@@ -282,14 +273,12 @@ def test_tc_path_bins_and_cuda_core_agree(G, orc, monkeypatch):
     with G.ILE(p, precision=G.RIFT_FP32, max_samples=1024) as s:
         g_cc, b_cc = s.eval(th, want_bins=True)
     exp, ebins, quad = orc.lnL(p, th, want_bins=True)
-    assert np.all(np.abs(b_tc - ebins) <= fp32_floor(ebins, quad[:, None]))
+    assert np.max(np.abs(b_tc - ebins)) <= FP32_TOL
     assert_fp32_close(g_tc, exp, quad)
+    assert_fp32_close(g_cc, exp, quad)
     # two float32 evaluations, each within the float32 bar of the oracle, agree within the
     # sum of their bars
-    d = np.abs(g_tc - g_cc)
-    near = exp >= np.max(exp) - 100.0
-    assert np.max(d[near]) <= 2e-3, np.max(d[near])
-    assert np.all(d <= 2.0 * fp32_floor(exp, quad)), np.max(d - 2.0 * fp32_floor(exp, quad))
+    assert np.max(np.abs(g_tc - g_cc)) <= 2 * FP32_TOL
 
 
 def test_tc_path_plain_config_and_spread_sky(G, orc, monkeypatch):
@@ -332,7 +321,7 @@ def test_mixed_precision_high_snr(G, orc):
     top = exp >= exp.max() - 40.0
     assert top.sum() >= 50
     assert np.max(np.abs(got[top] - exp[top])) <= 1e-3
-    assert np.all(np.abs(got - exp) <= fp32_floor(exp, quad))
+    assert_fp32_close(got, exp)
     # the float32 path alone is measurably worse on the same samples
     assert np.max(np.abs(got32[top] - exp[top])) > np.max(np.abs(got[top] - exp[top]))
 
@@ -372,19 +361,23 @@ def test_mixed_precision_adapt_lnZ(G, orc):
 # ------------------------------------------------------------------------------ full size
 
 @pytest.mark.slow
-def test_full_size_single_large_sampled(G, orc):
+def test_full_size_single_large_every_sample(G, orc):
     """1e6 samples, 3 detectors, 21 modes, 1001 bins, the benchmark's launch
-    configuration: 4000 sampled outputs against the oracle one by one, and
-    ln Z against the reduction of the device's own per-sample values."""
+    configuration (an adapted sampling prior, then one batch): every one of the 1e6
+    ln L values against the oracle's, and ln Z against the oracle's reduction of the
+    oracle's own ln L on the device's sample stream."""
     p = S.single_large_problem()
     n = 1_000_000
     with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=7) as s:
+        s.adapt(1, n)
         r = s.marginalize(n)
         th, lr, ll, lw = s.last_batch(n)
-    idx = np.random.default_rng(0).choice(n, 4000, replace=False)
-    assert_fp32_close(ll[idx], *olnL(orc, p, th[idx]))
-    red = orc.reduce(lw)
-    assert abs(r["lnZ"] - red["lnZ"]) <= 1e-9 * max(1, abs(red["lnZ"]))
+    oll = orc.lnL(p, th)
+    d = np.abs(ll - oll)
+    print(f"full size: max |d ln L| over {n} samples = {d.max():.3e}")
+    assert np.max(d) <= FP32_TOL, (np.max(d), int(np.argmax(d)))
+    red = orc.reduce(oll + lr)
+    assert abs(r["lnZ"] - red["lnZ"]) <= FP32_TOL, (r["lnZ"], red["lnZ"])
     assert r["n_total"] == n
 
 

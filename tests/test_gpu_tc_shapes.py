@@ -28,8 +28,7 @@ def orc(oracle_lib):
     return oracle_lib
 
 
-def fp32_floor(exp, quad):
-    return 1e-3 + 4e-7 * (np.abs(exp) + 2.0 * np.abs(quad))
+FP32_TOL = 1e-3   # |d ln L| on every sample for the float32 path
 
 
 def clustered(n, seed, center=(1.0, 0.3), width=0.06):
@@ -70,11 +69,9 @@ def test_tc_kernel_shapes_match_oracle(G, orc, monkeypatch, shape):
         with G.ILE(p, precision=G.RIFT_FP32, max_samples=2048) as s:
             got[tc] = s.eval(th)
             assert s.plan()[0] == (G.RIFT_KERNEL_TENSOR if tc == "1" else G.RIFT_KERNEL_CUDA_CORE)
-    for g in got.values():
+    for tc, g in got.items():
         d = np.abs(g - exp)
-        near = exp >= exp.max() - 100.0
-        assert np.max(d[near]) <= 1e-3, np.max(d[near])
-        assert np.all(d <= fp32_floor(exp, quad)), np.max(d - fp32_floor(exp, quad))
+        assert np.max(d) <= FP32_TOL, (tc, np.max(d))
 
 
 def test_tc_kernel_four_detectors_adapt_matches_fp64_path(G, monkeypatch):
