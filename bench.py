@@ -8,7 +8,11 @@ A step is one full pass of the hot path: draw 1e6 samples from the adaptive
 sampling prior -> sort by sky cell -> time-marginalised ln L (float32 bulk,
 float64 delays and sums) -> ln Z / n_eff / n_ESS reduction -> histogram
 adaptation.  Metric: ln L sample-evaluations per second (each evaluation
-includes the full 1001-bin time marginalisation).
+includes the full 1001-bin time marginalisation).  The same line carries the rest of
+the metric: a "batched" block (512 uneven solves as one CUDA graph: solves/s) and a
+"serving" block (a Poisson stream of solves: solves/s, p50/p99 latency), each with a
+fixed subset of its solves also run one at a time through the plain FP64 GPU path (the
+same requests on both arms) and the |d ln Z| of the served results against it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -50,11 +54,11 @@ import ile_synth as S  # noqa: E402
 METRIC = "ILE lnL sample-evals/s"
 UNIT = "sample-evals/s"
 N_SAMPLES = 1_000_000
-FP32_LANES_PER_SM = 128
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
-PROFILE = os.path.join(ROOT, "profiles", "lnl_tc_single_large.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", "k_tile_tc.cu")
+# DRAM bytes per 1e6-sample likelihood stage (the tensor-core kernel and the large-term
+# correction) from the ncu capture summarised in profiles/lnl_tc_single_large.md, keyed by
+# the SHA-256 of the two kernels' sources; traffic is reported as null for any other source.
+TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", f) for f in ("k_tile_tc.cu", "k_fixup.cu")]
+TRAFFIC_BY_SOURCE = {}
 
 
 def workload_config(prob, n):
@@ -75,22 +79,38 @@ def flops_per_sample(prob):
     return K * (4 * M * tw + 3 * nt) + 8 * K * M * M + 3 * nt
 
 
-def fp32_peak_tflops():
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+def kernel_traffic():
+    """DRAM bytes of one 1e6-sample likelihood stage from the recorded ncu capture, or None
+    when the kernels' sources differ from the captured ones."""
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        h.update(open(f, "rb").read())
+    return TRAFFIC_BY_SOURCE.get(h.hexdigest())
 
 
-def profile_traffic():
-    """dram bytes per launch of the tiled likelihood kernel from the committed ncu
-    summary, or None if the kernel source changed since it was captured."""
-    if not os.path.exists(PROFILE):
-        return None
-    text = open(PROFILE).read()
-    m = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"k_lnl_sha256:\s*([0-9a-f]{64})", text)
-    if not m or not h:
-        return None
-    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
-    return float(m.group(1)) if cur == h.group(1) else None
+def measured_peaks():
+    """The measured HBM copy and bf16 GEMM rates of the GB300s."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "of measured"
+        except (OSError, ValueError):
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+def unit_peaks(G):
+    """This device's float32 FMA and tcgen05 kind::f16 rates, measured by the library's own
+    microbenchmarks (rift_ile_peak_rate) before the timed region."""
+    out = {}
+    for name, what in (("fp32_fma_tflops", G.RIFT_PEAK_FP32_FMA), ("tc_f16_n128_tflops", G.RIFT_PEAK_TC_F16_N128),
+                       ("tc_f16_n256_tflops", G.RIFT_PEAK_TC_F16_N256)):
+        try:
+            out[name] = G.rift_ile_peak_rate(what)
+        except Exception as e:   # a failed measurement is reported, not hidden
+            out[name] = None
+            out[name + "_error"] = str(e)
+    return out
 
 
 class Clocks:
@@ -366,32 +386,50 @@ def run_ours(args, rank, world, local_rank):
     fps = flops_per_sample(prob)
     lnl_avg = statistics.mean(lnl_ms)
     achieved = fps * n / (lnl_avg / 1e3) / 1e12
-    peak = fp32_peak_tflops()
+    mp, basis = measured_peaks()
+    peak = float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
     plan = ile.plan()
     kernel = _lnl_kernel_name(G, plan)
-    traffic = profile_traffic() if plan[0] == G.RIFT_KERNEL_TENSOR else None
+    traffic = kernel_traffic() if plan[0] == G.RIFT_KERNEL_TENSOR else None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(prob, n),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": kernel, "samples_per_cell": plan[1], "kernel_ms": lnl_avg,
-                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (unit counts x max clock)",
-                     "flops_per_sample": fps,
-                     "note": "algorithmic flops of the method against the FP32 FMA peak; the mode contraction "
-                             "(95% of them) runs on tcgen05 as a float16 hi/lo split, so this fraction is not a "
-                             "unit's utilisation: in the ncu capture no unit is saturated (shared-memory "
-                             "wavefronts ~46% of the LSU pipe's bandwidth, issue 57%, tensor pipe 18%); the "
-                             "per-step drain of the accumulators into shared memory and the per-bin gather "
-                             "bound the kernel"},
+                     "kernel": kernel + " + large-term correction (the likelihood stage)",
+                     "samples_per_cell": plan[1], "kernel_ms": lnl_avg, "flops_per_sample": fps,
+                     "peak_basis": f"dense 16-bit tensor rate {basis} (bf16 GEMM sustained, MEASURED_PEAKS.json; "
+                                   "f16 has the same nominal rate), the likelihood stage being timed inside a "
+                                   "long step",
+                     "note": "achieved = algorithmic flops of the method (the mode contraction, 95% of them, is "
+                             "a dense contraction the kernel runs on tcgen05 as a float16 hi/lo split) / the "
+                             "likelihood stage's CUDA-event time.  The stage is bound by the per-step drain of "
+                             "the accumulators into shared memory and the per-bin gather, not by the tensor "
+                             "pipe (profiles/lnl_tc_single_large.md)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clocks,
         "lnZ_last": r["lnZ"], "n_eff_last": r["n_eff"], "precompute": pre, "distance_marg": dm,
     }
+    if not args.quick:
+        up = unit_peaks(G)
+        out["roofline"]["unit_peaks_measured"] = up
+        if up.get("fp32_fma_tflops"):
+            out["roofline"]["algorithmic_vs_fp32_fma"] = achieved / up["fp32_fma_tflops"]
+        if up.get("tc_f16_n128_tflops"):
+            out["roofline"]["frac_vs_tc_f16_n128_measured"] = achieved / up["tc_f16_n128_tflops"]
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         out["cpu_baseline"] = cpu_baseline(prob)
     ile.close()
+    if not (args.quick or args.no_workloads):
+        # the rest of the metric: solves/s of the batched workload and solves/s with p50/p99
+        # latency of the serving stream, each against the plain FP64 GPU path measured
+        # directly on a fixed subset of the same solves
+        clk2 = Clocks(gpu_id)
+        clk2.start()
+        out["batched"] = measure_batched(torch, G, rank, args.points, 2, 5)
+        out["serving"] = measure_serving(torch, G, rank, args.requests)
+        out["workload_clocks"] = clk2.stop()
     if rank == 0:
         emit(out)
 
@@ -446,10 +484,24 @@ def _clock_monitor(torch, local_rank):
     return Clocks(gpu_id)
 
 
-def run_batched(args, rank, world, local_rank):
-    """512 uneven solves as one graph per step; solves/s."""
-    torch, G = _setup(local_rank)
-    npts = args.points
+def _lnz_last_vs_fp64(G, s, prob, n, lnz_last):
+    """|d ln Z| of a solve's last iteration against the plain FP64 GPU path on the same
+    sample stream: the last batch's theta re-evaluated in float64, reduced the same way."""
+    th, lr, ll, lw = s.last_batch(n)
+    with G.ILE(prob, precision=G.RIFT_FP64, max_samples=min(n, 1 << 20)) as s64:
+        l64 = s64.eval(th)
+    x = l64 + lr
+    m = float(np.max(x))
+    return abs(lnz_last - (m + math.log(float(np.sum(np.exp(x - m)))) - math.log(n)))
+
+
+def measure_batched(torch, G, rank, npts, warmup, steps, quick=False, fp64_every=32):
+    """The batched workload: npts uneven solves (1-3 detectors, 2-21 modes, 1e4-1e6
+    samples, 3 adaptive iterations of N/3) as one CUDA graph per step.  Returns solves/s
+    and, unless quick, the same solves one at a time in float32, and a fixed subset of the
+    points (every fp64_every-th) run both as a batch and one at a time through the plain
+    FP64 GPU path (the same requests on both arms, no scaling), with each subset point's
+    |d ln Z| against the FP64 path on the same sample stream."""
     pts = [S.batched_problem(i) for i in rank_points(rank, npts)]
     n_iter = 3
     nper = [max(1, -(-n // n_iter)) for _, n in pts]
@@ -458,23 +510,12 @@ def run_batched(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     batch = G.Batch(solves, [n_iter] * npts, nper, stream=stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    samples = n_iter * sum(nper)
-    flops = sum(flops_per_sample(p) * n_iter * m for (p, _), m in zip(pts, nper))
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         res, rc = batch.run()
         assert rc == 0, rc
-    barrier()
-    clk = _clock_monitor(torch, local_rank)
-    clk.start()
+    torch.cuda.synchronize()
     step_ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -484,80 +525,74 @@ def run_batched(args, rank, world, local_rank):
         e1.synchronize()
         assert rc == 0, rc
         step_ms.append(e0.elapsed_time(e1))
-    barrier()
-    clocks = clk.stop()
-    value, total_s = aggregate_over_ranks(npts * args.steps, sum(step_ms) / 1e3, world)
-    total = 1e3 * total_s
-    launches = batch.kernel_launches() * args.steps
-
-    # end to end: every point's Q, U, V uploaded from pinned host memory, then the run
-    pinned = [{k: torch.from_numpy(np.ascontiguousarray(getattr(p, k), np.complex128)).pin_memory().numpy()
-               for k in ("Q", "U", "V")} for p, _ in pts]
-    h2d = sum(a.nbytes for d in pinned for a in d.values())
-    e2e_t = []
-    for _ in range(0 if args.quick else min(args.steps, 3)):
-        barrier()
-        t0 = time.perf_counter()
-        for sv, d in zip(solves, pinned):
-            sv.set_overlaps(d["Q"], d["U"], d["V"])
-        batch.run()
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_value = aggregate_over_ranks(npts * len(e2e_t), sum(e2e_t), world)[0] if e2e_t else None
+    launches = batch.kernel_launches()
     kinds = {}
     for sv in solves:
         k = _lnl_kernel_name(G, sv.plan())
         kinds[k] = kinds.get(k, 0) + 1
     batch.close()
-
-    # baselines, one solve at a time through rift_ile_adapt: FP32 for every point,
-    # the plain FP64 path on every 16th point (scaled by algorithmic work)
-    seq = {}
-    if not args.quick:
+    ms = statistics.mean(step_ms)
+    out = {"points": npts, "n_iter": n_iter, "samples_per_step": n_iter * sum(nper), "ms_per_step": ms,
+           "solves_per_s": npts / (ms / 1e3), "sample_evals_per_s": n_iter * sum(nper) / (ms / 1e3),
+           "steps": steps, "warmup": warmup, "lnl_kernels": kinds, "gpu_launches_per_step": launches,
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if not quick:
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for sv, m in zip(solves, nper):
             sv.adapt(n_iter, m)
-        seq["fp32_s"] = time.perf_counter() - t0
-        sub = list(range(0, npts, 16))
+        out["fp32_one_at_a_time_solves_per_s"] = npts / (time.perf_counter() - t0)
+        out["speedup_vs_fp32_one_at_a_time"] = out["solves_per_s"] / out["fp32_one_at_a_time_solves_per_s"]
+        sub = list(range(0, npts, fp64_every))
+        subsolves = [G.ILE(pts[i][0], precision=G.RIFT_FP32, max_samples=nper[i], n_bins=64, seed=1 + i)
+                     for i in sub]
+        sb = G.Batch(subsolves, [n_iter] * len(sub), [nper[i] for i in sub], stream=stream)
+        sb.run()   # capture; the timed run below replays the graph (the next 3 iterations)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sres, rc = sb.run()
+        torch.cuda.synchronize()
+        t_b = time.perf_counter() - t0
+        sb.close()
+        dz = [_lnz_last_vs_fp64(G, sv, pts[i][0], nper[i], r["lnZ_iter"][-1])
+              for sv, i, r in zip(subsolves, sub, sres)]
+        for sv in subsolves:
+            sv.close()
         t64 = 0.0
         for i in sub:
-            p, _ = pts[i]
-            with G.ILE(p, precision=G.RIFT_FP64, max_samples=nper[i], n_bins=64, seed=1 + i) as s64:
+            with G.ILE(pts[i][0], precision=G.RIFT_FP64, max_samples=nper[i], n_bins=64, seed=1 + i) as s64:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 s64.adapt(n_iter, nper[i])
                 t64 += time.perf_counter() - t0
-        w_sub = sum(flops_per_sample(pts[i][0]) * nper[i] for i in sub)
-        w_all = sum(flops_per_sample(p) * m for (p, _), m in zip(pts, nper))
-        seq["fp64_s"] = t64 * w_all / w_sub
-        seq["fp64_sample"] = f"{len(sub)} of {npts} points timed, scaled by algorithmic work ({w_all / w_sub:.1f}x)"
+        out["fp64_subset"] = {
+            "points": len(sub), "which": f"every {fp64_every}th point",
+            "batched_fp32_solves_per_s": len(sub) / t_b, "fp64_one_at_a_time_solves_per_s": len(sub) / t64,
+            "speedup_vs_fp64_one_at_a_time": t64 / t_b,
+            "max_abs_dlnZ_vs_fp64": float(max(dz)),
+            "dlnZ_basis": "each point's last iteration, its own samples re-evaluated by the FP64 GPU path"}
     for sv in solves:
         sv.close()
-    achieved = flops / (total / args.steps / 1e3) / 1e12 / world
-    peak = fp32_peak_tflops()
+    return out
+
+
+def run_batched(args, rank, world, local_rank):
+    """512 uneven solves as one graph per step; solves/s."""
+    torch, G = _setup(local_rank)
+    clk = _clock_monitor(torch, local_rank)
+    clk.start()
+    b = measure_batched(torch, G, rank, args.points, args.warmup, args.steps, args.quick, fp64_every=16)
+    clocks = clk.stop()
+    value, total_s = aggregate_over_ranks(args.points * args.steps, b["ms_per_step"] * args.steps / 1e3, world)
     out = {
         "metric": "ILE solves/s (batched uneven solves)", "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched uneven solves: {npts} points per GPU, detectors 1-3, modes 2-21, "
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched uneven solves: {args.points} points per GPU, detectors 1-3, modes 2-21, "
                                "samples 1e4-1e6 log-uniform, 3 adaptive iterations of N/3, one CUDA graph per step",
-                   "points": npts, "samples_per_step": samples, "n_iter": n_iter,
-                   "lnl_kernels": kinds, "l2": "flushed between timed steps (256 MiB write)"},
-        "sample_evals_per_s": samples * args.steps * world / (total / 1e3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole step (all kernels of all solves)",
-                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-                     "note": "algorithmic FP32 flops of every sample evaluation / whole step time"},
-        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": npts * 8 * (7 + 8 * n_iter)},
-        "gpu_launches": launches, "clocks": clocks,
+                   "l2": b["l2"]},
+        "batched": b, "e2e": None, "gpu_launches": b["gpu_launches_per_step"] * args.steps, "clocks": clocks,
     }
-    if seq:
-        out["sequential"] = {
-            "fp32_solves_per_s": npts / seq["fp32_s"], "fp64_solves_per_s": npts / seq["fp64_s"],
-            "speedup_vs_fp32_sequential": value / world / (npts / seq["fp32_s"]),
-            "speedup_vs_fp64_sequential": value / world / (npts / seq["fp64_s"]),
-            "fp64_sample": seq["fp64_sample"]}
     if rank == 0:
         emit(out)
 
@@ -734,68 +769,81 @@ def _latency_stats(got):
             "failed": int(sum(c["status"] != 0 for c in got))}
 
 
-def run_serving(args, rank, world, local_rank):
-    torch, G = _setup(local_rank)
-    reqs = serving_requests(G, args.requests, seed=17 + rank)
+def measure_serving(torch, G, rank, n_requests, quick=False, fp64_every=50):
+    """The serving stream: n_requests solves of four sizes through rift_srv_* (admission
+    by HBM footprint): saturated, then Poisson arrivals at 0.8x and 1.2x the saturated
+    rate.  Unless quick: every request one at a time at its served precision, and a fixed
+    subset (every fp64_every-th request) served on its own and run one at a time through
+    the plain FP64 GPU path (the same requests on both arms, no scaling), with each subset
+    request's |d ln Z| against the FP64 path on the same sample stream (a solve's result is
+    the same alone and in the mix, bitwise: tests/test_gpu_serve.py)."""
+    reqs = serving_requests(G, n_requests, seed=17 + rank)
     budget, slots = 96 << 30, 16
     _serve(G, reqs[:64], None, budget, slots)   # warm-up: kernels, tuner classes, pool
-    clk = _clock_monitor(torch, local_rank)
-    clk.start()
     sat = _latency_stats(_serve(G, reqs, None, budget, slots))
     lam = sat["solves_per_s"]
     at08 = _latency_stats(_serve(G, reqs, 0.8 * lam, budget, slots))
-    at12 = None if args.quick else _latency_stats(_serve(G, reqs, 1.2 * lam, budget, slots))
-    clocks = clk.stop()
-    # one solve at a time through the public API (create, upload, adapt, read back): each
-    # request at its served precision over the whole stream, and the plain FP64 path over
-    # every 25th request scaled to the whole stream by algorithmic work (FP64 takes about
-    # 1 s per 1e6 samples)
-    def one_at_a_time(prec, idx):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in idx:
-            k, p, it, n = reqs[i]
-            with G.ILE(p, precision=_precision(G, k) if prec is None else prec, max_samples=n, n_bins=64,
-                       seed=1 + i) as s:
-                s.adapt(it, n)
-        return time.perf_counter() - t0
-
-    def work(i):
-        k, p, it, n = reqs[i]
-        return flops_per_sample(p) * it * n
-
-    seq = {}
-    all_idx = list(range(len(reqs))) if not args.quick else list(range(min(len(reqs), 40)))
-    seq["served"] = len(all_idx) / one_at_a_time(None, all_idx)
-    sub = all_idx[::25]
-    t64 = one_at_a_time(G.RIFT_FP64, sub) * sum(work(i) for i in all_idx) / sum(work(i) for i in sub)
-    seq["fp64"] = len(all_idx) / t64
-    m = len(sub)
-    value = aggregate_over_ranks(len(reqs), sat["span_s"], world)[0]
-    flops = sum(work(i) for i in range(len(reqs)))
-    peak = fp32_peak_tflops()
+    at12 = _latency_stats(_serve(G, reqs, 1.2 * lam, budget, slots))
     mix = {k: int(sum(r[0] == k for r in reqs)) for k in ("plain", "batched", "large", "high_snr")}
+    out = {"requests": n_requests, "mix": mix, "hbm_budget_bytes": budget, "max_slots": slots,
+           "saturated": sat, "poisson_0.8x": at08, "poisson_1.2x": at12}
+    if quick:
+        return out
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, (k, p, it, n) in enumerate(reqs):
+        with G.ILE(p, precision=_precision(G, k), max_samples=n, n_bins=64, seed=1 + i) as s:
+            s.adapt(it, n)
+    t_seq = time.perf_counter() - t0
+    out["one_at_a_time_same_precision_solves_per_s"] = len(reqs) / t_seq
+    out["speedup_vs_one_at_a_time_same_precision"] = sat["solves_per_s"] * t_seq / len(reqs)
+    sub = list(range(0, len(reqs), fp64_every))
+    subreqs = [reqs[i] for i in sub]
+    got = _serve(G, subreqs, None, budget, slots)
+    ssub = _latency_stats(got)
+    byidx = {c["tag"]: c for c in got}
+    dz = []
+    for j, i in enumerate(sub):
+        k, p, it, n = reqs[i]
+        with G.ILE(p, precision=_precision(G, k), max_samples=n, n_bins=64, seed=1 + j) as s:
+            r = s.adapt(it, n)
+            assert r["lnZ"] == byidx[j]["lnZ"], (r["lnZ"], byidx[j]["lnZ"])   # alone == served
+            dz.append(_lnz_last_vs_fp64(G, s, p, n, r["lnZ_iter"][-1]))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j, i in enumerate(sub):
+        k, p, it, n = reqs[i]
+        with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=64, seed=1 + j) as s:
+            s.adapt(it, n)
+    t64 = time.perf_counter() - t0
+    out["fp64_subset"] = {
+        "requests": len(sub), "which": f"every {fp64_every}th request of the stream",
+        "mix": {k: int(sum(reqs[i][0] == k for i in sub)) for k in ("plain", "batched", "large", "high_snr")},
+        "served_solves_per_s": ssub["solves_per_s"], "fp64_one_at_a_time_solves_per_s": len(sub) / t64,
+        "speedup_vs_fp64_one_at_a_time": ssub["solves_per_s"] * t64 / len(sub),
+        "served_p50_ms": ssub["p50_ms"], "served_p99_ms": ssub["p99_ms"],
+        "max_abs_dlnZ_vs_fp64": float(max(dz)), "abs_dlnZ_vs_fp64": [float(x) for x in dz],
+        "dlnZ_basis": "each request's last iteration, its own samples re-evaluated by the FP64 GPU path"}
+    return out
+
+
+def run_serving(args, rank, world, local_rank):
+    torch, G = _setup(local_rank)
+    clk = _clock_monitor(torch, local_rank)
+    clk.start()
+    sv = measure_serving(torch, G, rank, args.requests, args.quick)
+    clocks = clk.stop()
+    sat = sv["saturated"]
+    value = aggregate_over_ranks(args.requests, sat["span_s"], world)[0]
     out = {
         "metric": "ILE serving solves/s (p50/p99 latency)", "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": len(reqs), "warmup": 64, "ms_per_step": 1e3 * sat["span_s"] / len(reqs), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"serving stream: {len(reqs)} requests (40% plain 2-det/2-mode 1e4 samples, 30% "
+        "steps": args.requests, "warmup": 64, "ms_per_step": 1e3 * sat["span_s"] / args.requests,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"serving stream: {args.requests} requests (40% plain 2-det/2-mode 1e4 samples, 30% "
                                "batched-workload points with 3 iterations, 20% single large 1e6, 10% high-SNR "
                                "2 x 1e6); float32, RIFT_MIXED for the high-SNR points; admission by HBM footprint",
-                   "requests": mix, "hbm_budget_bytes": budget, "max_slots": slots,
                    "problem_pool": "8 plain + 32 batched + 2 large + 2 high-SNR points, per-request seeds"},
-        "saturated": sat, "poisson_0.8x": at08, "poisson_1.2x": at12,
-        "roofline": {"bound": "alu", "achieved": flops / sat["span_s"] / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": flops / sat["span_s"] / 1e12 / peak, "traffic": None,
-                     "kernel": "whole saturated run (all kernels of all requests)",
-                     "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-                     "note": "algorithmic FP32 flops of every sample evaluation / span of the saturated "
-                             "run; the float64 refinement of RIFT_MIXED is extra work not counted"},
-        "sequential": {"served_precision_solves_per_s": seq["served"], "fp64_solves_per_s": seq["fp64"],
-                       "sample": f"served precision: all {len(all_idx)} requests one at a time; FP64: every 25th "
-                                 f"request ({m}), scaled by algorithmic work",
-                       "speedup_vs_sequential_same_precision": sat["solves_per_s"] / seq["served"],
-                       "speedup_vs_fp64_sequential": sat["solves_per_s"] / seq["fp64"]},
+        "serving": sv,
         "e2e": {"value": value, "unit": "solves/s", "note": "requests carry host Q/U/V; the serving loop uploads "
                 "them and reads each result back (latency = submit to result)"},
         "gpu_launches": None, "clocks": clocks,
@@ -804,11 +852,10 @@ def run_serving(args, rank, world, local_rank):
         emit(out)
 
 
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -817,6 +864,8 @@ def main():
     ap.add_argument("--workload", default="single_large", choices=["single_large", "batched", "high_snr", "serving"])
     ap.add_argument("--points", type=int, default=512, help="points of the batched workload")
     ap.add_argument("--requests", type=int, default=2000, help="requests of the serving workload")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="single-large line only (no batched and serving blocks)")
     ap.add_argument("--snr", type=float, default=150.0, help="SNR of the high-SNR workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -335,6 +335,25 @@ int64_t rift_ile_kernel_launches(const rift_ile_t *h);
 #define RIFT_NOALLOC_MAX_SAMPLES ((int64_t)1 << 31)
 int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, double *out, void *cuda_stream);
 
+/* ---- measurement ---------------------------------------------------------------------------
+ * Peak rate of a unit the likelihood kernels use, measured on the current device with
+ * CUDA events (best of three timed launches after a warm-up), in TFLOP/s: a measurement
+ * utility with no counterpart in the paper, so that roofline fractions are taken against
+ * this part's rates rather than datasheet figures.
+ *   RIFT_PEAK_FP32_FMA     float32 FMA (2 flop), independent chains on every SM;
+ *   RIFT_PEAK_TC_F16_N128  tcgen05.mma kind::f16, M = 128, N = 128, K = 16, A in tensor
+ *                          memory, float32 accumulation (the likelihood kernel's shape);
+ *   RIFT_PEAK_TC_F16_N256  the same with N = 256.
+ * One CTA per SM; the tensor-core runs allocate 512 tensor-memory columns per SM, so run
+ * them on an otherwise idle device.  Allocates and frees its own small buffers and stream.
+ * RIFT_EINVAL for an unknown `what` or a tensor-core rate on a device outside the sm_100
+ * family, RIFT_ETIMEOUT if the MMAs did not complete within 2 s, RIFT_ECUDA on a CUDA
+ * error. */
+#define RIFT_PEAK_FP32_FMA 0
+#define RIFT_PEAK_TC_F16_N128 1
+#define RIFT_PEAK_TC_F16_N256 2
+int rift_ile_peak_rate(int32_t what, double *tflops);
+
 void rift_ile_destroy(rift_ile_t *h);
 const char *rift_ile_strerror(int code);
 

@@ -31,7 +31,7 @@ RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_set_waveforms", "rift_ile_get_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_get_plan", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_ile_get_plan", "rift_ile_peak_rate", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
             "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
@@ -121,6 +121,7 @@ def load(build_if_missing: bool = False):
     L.rift_srv_destroy.restype = None
     L.rift_ile_get_plan.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
     L.rift_ile_wait_selftest.argtypes = [vp, i64]
+    L.rift_ile_peak_rate.argtypes = [i32, C.POINTER(C.c_double)]
     L.rift_ile_fair_draws.argtypes = [vp, i64, C.c_uint64, C.c_int, vp, vp, vp]
     L.rift_ile_set_waveforms.argtypes = [vp, i32, vp, vp, vp, vp, C.c_int]
     L.rift_ile_get_overlaps.argtypes = [vp, vp, vp, vp, C.c_int]
@@ -289,6 +290,16 @@ def rift_ile_kernel_launches(h):
 def rift_ile_wait_selftest(h, limit_ns):
     """Status of one bounded wait that runs out (RIFT_ETIMEOUT when the failure path works)."""
     return int(load().rift_ile_wait_selftest(h, int(limit_ns)))
+
+
+RIFT_PEAK_FP32_FMA, RIFT_PEAK_TC_F16_N128, RIFT_PEAK_TC_F16_N256 = 0, 1, 2
+
+
+def rift_ile_peak_rate(what):
+    """Measured peak rate (TFLOP/s) of the float32 FMA pipe or of tcgen05 kind::f16 MMAs."""
+    v = C.c_double()
+    _check(load().rift_ile_peak_rate(int(what), C.byref(v)), "rift_ile_peak_rate")
+    return v.value
 
 
 def rift_ile_get_plan(h):
