@@ -54,11 +54,13 @@ import ile_synth as S  # noqa: E402
 METRIC = "ILE lnL sample-evals/s"
 UNIT = "sample-evals/s"
 N_SAMPLES = 1_000_000
-# DRAM bytes per 1e6-sample likelihood stage (the tensor-core kernel and the large-term
-# correction) from the ncu capture summarised in profiles/lnl_tc_single_large.md, keyed by
-# the SHA-256 of the two kernels' sources; traffic is reported as null for any other source.
+# DRAM bytes of one 1e6-sample launch of the tensor-core likelihood kernel (a 2e5-sample
+# ncu capture scaled by the samples, profiles/lnl_tc_single_large.md), keyed by the SHA-256
+# of the tensor-core kernel's and the correction's sources; null for any other source.
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", f) for f in ("k_tile_tc.cu", "k_fixup.cu")]
-TRAFFIC_BY_SOURCE = {}
+TRAFFIC_BY_SOURCE = {
+    "3e98ac2b2f6e30de16cf5dde8c8e0c1c184a69bbe778eea4e7a9c189816e4061": 5.98e7,
+}
 
 
 def workload_config(prob, n):

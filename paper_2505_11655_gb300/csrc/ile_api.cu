@@ -907,6 +907,49 @@ int rift_ile_set_waveforms(rift_ile_t *h, int32_t n_freq, const double *freqs, c
     };
     auto A = static_cast<double2 *>(grab(sizeof(double2) * (size_t)K * M * F));
     auto t0 = static_cast<double *>(grab(sizeof(double) * K));
+    // Q by FFT when the grid lies on a lattice f_j = f_0 + n_j df (ascending, integer n_j
+    // within 1e-9 relative) and L = f_s / df is a power of two spanning every n_j; else the
+    // direct sum.  RIFT_ILE_DFT=1 forces the direct sum.
+    FftPlan plan{};
+    bool use_fft = !(std::getenv("RIFT_ILE_DFT") && std::getenv("RIFT_ILE_DFT")[0] == '1');
+    std::vector<int> nidx(F);
+    {
+        double df = 0.0, fmax = 0.0;
+        for (int j = 0; j < F; ++j)
+            fmax = std::max(fmax, std::fabs(hf[j]));
+        for (int j = 1; j < F && use_fft; ++j) {
+            const double gap = hf[j] - hf[j - 1];
+            if (!(gap > 0.0))
+                use_fft = false;
+            else if (df == 0.0 || gap < df)
+                df = gap;
+        }
+        const double Lr = use_fft && df > 0.0 ? h->prob.fs / df : 0.0;
+        const int64_t L = (int64_t)std::llround(Lr);
+        use_fft = use_fft && L >= 2 && L <= ((int64_t)1 << 26) && (L & (L - 1)) == 0 &&
+                  std::fabs(Lr - (double)L) <= 1e-9 * (double)L;
+        for (int j = 0; j < F && use_fft; ++j) {
+            const double nr = (hf[j] - hf[0]) / df;
+            const int64_t nj = std::llround(nr);
+            if (std::fabs(hf[j] - hf[0] - (double)nj * df) > 1e-9 * std::max(1.0, fmax) || nj < 0 || nj >= L)
+                use_fft = false;
+            else
+                nidx[j] = (int)nj;
+        }
+        if (use_fft) {
+            plan.L = (int)L;
+            plan.f0 = hf[0];
+            auto ni = static_cast<int *>(grab(sizeof(int) * F));
+            plan.X = static_cast<double2 *>(grab(sizeof(double2) * (size_t)K * M * L));
+            plan.Y = static_cast<double2 *>(grab(sizeof(double2) * (size_t)K * M * L));
+            plan.T = static_cast<double2 *>(grab(sizeof(double2) * (size_t)std::max<int64_t>(1, L / 2)));
+            if (!ni || !plan.X || !plan.Y || !plan.T ||
+                cudaMemcpyAsync(ni, nidx.data(), sizeof(int) * F, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+                use_fft = false;   // the direct sum needs no scratch of this size
+            plan.nidx = ni;
+        }
+    }
+    int launched = 0;
     const double *df = freqs, *dw = weights;
     const double2 *dh = static_cast<const double2 *>(hlm), *dd = static_cast<const double2 *>(data);
     int rc = (A && t0) ? RIFT_OK : RIFT_ENOMEM;
@@ -931,10 +974,10 @@ int rift_ile_set_waveforms(rift_ile_t *h, int32_t n_freq, const double *freqs, c
         (cudaMemcpyAsync(t0, h->q_t0.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream) ||
          cudaMemsetAsync(h->err, 0, sizeof(int), h->stream) ||
          launch_precompute(dh, dd, dw, df, K, M, F, t0, h->prob.fs, h->prob.n_q, A, h->Q64, h->U64, h->V64,
-                           h->stream)))
+                           h->stream, use_fft ? &plan : nullptr, &launched)))
         rc = RIFT_ECUDA;
     if (rc == RIFT_OK)
-        h->launches += 3;
+        h->launches += launched;
     for (void *q : tmp)
         cudaFreeAsync(q, h->stream);
     if (rc != RIFT_OK) {

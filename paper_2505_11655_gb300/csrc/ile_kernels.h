@@ -42,10 +42,19 @@ template <typename Kernel> inline cudaError_t allow_max_dynamic_smem(Kernel kern
 
 // Overlaps from frequency-domain inputs (k_precompute.cu): h [M][F], d [K][F] complex,
 // w [K][F], f [F] (mirror symmetric), q_t0 [K]; A_scratch [K][M][F]; Q [K][M][n_q],
-// U, V [K][M][M] (all device memory).
+// U, V [K][M][M] (all device memory).  fft (optional): Q by FFT on the lattice
+// f_j = f0 + nidx[j] df, L = f_s / df a power of two (nidx in [0, L)); X, Y [K][M][L] and
+// T [L/2] scratch.  *launched (optional): kernels enqueued.
+struct FftPlan {
+    int L;
+    double f0;
+    const int *nidx;
+    double2 *X, *Y, *T;
+};
 cudaError_t launch_precompute(const double2 *h, const double2 *d, const double *w, const double *f, int K, int M,
                               int F, const double *q_t0_dev, double fs, int n_q, double2 *A_scratch, double2 *Q,
-                              double2 *U, double2 *V, cudaStream_t st);
+                              double2 *U, double2 *V, cudaStream_t st, const FftPlan *fft = nullptr,
+                              int *launched = nullptr);
 
 // Fair draws (k_fair.cu): fixed-point weights of lnw (max from stats[slot]), their
 // running sums, and n_draws sample choices with their time-choice integers.

@@ -6,7 +6,18 @@
 //   U_k,lm,l'm'   = 2 sum_j w_k conj(h_lm) h_l'm',   V_k,lm,l'm' = 2 sum_j w_k h_lm(-f_j) h_l'm'(f_j).
 // U is Hermitian and V symmetric (the weights are symmetric in f), so only pairs
 // lm <= l'm' are summed and mirrored (the halving the paper describes for U and V).
-// All in float64: this is the precompute stage, ~1e8 multiply-adds per point.
+// All in float64.
+//
+// Q by a fast Fourier transform.  When the frequencies lie on a lattice f_j = f_0 + n_j df
+// (integers n_j spanning fewer than L = f_s / df points, L a power of two), then with
+// t_s = q_t0 + s / f_s,
+//   exp(2 pi i f_j t_s) = exp(2 pi i f_j q_t0) exp(2 pi i f_0 s / f_s) exp(2 pi i n_j s / L),
+// so Q_k,lm(t_s) = exp(2 pi i f_0 s / f_s) Y[s mod L], Y the length-L transform (sign +)
+// of X[n_j] = A_j exp(2 pi i f_j q_t0): O(L log L) per (detector, mode) instead of
+// O(n_q F).  The transform is a radix-2 Stockham (self-sorting) FFT, one kernel per
+// stage over every (detector, mode) sequence at once, twiddles exp(2 pi i e / L) from a
+// table.  Grids off a lattice (or with L not a power of two) take the direct sum.
+#include <algorithm>
 #include <cmath>
 
 #include "ile_kernels.h"
@@ -121,16 +132,110 @@ __global__ void uv_kernel(const double2 *__restrict__ h, const double *__restric
     }
 }
 
+// ---------------------------------------------------------------- FFT path for Q
+
+// T[e] = exp(2 pi i e / L), e < L / 2
+__global__ void fft_twiddle_kernel(int L, double2 *__restrict__ T)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < L / 2; e += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)e / (double)L, &sn, &cs);
+        T[e] = make_double2(cs, sn);
+    }
+}
+
+// X [K M][L] (zeroed): X[km][n_j] = A[km][j] exp(2 pi i f_j q_t0_k)
+__global__ void fft_scatter_kernel(const double2 *__restrict__ A, const double *__restrict__ f,
+                                   const int *__restrict__ nidx, int K, int M, int F, const double *__restrict__ q_t0,
+                                   int L, double2 *__restrict__ X)
+{
+    const int64_t total = (int64_t)K * M * F;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % F);
+        const int64_t km = e / F;
+        const int k = (int)(km / M);
+        double sn, cs;
+        sincospi(2.0 * f[j] * q_t0[k], &sn, &cs);
+        const double2 a = A[e];
+        X[km * L + nidx[j]] = make_double2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+    }
+}
+
+// One radix-2 Stockham stage (sub-transforms of length Ns combined into 2 Ns) of every
+// sequence: butterfly j < L/2 of a sequence reads j and j + L/2 and writes
+// (j / Ns) 2 Ns + j % Ns and that plus Ns, with twiddle exp(2 pi i (j % Ns) / (2 Ns)).
+__global__ void fft_stage_kernel(const double2 *__restrict__ in, double2 *__restrict__ out, int L, int Ns,
+                                 const double2 *__restrict__ T, int64_t n_seq)
+{
+    const int half = L >> 1;
+    const int64_t total = n_seq * half;
+    const int tstride = half / Ns;   // T index step: (j % Ns) L / (2 Ns)
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / half;
+        const int j = (int)(e - q * half);
+        const int kk = j & (Ns - 1);
+        const double2 w = T[(size_t)kk * tstride];
+        const double2 a = in[q * L + j], b0 = in[q * L + j + half];
+        const double2 b = make_double2(b0.x * w.x - b0.y * w.y, b0.x * w.y + b0.y * w.x);
+        const int64_t o = q * L + (int64_t)(j / Ns) * 2 * Ns + kk;
+        out[o] = make_double2(a.x + b.x, a.y + b.y);
+        out[o + Ns] = make_double2(a.x - b.x, a.y - b.y);
+    }
+}
+
+// Q[km][s] = exp(2 pi i f_0 s / f_s) Y[km][s mod L]
+__global__ void fft_extract_kernel(const double2 *__restrict__ Y, int64_t n_seq, int L, double f0, double fs, int n_q,
+                                   double2 *__restrict__ Q)
+{
+    const int64_t total = n_seq * n_q;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t km = e / n_q;
+        const int s = (int)(e - km * n_q);
+        double sn, cs;
+        sincospi(2.0 * f0 * ((double)s / fs), &sn, &cs);
+        const double2 y = Y[km * L + (s & (L - 1))];
+        Q[e] = make_double2(y.x * cs - y.y * sn, y.x * sn + y.y * cs);
+    }
+}
+
 cudaError_t launch_precompute(const double2 *h, const double2 *d, const double *w, const double *f, int K, int M,
                               int F, const double *q_t0_dev, double fs, int n_q, double2 *A_scratch, double2 *Q,
-                              double2 *U, double2 *V, cudaStream_t st)
+                              double2 *U, double2 *V, cudaStream_t st, const FftPlan *fft, int *launched)
 {
     const int64_t nA = (int64_t)K * M * F;
+    int k = 0;
     qfreq_kernel<<<(int)std::min<int64_t>((nA + 255) / 256, 152 * 8), 256, 0, st>>>(h, d, w, K, M, F, A_scratch);
-    dim3 grid((n_q + kPcThreads - 1) / kPcThreads, K);
-    q_series_kernel<<<grid, kPcThreads, 0, st>>>(A_scratch, f, K, M, F, q_t0_dev, fs, n_q, Q);
+    ++k;
+    if (fft) {
+        const int L = fft->L;
+        const int64_t nseq = (int64_t)K * M;
+        cudaError_t e = cudaMemsetAsync(fft->X, 0, sizeof(double2) * (size_t)nseq * L, st);
+        if (e != cudaSuccess)
+            return e;
+        fft_twiddle_kernel<<<std::max(1, std::min(L / 2 / 256, 152 * 8)), 256, 0, st>>>(L, fft->T);
+        fft_scatter_kernel<<<(int)std::min<int64_t>((nA + 255) / 256, 152 * 8), 256, 0, st>>>(
+            A_scratch, f, fft->nidx, K, M, F, q_t0_dev, L, fft->X);
+        double2 *a = fft->X, *b = fft->Y;
+        const int64_t nb = nseq * (L / 2);
+        for (int Ns = 1; Ns < L; Ns <<= 1) {
+            fft_stage_kernel<<<(int)std::min<int64_t>((nb + 255) / 256, 152 * 16), 256, 0, st>>>(a, b, L, Ns, fft->T,
+                                                                                                 nseq);
+            std::swap(a, b);
+            ++k;
+        }
+        const int64_t nqt = nseq * n_q;
+        fft_extract_kernel<<<(int)std::min<int64_t>((nqt + 255) / 256, 152 * 8), 256, 0, st>>>(a, nseq, L, fft->f0,
+                                                                                              fs, n_q, Q);
+        k += 3;
+    } else {
+        dim3 grid((n_q + kPcThreads - 1) / kPcThreads, K);
+        q_series_kernel<<<grid, kPcThreads, 0, st>>>(A_scratch, f, K, M, F, q_t0_dev, fs, n_q, Q);
+        ++k;
+    }
     const int64_t pairs = (int64_t)K * M * (M + 1) / 2;
     uv_kernel<<<(int)std::min<int64_t>((pairs + 7) / 8, 152 * 8), 256, 0, st>>>(h, w, K, M, F, U, V);
+    if (launched)
+        *launched = k + 1;
     return cudaGetLastError();
 }
 

@@ -81,3 +81,54 @@ def test_waveforms_device_inputs_and_errors(G, orc):
         with pytest.raises(G.RiftError) as e:
             s.set_waveforms(f, h, d, wb)
         assert e.value.code == G.RIFT_ENONFINITE
+
+
+def test_fft_and_direct_sum_agree_on_the_workload_grids(G, monkeypatch):
+    """The workload grids lie on a lattice (+-2..256 Hz in steps of 2 Hz, f = 0 left out),
+    so Q comes from the FFT path; forcing the direct sum gives the same Q to 1e-12 of
+    max |Q|, and identical U, V."""
+    for p in (S.plain_fp64_problem(), S.single_large_problem()):
+        f, h, d, w = inputs(p)
+        got = {}
+        for dft in ("0", "1"):
+            monkeypatch.setenv("RIFT_ILE_DFT", dft)
+            with G.ILE(p, precision=G.RIFT_FP64, max_samples=16, set_overlaps=False) as s:
+                s.set_waveforms(f, h, d, w)
+                got[dft] = s.get_overlaps(p.n_q)
+        (Qf, Uf, Vf), (Qd, Ud, Vd) = got["0"], got["1"]
+        assert np.max(np.abs(Qf - Qd)) <= 1e-12 * np.max(np.abs(Qd))
+        assert np.array_equal(Uf, Ud) and np.array_equal(Vf, Vd)
+
+
+def long_segment_inputs(n_freq, df, K, M, seed, jitter=0.0):
+    """A two-sided mirror-symmetric grid of n_freq frequencies (f_j = (j - (n_freq-1)/2) df,
+    optionally moved off the lattice by a symmetric jitter), random mode waveforms and
+    data, and symmetric weights."""
+    rng = np.random.default_rng(seed)
+    half = n_freq // 2
+    fpos = (np.arange(half) + 0.5) * df
+    if jitter:
+        fpos = fpos + jitter * df * rng.random(half)
+    f = np.concatenate([-fpos[::-1], fpos])
+    h = (rng.normal(size=(M, n_freq)) + 1j * rng.normal(size=(M, n_freq))) / np.sqrt(n_freq)
+    d = (rng.normal(size=(K, n_freq)) + 1j * rng.normal(size=(K, n_freq))) / np.sqrt(n_freq)
+    wpos = rng.uniform(0.5, 2.0, size=(K, half))
+    w = np.concatenate([wpos[:, ::-1], wpos], axis=1)
+    return f, h, d, w
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.3])
+def test_long_segment_overlaps_against_oracle(G, jitter):
+    """A 4 s segment at 4096 Hz: 2^14 frequencies (df = 0.25 Hz, L = f_s / df = 2^14).  On the
+    lattice Q comes from the radix-2 FFT, off it (jitter) from the direct sum; both against
+    the oracle's plain sums to 1e-12 of max |Q| (Eq. QUV), U and V to 1e-12 of their maxima."""
+    from oracle import precompute as PC
+    p = S.make_problem(("H1", "L1"), 4, 4096.0, n_t=401, snr=15.0, seed=S.config_seed(3, 81))
+    f, h, d, w = long_segment_inputs(1 << 14, 0.25, p.n_det, p.n_modes, 17, jitter)
+    Q, U, V = PC.overlaps(f, h, d, w, p.q_t0, p.fs, p.n_q)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=16, set_overlaps=False) as s:
+        s.set_waveforms(f, h, d, w)
+        gQ, gU, gV = s.get_overlaps(p.n_q)
+    assert np.max(np.abs(gQ - Q)) <= 1e-12 * np.max(np.abs(Q))
+    assert np.max(np.abs(gU - U)) <= 1e-12 * np.max(np.abs(U))
+    assert np.max(np.abs(gV - V)) <= 1e-12 * np.max(np.abs(V))
