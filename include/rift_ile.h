@@ -318,7 +318,9 @@ int64_t rift_ile_kernel_launches(const rift_ile_t *h);
  *             (NULL: the maximum of lnw is reported instead)
  *   out  [8]  DEVICE memory, written: ln Z = ln((1/n) sum w), sigma_lnZ, n_eff =
  *             sum w / max w, n_ESS = (sum w)^2 / sum w^2, max ln w, max lnL, n, 0
- *             (the same definitions and the same kernels as rift_ile_marginalize)
+ *             (the same definitions and kernels as rift_ile_marginalize in RIFT_FP64
+ *             mode: every term exp(ln w - max) in float64; the float32 modes of
+ *             rift_ile_marginalize sum float32 terms, ~1e-7 relative)
  *   cuda_stream  cudaStream_t (NULL: legacy default stream); the call waits for
  *             the stream before returning, to read its status.
  *
@@ -326,7 +328,8 @@ int64_t rift_ile_kernel_launches(const rift_ile_t *h);
  * GPU that loads the library until the process exits; nothing is allocated per
  * call (no cudaMalloc, cudaFree or allocating library routine).  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and caches it: make that first call before any stream capture.
+ * device current) and caches it: make that first call on a device before any stream
+ * capture begins there.
  * All calls share the one array, which keeps the last call's contents; the error
  * word is cleared by each call.  Calls that overlap on the GPU (different streams
  * or threads at the same time) race on the array and must be serialised by the

@@ -32,10 +32,11 @@ def G():
 
 
 def test_noalloc_reduction_matches_marginalize_twice(G):
+    """Against rift_ile_marginalize of a float64 handle (the same float64 terms)."""
     import torch
     p = S.single_large_problem()
     n = 20000
-    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=21) as s:
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=32, seed=21) as s:
         for _ in range(2):
             r = s.marginalize(n)
             lnw = torch.empty(n, dtype=torch.float64, device="cuda")
@@ -50,6 +51,25 @@ def test_noalloc_reduction_matches_marginalize_twice(G):
             assert abs(o[3] - r["n_ess"]) <= 1e-12 * r["n_ess"]
             assert abs(o[5] - r["lnL_max"]) <= 1e-12 * max(1.0, abs(r["lnL_max"]))
             assert o[6] == n
+
+
+def test_noalloc_reduction_spread_weights_against_oracle_twice(G, oracle_lib):
+    """Log-weights spread uniformly over [-5, 0] (no single sample dominates): ln Z,
+    sigma, n_eff and n_ESS equal the oracle's float64 definitions to 1e-12 on two calls in
+    a row with different inputs."""
+    import torch
+    rng = np.random.default_rng(4)
+    for n in (100000, 777):
+        lnw = rng.uniform(-5.0, 0.0, n)
+        ref = oracle_lib.reduce(lnw)
+        out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+        G.rift_ile_reduce_noalloc(torch.from_numpy(lnw).cuda(), n, out)
+        o = out.cpu().numpy()
+        assert abs(o[0] - ref["lnZ"]) <= 1e-12 * max(1.0, abs(ref["lnZ"]))
+        assert abs(o[1] - ref["sigma_lnZ"]) <= 1e-12
+        assert abs(o[2] - ref["n_eff"]) <= 1e-12 * ref["n_eff"]
+        assert abs(o[3] - ref["n_ess"]) <= 1e-12 * ref["n_ess"]
+        assert o[6] == n
 
 
 def test_noalloc_reduction_rejects_bad_sizes(G):
