@@ -73,7 +73,9 @@ def lib():
             L.orc_philox4x32_10.restype = None
             L.orc_uniforms.argtypes = [C.c_uint64, C.c_uint32, i64, vp]
             L.orc_uniforms.restype = None
-            L.orc_draw.argtypes = [vp, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, C.c_int, vp, vp, vp]
+            L.orc_draw.argtypes = [vp, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, C.c_int, vp, vp, vp, vp]
+            L.orc_portfolio_members.argtypes = [C.c_uint64, C.c_uint32, i64, dbl, vp]
+            L.orc_portfolio_members.restype = None
             L.orc_draw.restype = None
             L.orc_adapt.argtypes = [vp, C.c_int, vp, vp, i64, dbl, dbl, C.c_int]
             L.orc_adapt.restype = None
@@ -228,15 +230,26 @@ class Sampler:
         self.dist_marg = bool(dist_marg)
         self.iteration = 0
 
-    def draw(self, n, it=None, i0=0):
+    def draw(self, n, it=None, i0=0, want_v=False):
         it = self.iteration if it is None else it
         th = np.empty((n, 6))
         lr = np.empty(n)
         bins = np.empty((n, 6), np.int32)
+        v = np.empty((n, 6)) if want_v else None
         Pc = np.ascontiguousarray(self.P)
         lib().orc_draw(_p(Pc), self.B, self.seed, it, i0, n, self.d_min, self.d_max, int(self.dist_marg), _p(th),
-                       _p(lr), _p(bins))
-        return th, lr, bins
+                       _p(lr), _p(bins), _p(v) if want_v else None)
+        return (th, lr, bins, v) if want_v else (th, lr, bins)
+
+    def ln_density(self, v):
+        """ln p_s at points v [n][6] of the unit cube (bins floor(v B)), and the bins."""
+        b = np.minimum(np.floor(np.asarray(v) * self.B), self.B - 1).astype(np.int32)
+        tot = np.cumsum(self.P, axis=1)[:, -1]   # the running sum, as in the draws
+        lnd = np.zeros(len(b))
+        for d in range(6):
+            if not (self.dist_marg and d == 5):
+                lnd += np.log(self.B * self.P[d, b[:, d]] / tot[d])
+        return lnd, b
 
     def adapt(self, bins, lnw):
         Pc = np.ascontiguousarray(self.P)

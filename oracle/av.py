@@ -137,6 +137,20 @@ class AV:
         th, v = self.draw(n)
         ll = np.asarray(lnL_fn(th), np.float64)
         lnw = ll + math.log(V_draw)
+        rec = self.update(v, ll)
+        rec.update(theta=th, v=v, lnL=ll, lnw=lnw, level=level_draw, n_cells=ncell_draw, V=V_draw)
+        return rec
+
+    def contains(self, v):
+        """Whether points v [n][6] lie in the active cells."""
+        keys = cell_keys(v, self.level)
+        pos = np.searchsorted(self.cells, keys)
+        return (pos < self.cells.size) & (self.cells[np.minimum(pos, self.cells.size - 1)] == keys)
+
+    def update(self, v, ll):
+        """Steps 3-5 on fresh points v [n][6] with ln L values ll (index order); returns
+        dict(n_live, n_min, next_level, next_cells)."""
+        n = ll.size
         # 3. live set
         if self.thr is None:
             keep = np.ones(n, bool)
@@ -160,8 +174,7 @@ class AV:
         self.V = self.cells.size * 2.0 ** (-6 * self.level)
         self.thr = (m, b_thr)
         self.iteration += 1
-        return dict(theta=th, v=v, lnL=ll, lnw=lnw, level=level_draw, n_cells=ncell_draw, V=V_draw,
-                    n_live=n_live, n_min=n_min, next_level=self.level, next_cells=self.cells.size)
+        return dict(n_live=n_live, n_min=n_min, next_level=self.level, next_cells=self.cells.size)
 
 
 def run(lnL_fn, n_iter, n, **kw):

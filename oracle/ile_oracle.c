@@ -467,7 +467,8 @@ void orc_uniforms(uint64_t seed, uint32_t iter, int64_t i, double u[6])
  * P, C[0] = 0), and v = (b + (u C[B] - C[b]) / P[b]) / B, the within-bin
  * fraction clamped to [0, 1). */
 void orc_draw(const double *P, int B, uint64_t seed, uint32_t iter, int64_t i0, int64_t n,
-              double d_min, double d_max, int marg, double *theta, double *lnp_minus_lnps, int32_t *bins)
+              double d_min, double d_max, int marg, double *theta, double *lnp_minus_lnps, int32_t *bins,
+              double *v_out)
 {
     double *C = malloc(sizeof(double) * 6 * (size_t)(B + 1));
     for (int d = 0; d < 6; ++d) {
@@ -507,6 +508,9 @@ void orc_draw(const double *P, int B, uint64_t seed, uint32_t iter, int64_t i0, 
         th[4] = acos(1.0 - 2.0 * v[4]);
         th[5] = cbrt(d_min * d_min * d_min + v[5] * (d_max * d_max * d_max - d_min * d_min * d_min));
         lnp_minus_lnps[s] = lr;
+        if (v_out)
+            for (int d = 0; d < 6; ++d)
+                v_out[6 * s + d] = v[d];
     }
     free(C);
 }
@@ -582,6 +586,25 @@ void orc_av_draw(const uint64_t *cells, int64_t n_cells, int level, uint64_t see
         th[3] = 2.0 * ORC_PI * v[3];
         th[4] = acos(1.0 - 2.0 * v[4]);
         th[5] = cbrt(d_min * d_min * d_min + v[5] * (d_max * d_max * d_max - d_min * d_min * d_min));
+    }
+}
+
+/* ---------------------------------------------------------------- portfolio member choice */
+
+/* The portfolio integrator (Sec. IV, "Portfolio integrator") draws each sample from one
+ * member, member 0 with probability W0 (the weights normalised to sum 1).  Draw i of
+ * portfolio iteration `iter` uses Philox4x32-10 with key = seed and counter
+ * (i low, i high, iter, 7): words (0,1) give the 53-bit integer U, and the sample comes
+ * from member 0 when U 2^-53 < W0 (exact in double precision), else member 1. */
+void orc_portfolio_members(uint64_t seed, uint32_t iter, int64_t n, double w0, int32_t *member)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t ctr[4] = {(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, 7u};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        member[i] = orc_u53(r[0], r[1]) < w0 ? 0 : 1;
     }
 }
 
