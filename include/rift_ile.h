@@ -260,6 +260,69 @@ int rift_ile_av(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, double p_thr,
  * live points, active volume.  Any output may be NULL. */
 int rift_ile_av_info(const rift_ile_t *h, int32_t *level, int64_t *n_cells, int64_t *n_live, double *volume);
 
+/* Portfolio integrator (arXiv:2505.11655 Sec. IV, "Portfolio integrator"): the sampling
+ * prior is the weighted average of its members' priors, p_s = sum_a W_a p_s,a / sum_a W_a,
+ * here over the histogram sampler (member 0: rift_ile_adapt's, the handle's masses) and
+ * the adaptive-volume integrator (member 1: rift_ile_av's, the handle's AV state).  Both
+ * draw through the prior-CDF cube, where g_hist = prod_d B P_d[b_d] / sum_b P_d[b] and
+ * g_AV = 1/V on the active cells (0 elsewhere) are their densities relative to the prior.
+ * Portfolio iteration g (counted from the last restart), weights W (sum 1):
+ *   1. draw i comes from member 0 when U 2^-53 < W_0, U the 53-bit integer of words 0,1 of
+ *      Philox4x32-10 (key = seed, counter (i low, i high, g, 7)); member 0 then draws as
+ *      rift_ile_adapt's iteration g would, member 1 as rift_ile_av's iteration g would;
+ *   2. ln p - ln p_s = -ln(W_0 g_hist(v) + W_1 g_AV(v)) (the bin of an AV draw is
+ *      floor(v_d B); with one member active, that member's own value);
+ *   3. time-marginalised ln L, ln w, the iteration's record;
+ *   4. weights (adapt_weights = 1, both members active): n_ESS,a = (sum w)^2 / sum w^2 over
+ *      the batch's draws from member a; W' proportional to n_ESS; no weight below 0.05/N_s
+ *      (N_s = 2): weights below are set to it, the other scaled to fill the rest;
+ *   5. training: a member whose new weight is below 0.05 is frozen (not trained); member 0
+ *      adapts its masses on every sample of the batch (bins, ln w), member 1 updates its
+ *      live set, threshold and grid (rift_ile_av steps 3-5) from its own draws in index
+ *      order (none: not trained).
+ *   cfg->members       RIFT_MEMBER_HIST | RIFT_MEMBER_AV (at least one)
+ *   cfg->av_start      first iteration in which member 1 draws (before it member 0 alone,
+ *                      W = (1, 0)); at av_start the weights restart from w_init; 0 when
+ *                      member 1 is the only member
+ *   cfg->adapt_weights 1: step 4; 0: the weights stay at w_init
+ *   cfg->w_init[2]     initial weights, >= 0, normalised over the active members (an
+ *                      active member's must be > 0 unless the other's is)
+ *   cfg->p_thr, n_min_star, capacity   member 1's settings, as for rift_ile_av (the
+ *                      capacity is fixed by the first rift_ile_av or portfolio call)
+ * restart = 1 (or the first call): weights from w_init, iteration 0, uniform histogram
+ * masses, the AV member on the whole cube.  Results pool the call's iterations like
+ * rift_ile_adapt; the last iteration's draws are the handle's most recent batch.  Not
+ * with distance_marg.  RIFT_EINVAL for bad arguments (as rift_ile_av, and the above). */
+#define RIFT_MEMBER_HIST 1
+#define RIFT_MEMBER_AV 2
+typedef struct {
+    int32_t members;
+    int32_t av_start;
+    int32_t adapt_weights;
+    int32_t reserved;
+    double w_init[2];
+    double p_thr;
+    int64_t n_min_star;
+    int64_t capacity;
+} rift_portfolio_config;
+int rift_ile_portfolio(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, const rift_portfolio_config *cfg,
+                       int32_t restart, rift_ile_result *out);
+/* State after the last portfolio iteration: iterations since restart, the weights the
+ * last batch was drawn with and those of the next, each member's n_ESS and draw count in
+ * the last batch, whether it took part (active) and whether it was frozen (not trained
+ * after that batch). */
+typedef struct {
+    int32_t iteration;
+    int32_t active[2];
+    int32_t frozen[2];
+    int32_t reserved;
+    double W_last[2];
+    double W_next[2];
+    double n_ess[2];
+    int64_t n_drawn[2];
+} rift_portfolio_info;
+int rift_ile_portfolio_info(const rift_ile_t *h, rift_portfolio_info *info);
+
 /* Fair draws from the most recent batch (the final ILE pass: extrinsic samples drawn
  * fairly from the Monte Carlo integral's weighted samples, arXiv:2505.11655 Sec. II;
  * the two-step fair draw of Sec. II D).  Draw d takes sample i, with replacement, with

@@ -31,7 +31,7 @@ RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_set_waveforms", "rift_ile_get_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_get_plan", "rift_ile_peak_rate", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_ile_get_plan", "rift_ile_peak_rate", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_portfolio", "rift_ile_portfolio_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
             "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
@@ -52,6 +52,27 @@ class rift_ile_config(C.Structure):
         ("adapt_temper", C.c_double), ("seed", C.c_uint64), ("max_samples", C.c_int64),
         ("distance_marg", C.c_int32),
     ]
+
+
+RIFT_MEMBER_HIST = 1
+RIFT_MEMBER_AV = 2
+
+
+class rift_portfolio_config(C.Structure):
+    _fields_ = [("members", C.c_int32), ("av_start", C.c_int32), ("adapt_weights", C.c_int32),
+                ("reserved", C.c_int32), ("w_init", C.c_double * 2), ("p_thr", C.c_double),
+                ("n_min_star", C.c_int64), ("capacity", C.c_int64)]
+
+
+class rift_portfolio_info(C.Structure):
+    _fields_ = [("iteration", C.c_int32), ("active", C.c_int32 * 2), ("frozen", C.c_int32 * 2),
+                ("reserved", C.c_int32), ("W_last", C.c_double * 2), ("W_next", C.c_double * 2),
+                ("n_ess", C.c_double * 2), ("n_drawn", C.c_int64 * 2)]
+
+    def as_dict(self):
+        return dict(iteration=self.iteration, active=list(self.active), frozen=list(self.frozen),
+                    W_last=list(self.W_last), W_next=list(self.W_next), n_ess=list(self.n_ess),
+                    n_drawn=list(self.n_drawn))
 
 
 class rift_ile_result(C.Structure):
@@ -127,6 +148,8 @@ def load(build_if_missing: bool = False):
     L.rift_ile_get_overlaps.argtypes = [vp, vp, vp, vp, C.c_int]
     L.rift_ile_av.argtypes = [vp, i32, i64, C.c_double, i64, i64, i32, C.POINTER(rift_ile_result)]
     L.rift_ile_av_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]
+    L.rift_ile_portfolio.argtypes = [vp, i32, i64, C.POINTER(rift_portfolio_config), i32, C.POINTER(rift_ile_result)]
+    L.rift_ile_portfolio_info.argtypes = [vp, C.POINTER(rift_portfolio_info)]
     L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
     L.rift_batch_run.argtypes = [vp, C.POINTER(rift_ile_result)]
     L.rift_batch_kernel_launches.argtypes = [vp]
@@ -331,6 +354,19 @@ def rift_ile_av(h, n_iter, n_per_iter, p_thr, n_min_star, capacity, restart):
     _check(load().rift_ile_av(h, int(n_iter), int(n_per_iter), float(p_thr), int(n_min_star), int(capacity),
                               int(restart), C.byref(r)), "rift_ile_av")
     return r
+
+
+def rift_ile_portfolio(h, n_iter, n_per_iter, cfg, restart):
+    r = rift_ile_result()
+    _check(load().rift_ile_portfolio(h, int(n_iter), int(n_per_iter), C.byref(cfg), int(restart), C.byref(r)),
+           "rift_ile_portfolio")
+    return r
+
+
+def rift_ile_portfolio_info(h):
+    info = rift_portfolio_info()
+    _check(load().rift_ile_portfolio_info(h, C.byref(info)), "rift_ile_portfolio_info")
+    return info.as_dict()
 
 
 def rift_ile_av_info(h):
@@ -571,6 +607,18 @@ class ILE:
 
     def av_info(self):
         return rift_ile_av_info(self.h)
+
+    def portfolio(self, n_iter, n_per_iter, members=RIFT_MEMBER_HIST | RIFT_MEMBER_AV, av_start=0, adapt_weights=True,
+                  w_init=(0.5, 0.5), p_thr=0.9999, n_min_star=1000, capacity=None, restart=False):
+        """Portfolio iterations over {histogram, AV} (rift_ile_portfolio); capacity
+        defaults to 4 n_per_iter."""
+        cfg = rift_portfolio_config(int(members), int(av_start), 1 if adapt_weights else 0, 0,
+                                    (C.c_double * 2)(*[float(x) for x in w_init]), float(p_thr), int(n_min_star),
+                                    int(capacity if capacity is not None else 4 * n_per_iter))
+        return rift_ile_portfolio(self.h, n_iter, n_per_iter, cfg, 1 if restart else 0).as_dict()
+
+    def portfolio_info(self):
+        return rift_ile_portfolio_info(self.h)
 
     def fair_draws(self, n_draws, seed=1):
         """Fair draws from the most recent batch: (theta [n][6], t [n], index [n])."""

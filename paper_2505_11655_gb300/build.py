@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librift_ile.so")
-SOURCES = ["ile_api.cu", "ile_batch.cu", "ile_tune.cu", "ile_serve.cu", "k_lnl.cu", "k_tile.cu", "k_tile_tc.cu", "k_refine.cu", "k_fixup.cu", "k_sampler.cu", "k_fair.cu", "ile_av.cu", "k_precompute.cu", "k_selftest.cu", "k_peaks.cu"]
+SOURCES = ["ile_api.cu", "ile_batch.cu", "ile_tune.cu", "ile_serve.cu", "k_lnl.cu", "k_tile.cu", "k_tile_tc.cu", "k_refine.cu", "k_fixup.cu", "k_sampler.cu", "k_fair.cu", "ile_av.cu", "ile_portfolio.cu", "k_precompute.cu", "k_selftest.cu", "k_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

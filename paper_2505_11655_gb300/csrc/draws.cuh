@@ -1,0 +1,143 @@
+// Per-sample draws of the two sampling priors on the unit cube of prior-CDF coordinates
+// v (internal): the product-form histogram (arXiv:2505.11655 Sec. II B) and the
+// adaptive-volume cells (Sec. IV A).  Shared by their own draw kernels and by the
+// portfolio's, which mixes them (Sec. IV, "Portfolio integrator").
+#pragma once
+
+#include "ile_kernels.h"
+
+namespace rift {
+
+// Shared-memory tables of the histogram draw: [6][B+1] running sums, [6][B] reciprocal
+// masses, [6][B] log densities (float64 divisions once per block instead of per sample).
+__host__ __device__ inline size_t hist_table_doubles(int B) { return 6 * (size_t)(B + 1) + 12 * (size_t)B; }
+
+__device__ __forceinline__ void hist_load_tables(const SamplerDev &S, double *sC)
+{
+    const int B = S.B;
+    double *sR = sC + 6 * (B + 1);
+    double *sL = sR + 6 * B;
+    for (int e = threadIdx.x; e < 6 * (B + 1); e += blockDim.x)
+        sC[e] = S.C[e];
+    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x) {
+        sR[e] = 1.0 / S.P[e];
+        sL[e] = S.L[e];
+    }
+}
+
+// Draw i of histogram iteration `iter`: Philox4x32-10 (key = seed, counter (i lo, i hi,
+// iter, p), p = 0..2; words (0,1) give dimension 2p, (2,3) dimension 2p+1); inverse CDF of
+// the piecewise-constant masses.  Writes v, lr = ln p - ln p_s (the distance excluded when
+// marginalised) and the six 10-bit bin indices packed (dimension d at bit 10 d).
+__device__ __forceinline__ void hist_draw_one(const double *sC, int B, int marg, uint32_t iter, int64_t i,
+                                              uint32_t k0, uint32_t k1, double v[6], double &lr, uint64_t &packed)
+{
+    const double *sR = sC + 6 * (B + 1);
+    const double *sL = sR + 6 * B;
+    const double inv_b = 1.0 / B;
+    // the 53-bit integers m of the uniforms u = m 2^-53
+    double m53[6];
+#pragma unroll
+    for (uint32_t p = 0; p < 3; ++p) {
+        U4 r = philox10(U4{(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p}, k0, k1);
+        m53[2 * p] = (double)bits53(r.x, r.y);
+        m53[2 * p + 1] = (double)bits53(r.z, r.w);
+    }
+    lr = 0.0;
+    packed = 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const double *Cd = sC + d * (B + 1);
+        // x = u tot = m (2^-53 tot): both scalings by 2^-53 are exact, so this is the
+        // same single rounding as (m 2^-53) tot
+        const double x = m53[d] * (Cd[B] * 0x1.0p-53);
+        // last b in [0, B-1] with C[b] <= x (C[0] = 0 <= x always).  Non-negative doubles
+        // order like their bit patterns read as integers, so the search compares integers
+        // (float64 comparisons run on the slow float64 pipe of this part)
+        const long long xb = __double_as_longlong(x);
+        const long long *Cb = reinterpret_cast<const long long *>(Cd);
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (Cb[mid] <= xb)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        // t in [0, 1): negative or NaN -> 0, [1, inf] -> the largest double below 1,
+        // decided on the bit pattern (integer comparisons)
+        long long tb = __double_as_longlong((x - Cd[lo]) * sR[d * B + lo]);
+        if (tb < 0 || (tb & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL)
+            tb = 0;
+        else if (tb >= 0x3ff0000000000000LL)
+            tb = 0x3fefffffffffffffLL;
+        const double t = __longlong_as_double(tb);
+        v[d] = (lo + t) * inv_b;
+        if (!(marg && d == 5))
+            lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
+        packed |= (uint64_t)lo << (10 * d);
+    }
+}
+
+// The histogram draw's mapping v -> theta.
+__device__ __forceinline__ void hist_theta(const double v[6], double d3lo, double d3hi, double th[6])
+{
+    th[0] = 2.0 * kPi * v[0];
+    th[1] = asin(2.0 * v[1] - 1.0);
+    th[2] = kPi * v[2];
+    th[3] = 2.0 * kPi * v[3];
+    th[4] = acos(1.0 - 2.0 * v[4]);
+    th[5] = cbrt(d3lo + v[5] * (d3hi - d3lo));
+}
+
+// Draw i of AV iteration `iter`: Philox4x32-10 (key = seed, counter (i lo, i hi, iter, p),
+// p = 0..3); words 0,1 give the 53-bit integer U of the cell choice cells[floor(U n / 2^53)],
+// the next twelve the six in-cell uniforms.  v_d = (coordinate_d + u_d) 2^-level.
+__device__ __forceinline__ void av_draw_one(const uint64_t *__restrict__ cells, int64_t n_cells, int level,
+                                            uint32_t iter, int64_t i, uint32_t k0, uint32_t k1, double v[6])
+{
+    const uint64_t mask = level > 0 ? ((1ull << level) - 1ull) : 0ull;
+    uint32_t w[16];
+#pragma unroll
+    for (uint32_t p = 0; p < 4; ++p) {
+        const U4 r = philox10(U4{(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p}, k0, k1);
+        w[4 * p] = r.x;
+        w[4 * p + 1] = r.y;
+        w[4 * p + 2] = r.z;
+        w[4 * p + 3] = r.w;
+    }
+    const uint64_t U = ((uint64_t)(w[0] >> 5) << 26) | (uint64_t)(w[1] >> 6);
+    const uint64_t nc = (uint64_t)n_cells;
+    const uint64_t c = (__umul64hi(U, nc) << 11) | ((U * nc) >> 53);
+    const uint64_t cell = cells[c];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const double u = unit53(w[2 + 2 * d], w[3 + 2 * d]);
+        const double coord = (double)((cell >> (level * d)) & mask);
+        v[d] = ldexp(__dadd_rn(coord, u), -level);
+    }
+}
+
+// The AV draw's mapping v -> theta (every operation rounded as written).
+__device__ __forceinline__ void av_theta(const double v[6], double d3lo, double d3hi, double th[6])
+{
+    th[0] = __dmul_rn(2.0 * kPi, v[0]);
+    th[1] = asin(__dsub_rn(__dmul_rn(2.0, v[1]), 1.0));
+    th[2] = __dmul_rn(kPi, v[2]);
+    th[3] = __dmul_rn(2.0 * kPi, v[3]);
+    th[4] = acos(__dsub_rn(1.0, __dmul_rn(2.0, v[4])));
+    th[5] = cbrt(__dadd_rn(d3lo, __dmul_rn(v[5], __dsub_rn(d3hi, d3lo))));
+}
+
+// Key of the level-`level` cell holding v (coordinate d in bits [level d, level (d+1))).
+__device__ __forceinline__ uint64_t av_cell_key(const double v[6], int level)
+{
+    const double side = ldexp(1.0, level);
+    uint64_t k = 0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+        k |= (uint64_t)floor(__dmul_rn(v[d], side)) << (level * d);
+    return k;
+}
+
+}  // namespace rift

@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include "draws.cuh"
 #include "ile_handle.h"
 
 using namespace rift;
@@ -44,37 +45,14 @@ __global__ void av_draw_kernel(const uint64_t *__restrict__ cells, int64_t n_cel
                                double *__restrict__ theta, double *__restrict__ lnpw, double *__restrict__ v_out)
 {
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    const uint64_t mask = level > 0 ? ((1ull << level) - 1ull) : 0ull;
     const double d3lo = d_min * d_min * d_min, d3hi = d_max * d_max * d_max;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t w[16];
-#pragma unroll
-        for (uint32_t p = 0; p < 4; ++p) {
-            const U4 r = philox10(U4{(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p}, k0, k1);
-            w[4 * p] = r.x;
-            w[4 * p + 1] = r.y;
-            w[4 * p + 2] = r.z;
-            w[4 * p + 3] = r.w;
-        }
-        const uint64_t U = ((uint64_t)(w[0] >> 5) << 26) | (uint64_t)(w[1] >> 6);
-        const uint64_t nc = (uint64_t)n_cells;
-        const uint64_t c = (__umul64hi(U, nc) << 11) | ((U * nc) >> 53);
-        const uint64_t cell = cells[c];
         double v[6];
+        av_draw_one(cells, n_cells, level, iter, i, k0, k1, v);
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const double u = unit53(w[2 + 2 * d], w[3 + 2 * d]);
-            const double coord = (double)((cell >> (level * d)) & mask);
-            v[d] = ldexp(__dadd_rn(coord, u), -level);
+        for (int d = 0; d < 6; ++d)
             v_out[6 * i + d] = v[d];
-        }
-        double *th = theta + 6 * i;
-        th[0] = __dmul_rn(2.0 * kPi, v[0]);
-        th[1] = asin(__dsub_rn(__dmul_rn(2.0, v[1]), 1.0));
-        th[2] = __dmul_rn(kPi, v[2]);
-        th[3] = __dmul_rn(2.0 * kPi, v[3]);
-        th[4] = acos(__dsub_rn(1.0, __dmul_rn(2.0, v[4])));
-        th[5] = cbrt(__dadd_rn(d3lo, __dmul_rn(v[5], __dsub_rn(d3hi, d3lo))));
+        av_theta(v, d3lo, d3hi, theta + 6 * i);
         lnpw[i] = lnV;
     }
 }
@@ -245,6 +223,11 @@ int ceil_log2(int64_t n)
     return c;
 }
 
+}  // namespace
+
+namespace rift {
+namespace host {
+
 int av_alloc(rift_ile_t *h, int64_t cap)
 {
     auto &a = h->av;
@@ -279,6 +262,11 @@ int av_restart(rift_ile_t *h)
     CK(cudaMemsetAsync(a.cells, 0, sizeof(uint64_t), h->stream));
     return RIFT_OK;
 }
+
+}  // namespace host
+}  // namespace rift
+
+namespace {
 
 // Exclusive scan of flags[0..n] in place and the total (flags[n] after the scan).
 int scan_total(rift_ile_t *h, int64_t n, int64_t *total)
@@ -324,12 +312,25 @@ int av_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, double p
                      st, h->cfg.precision == RIFT_FP32));
     CK(mark(h, slot, 3));
     h->launches += 1 + sorted + 1 + 2;
+    return av_update(h, a.v_fresh, h->lnL, n, p_thr, n_min_star);
+}
+
+}  // namespace
+
+namespace rift {
+namespace host {
+
+int av_update(rift_ile_t *h, const double *v_fresh, const double *lnL_fresh, int64_t n, double p_thr,
+              int64_t n_min_star)
+{
+    auto &a = h->av;
+    cudaStream_t st = h->stream;
     // 3. live set
-    av_flags_kernel<<<grid1(n + 1), 256, 0, st>>>(h->lnL, n, a.has_thr, a.m, a.b, a.flags);
+    av_flags_kernel<<<grid1(n + 1), 256, 0, st>>>(lnL_fresh, n, a.has_thr, a.m, a.b, a.flags);
     int64_t passed = 0;
     RK(scan_total(h, n, &passed));
     const int64_t room = a.cap - a.n_live;
-    av_scatter_kernel<<<grid1(n), 256, 0, st>>>(a.v_fresh, h->lnL, n, a.has_thr, a.m, a.b, a.flags, a.n_live, room,
+    av_scatter_kernel<<<grid1(n), 256, 0, st>>>(v_fresh, lnL_fresh, n, a.has_thr, a.m, a.b, a.flags, a.n_live, room,
                                                 a.v, a.lnL);
     CK(cudaGetLastError());
     a.n_live += std::min(passed, room);
@@ -418,7 +419,8 @@ int av_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, double p
     return RIFT_OK;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace rift
 
 extern "C" {
 

@@ -108,6 +108,22 @@ struct rift_ile {
         uint32_t *count_part = nullptr, *count = nullptr;
         unsigned long long *maxbits = nullptr;
     } av;
+    // portfolio integrator state (allocated by the first rift_ile_portfolio call)
+    struct PortfolioState {
+        bool alloc = false;
+        uint8_t *member = nullptr;              // [max_samples] member that drew each sample
+        double *v = nullptr;                    // [max_samples][6] prior-CDF coordinates of the draws
+        double *v_av = nullptr, *lnL_av = nullptr;   // the AV member's draws, compacted
+        double *part = nullptr, *sums = nullptr;     // per-member weight sums: block partials, result
+        uint32_t iter = 0;                      // portfolio iterations since restart
+        bool have_w = false;
+        double W[2] = {0.0, 0.0};               // weights of the next batch
+        double W_last[2] = {0.0, 0.0};
+        double n_ess[2] = {0.0, 0.0};
+        int64_t n_drawn[2] = {0, 0};
+        int frozen[2] = {1, 1};
+        int active[2] = {0, 0};
+    } pf;
 };
 
 #define CK(call)                                                                                                        \
@@ -168,6 +184,13 @@ template <typename T> int dalloc(rift_ile_t *h, T **p, size_t count)
     return RIFT_OK;
 }
 constexpr int kScratchSlot = RIFT_MAX_ITER;
+
+// Adaptive-volume steps (ile_av.cu) shared with the portfolio integrator.
+int av_alloc(rift_ile_t *h, int64_t cap);
+int av_restart(rift_ile_t *h);
+// Steps 3-5 (live set, threshold, refinement) on n fresh points v [n][6] with their ln L,
+// in index order.
+int av_update(rift_ile_t *h, const double *v, const double *lnL, int64_t n, double p_thr, int64_t n_min_star);
 
 }  // namespace host
 }  // namespace rift

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "draws.cuh"
 #include "ile_kernels.h"
 
 namespace rift {
@@ -28,72 +29,16 @@ __global__ void __launch_bounds__(kDrawThreads) draw_kernel(SamplerDev S, SkyGri
                                                             uint32_t *__restrict__ key)
 {
     const uint32_t iter = *iter_base + iter_off;
-    // [6][B+1] running sums, then [6][B] reciprocal masses, [6][B] log densities (float64
-    // divisions once per block instead of per sample)
     extern __shared__ double sC[];
-    const int B = S.B;
-    double *sR = sC + 6 * (B + 1);
-    double *sL = sR + 6 * B;
-    for (int e = threadIdx.x; e < 6 * (B + 1); e += blockDim.x)
-        sC[e] = S.C[e];
-    for (int e = threadIdx.x; e < 6 * B; e += blockDim.x) {
-        sR[e] = 1.0 / S.P[e];
-        sL[e] = S.L[e];
-    }
+    hist_load_tables(S, sC);
     __syncthreads();
-    const double inv_b = 1.0 / B;
     const uint32_t k0 = (uint32_t)S.seed, k1 = (uint32_t)(S.seed >> 32);
     const double d3lo = S.d_min * S.d_min * S.d_min, d3hi = S.d_max * S.d_max * S.d_max;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        // the 53-bit integers m of the uniforms u = m 2^-53
-        double m53[6];
-#pragma unroll
-        for (uint32_t p = 0; p < 3; ++p) {
-            U4 r = philox10(U4{(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, p}, k0, k1);
-            m53[2 * p] = (double)bits53(r.x, r.y);
-            m53[2 * p + 1] = (double)bits53(r.z, r.w);
-        }
-        double v[6], lr = 0.0;
-        uint64_t packed = 0;
-#pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            const double *Cd = sC + d * (B + 1);
-            // x = u tot = m (2^-53 tot): both scalings by 2^-53 are exact, so this is the
-            // same single rounding as (m 2^-53) tot
-            const double x = m53[d] * (Cd[B] * 0x1.0p-53);
-            // last b in [0, B-1] with C[b] <= x (C[0] = 0 <= x always).  Non-negative doubles
-            // order like their bit patterns read as integers, so the search compares integers
-            // (float64 comparisons run on the slow float64 pipe of this part)
-            const long long xb = __double_as_longlong(x);
-            const long long *Cb = reinterpret_cast<const long long *>(Cd);
-            int lo = 0, hi = B - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (Cb[mid] <= xb)
-                    lo = mid;
-                else
-                    hi = mid - 1;
-            }
-            // t in [0, 1): negative or NaN -> 0, [1, inf] -> the largest double below 1,
-            // decided on the bit pattern (integer comparisons)
-            long long tb = __double_as_longlong((x - Cd[lo]) * sR[d * B + lo]);
-            if (tb < 0 || (tb & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL)
-                tb = 0;
-            else if (tb >= 0x3ff0000000000000LL)
-                tb = 0x3fefffffffffffffLL;
-            const double t = __longlong_as_double(tb);
-            v[d] = (lo + t) * inv_b;
-            if (!(S.marg && d == 5))
-                lr -= sL[d * B + lo];   // ln(B pb / tot), tabulated when the masses change
-            packed |= (uint64_t)lo << (10 * d);
-        }
-        double th[6];
-        th[0] = 2.0 * kPi * v[0];
-        th[1] = asin(2.0 * v[1] - 1.0);
-        th[2] = kPi * v[2];
-        th[3] = 2.0 * kPi * v[3];
-        th[4] = acos(1.0 - 2.0 * v[4]);
-        th[5] = cbrt(d3lo + v[5] * (d3hi - d3lo));
+        double v[6], lr, th[6];
+        uint64_t packed;
+        hist_draw_one(sC, S.B, S.marg, iter, i, k0, k1, v, lr, packed);
+        hist_theta(v, d3lo, d3hi, th);
         double *out = theta + 6 * i;
 #pragma unroll
         for (int d = 0; d < 6; ++d)
@@ -126,7 +71,7 @@ cudaError_t launch_draw(const SamplerDev &S, const SkyGrid &G, const uint32_t *i
 {
     if (n <= 0)
         return cudaSuccess;
-    size_t smem = sizeof(double) * (6 * (S.B + 1) + 12 * S.B);
+    size_t smem = sizeof(double) * hist_table_doubles(S.B);
     if (smem > 48 * 1024) {
         cudaError_t e = allow_max_dynamic_smem(draw_kernel);
         if (e != cudaSuccess)

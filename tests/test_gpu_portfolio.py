@@ -1,0 +1,150 @@
+"""Portfolio integrator (rift_ile_portfolio) against the oracle's step-by-step portfolio.
+
+With the float64 path every discrete decision (member choice, histogram bin, AV cell,
+live set, threshold, grid level, weight floor, freeze) is taken on values that agree with
+the oracle's to ~1e-10, so the state after every iteration is compared exactly, the draws
+to the last-bit differences of the inverse-CDF transcendentals, the weights, n_ESS and
+ln Z to 1e-9 relative in the first iteration.  Once the histogram masses are trained
+(they agree to ~1e-10) the histogram draws agree to 1e-6 and the weights to 1e-4, while
+the AV member's state stays exact, and every ln L and ln Z on the device's own draws meet
+the oracle to 1e-9.  The float32 path is held to the float32 bar (1e-3) on its own
+draws.  Single-member portfolios reproduce the library's own samplers exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ile_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2505_11655_gb300 as G
+    G.load(build_if_missing=True)
+    return G
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_lib):
+    return oracle_lib
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)) / np.maximum(1.0, np.abs(np.asarray(b)))))
+
+
+@pytest.mark.parametrize("problem,av_start", [("plain", 0), ("large", 0), ("large", 2)])
+def test_portfolio_fp64_matches_oracle_step_by_step(G, orc, problem, av_start):
+    from oracle import portfolio as PF
+    p = S.plain_fp64_problem() if problem == "plain" else S.single_large_problem()
+    n, iters, B = 20000, 6, 32
+    kw = dict(p_thr=0.999, n_min_star=300)
+    pf = PF.Portfolio(seed=13, n_bins=B, capacity=4 * n, av_start=av_start, w_init=(0.5, 0.5), d_min=p.d_min,
+                      d_max=p.d_max, **kw)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=B, seed=13) as s:
+        for g in range(iters):
+            r = s.portfolio(1, n, capacity=4 * n, av_start=av_start, restart=(g == 0), **kw)
+            info = s.portfolio_info()
+            av = s.av_info()
+            th, lr, ll, lw = s.last_batch(n)
+            rec = pf.step(lambda t, v: orc.lnL(p, t), n)
+            assert info["iteration"] == g + 1
+            if g < av_start:
+                assert info["n_drawn"] == [n, 0] and info["active"] == [1, 0]
+            assert info["n_drawn"] == rec["n_drawn"].tolist(), g
+            # before any training the two draw streams agree to the last bits; afterwards the
+            # histogram masses agree to ~1e-10 (weighted sums of a wide dynamic range in
+            # another order), which moves a histogram draw in a light bin by up to ~1e-7
+            first = g == 0
+            assert np.allclose(th, rec["theta"], rtol=1e-12 if first else 1e-6, atol=1e-12 if first else 1e-9), g
+            assert _rel(lr, rec["lr"]) < (1e-11 if first else 1e-6), g
+            assert np.allclose(info["W_last"], rec["W"], rtol=1e-12 if first else 1e-6, atol=1e-15), (g, info)
+            assert np.allclose(info["W_next"], rec["W_next"], rtol=1e-9 if first else 1e-4, atol=1e-12), (g, info)
+            assert np.allclose(info["n_ess"], rec["n_ess"], rtol=1e-9 if first else 1e-4, atol=1e-9), (g, info)
+            assert info["frozen"] == rec["frozen"].astype(int).tolist(), g
+            # the AV member learns from its own draws, which do not depend on the masses: exact
+            assert (av["level"], av["n_cells"], av["n_live"], av["V"]) == \
+                (pf.av.level, pf.av.cells.size, pf.av.live_lnL.size, pf.av.V), (g, av)
+            red = orc.reduce(rec["lnw"])
+            assert abs(r["lnZ"] - red["lnZ"]) <= (1e-9 if first else 1e-4) * max(1.0, abs(red["lnZ"])), g
+            # on the device's own draws: every ln L and the reduction to 1e-9
+            oll = orc.lnL(p, th)
+            assert _rel(ll, oll) < 1e-9, g
+            own = orc.reduce(oll + lr)
+            assert abs(r["lnZ"] - own["lnZ"]) <= 1e-9 * max(1.0, abs(own["lnZ"])), g
+            assert abs(r["n_ess"] - own["n_ess"]) <= 1e-9 * own["n_ess"], g
+    assert pf.av.level >= 1
+
+
+def test_portfolio_fp32_meets_oracle_on_its_draws(G, orc):
+    """Five float32 iterations on the single large problem: the weights stay normalised
+    and above 0.05/2, both members draw, and the last iteration's ln Z on the device's own
+    draws is within 1e-3 of the oracle's float64 reduction of those draws."""
+    p = S.single_large_problem()
+    n = 30000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, seed=17) as s:
+        for g in range(5):
+            r = s.portfolio(1, n, p_thr=0.999, n_min_star=500, restart=(g == 0))
+            info = s.portfolio_info()
+            assert abs(sum(info["W_next"]) - 1.0) < 1e-12 and min(info["W_next"]) >= 0.025 - 1e-15
+            assert min(info["n_drawn"]) > 0 and sum(info["n_drawn"]) == n
+        th, lr, ll, lw = s.last_batch(n)
+    oll = orc.lnL(p, th)
+    assert np.max(np.abs(ll - oll)) <= 1e-3
+    red = orc.reduce(oll + lr)
+    assert abs(r["lnZ"] - red["lnZ"]) <= 1e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_single_member_portfolios_are_the_library_samplers(G, precision):
+    """Histogram alone reproduces rift_ile_adapt, AV alone rift_ile_av, iteration by
+    iteration (the same draws, weights and training)."""
+    p = S.single_large_problem()
+    prec = G.RIFT_FP64 if precision == "fp64" else G.RIFT_FP32
+    n, iters = 20000, 4
+    with G.ILE(p, precision=prec, max_samples=n, n_bins=32, seed=5) as s:
+        ra = s.adapt(iters, n)
+    with G.ILE(p, precision=prec, max_samples=n, n_bins=32, seed=5) as s:
+        rp = s.portfolio(iters, n, members=G.RIFT_MEMBER_HIST, restart=True)
+        info = s.portfolio_info()
+    assert rp["lnZ_iter"] == ra["lnZ_iter"] and rp["lnZ"] == ra["lnZ"]
+    assert info["n_drawn"] == [n, 0] and info["frozen"] == [0, 1]
+    with G.ILE(p, precision=prec, max_samples=n, seed=5) as s:
+        rv = s.av(iters, n, p_thr=0.999, n_min_star=300, capacity=4 * n, restart=True)
+        av1 = s.av_info()
+    with G.ILE(p, precision=prec, max_samples=n, seed=5) as s:
+        rq = s.portfolio(iters, n, members=G.RIFT_MEMBER_AV, p_thr=0.999, n_min_star=300, capacity=4 * n,
+                         restart=True)
+        av2 = s.av_info()
+    assert rq["lnZ_iter"] == rv["lnZ_iter"] and av1 == av2
+
+
+def test_portfolio_arguments(G):
+    p = S.plain_fp64_problem()
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=1000, seed=1) as s:
+        bad = [dict(members=0), dict(members=4), dict(members=G.RIFT_MEMBER_AV, av_start=1), dict(av_start=-1),
+               dict(w_init=(0.0, 1.0)), dict(w_init=(1.0, float("nan"))), dict(p_thr=0.0), dict(n_min_star=0),
+               dict(capacity=10), dict(n_per_iter=2000)]
+        for b in bad:
+            kw = dict(n_iter=1, n_per_iter=1000, capacity=4000)
+            kw.update(b)
+            with pytest.raises(G.RiftError) as e:
+                s.portfolio(**kw)
+            assert e.value.code == G.RIFT_EINVAL, b
+        s.portfolio(2, 1000, capacity=4000, restart=True)
+        with pytest.raises(G.RiftError) as e:
+            s.portfolio(1, 1000, capacity=8000)   # the AV capacity is fixed by the first call
+        assert e.value.code == G.RIFT_EINVAL
+        th, t, idx = s.fair_draws(100, seed=2)   # fair draws work on the portfolio's batch
+        assert th.shape == (100, 6)
+    pd = S.plain_fp64_problem()
+    with G.ILE(pd, precision=G.RIFT_FP64, max_samples=1000, seed=1, distance_marg=True) as s:
+        with pytest.raises(G.RiftError) as e:
+            s.portfolio(1, 1000, capacity=4000)
+        assert e.value.code == G.RIFT_EINVAL
