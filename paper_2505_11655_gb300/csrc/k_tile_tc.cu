@@ -759,10 +759,12 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     const float sc = invs[k * kTcS + gs];
                     if (k == 0) {
                         // this thread's bins of the chunk, shared by every detector (idle slots
-                        // re-read the chunk's last bin; one 8-byte broadcast load each)
+                        // re-read the quarter's last bin, so that they repeat its value, or a
+                        // valid bin when the quarter has none; one 8-byte broadcast load each)
+                        const int jl = jn > 0 ? jb + jn - 1 : min(jb, NT - 1);
 #pragma unroll
                         for (int i = 0; i < kTcBPT; ++i) {
-                            const int j = min(jb + i, j0 + J - 1);
+                            const int j = min(jb + i, jl);
                             const int2 bv = bins[j];
                             bj[i] = bv.x;
                             bfj[i] = __int_as_float(bv.y);
@@ -837,15 +839,16 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             // lin holds the data term; ln L = lin - gqd, the template term
                             // subtracted once per sample in the epilogue (in float64)
                             // (the maximum by blocks of kPeakBlockTc bins, the same number of
-                            // operations, so that the block holding it is known)
+                            // operations, so that the block holding it is known).  Idle slots
+                            // repeat the last bin's value: the maximum is that of the valid
+                            // bins, and the lowest block attaining it holds a valid bin.
                             float qm[kTcBPT / kPeakBlockTc];
 #pragma unroll
                             for (int a = 0; a < kTcBPT / kPeakBlockTc; ++a) {
-                                qm[a] = -INFINITY;
+                                qm[a] = lin[kPeakBlockTc * a];
 #pragma unroll
-                                for (int i = kPeakBlockTc * a; i < kPeakBlockTc * (a + 1); ++i)
-                                    if (i < jn)
-                                        qm[a] = fmaxf(qm[a], lin[i]);
+                                for (int i = kPeakBlockTc * a + 1; i < kPeakBlockTc * (a + 1); ++i)
+                                    qm[a] = fmaxf(qm[a], lin[i]);
                             }
                             const float m01 = fmaxf(qm[0], qm[1]), m23 = fmaxf(qm[2], qm[3]);
                             cmx = fmaxf(m01, m23);
