@@ -144,3 +144,34 @@ def test_tuner_appends_new_classes_to_cache_file(G, monkeypatch, tmp_path):
     assert len(lines) == 4 and lines[0].startswith("K1_kp1_nt333_")
     assert int(lines[1]) == (1 if k == G.RIFT_KERNEL_TENSOR else 0) and int(lines[2]) == cell
     assert lines[3] == "0"   # the three-delay key is a candidate only with three detectors
+
+
+@pytest.mark.slow
+def test_batched_workload_every_point_meets_oracle(G, orc):
+    """All 512 points of the batched uneven workload (sizes, detectors, modes, rates and
+    bin counts as the benchmark draws them; sample budgets capped at 2000 so that the
+    oracle check stays quick) as one float32 batch: every point's last-iteration ln Z
+    is within 1e-3 of the oracle's float64 reduction of that point's own last batch."""
+    pts = []
+    for i in range(512):
+        p, n = S.batched_problem(i)
+        pts.append((p, max(300, min(2000, n // 40))))
+    iters = [1 + i % 3 for i in range(len(pts))]
+    solves = [G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=32, seed=41 + i) for i, (p, n) in enumerate(pts)]
+    try:
+        with G.Batch(solves, iters, [n for _, n in pts]) as b:
+            res, rc = b.run()
+            assert rc == 0
+        last = [s.last_batch(n) for s, (_, n) in zip(solves, pts)]
+    finally:
+        for s in solves:
+            s.close()
+    worst = 0.0
+    for i, (p, n) in enumerate(pts):
+        assert res[i]["status"] == 0 and res[i]["n_total"] == iters[i] * n
+        th, lr, ll, lw = last[i]
+        red = orc.reduce(orc.lnL(p, th) + lr)
+        d = abs(res[i]["lnZ_iter"][-1] - red["lnZ"])
+        worst = max(worst, d)
+        assert d <= 1e-3, (i, res[i]["lnZ_iter"][-1], red["lnZ"])
+    print("max |d lnZ| over 512 points:", worst)

@@ -84,3 +84,30 @@ def test_oversize_request_refused(G):
             srv.submit(p, 1, 1_000_000, 0)
         assert e.value.code == G.RIFT_ENOMEM
         assert srv.pending() == (0, 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_served_results_meet_oracle(G, oracle_lib, precision):
+    """Each served request (in a mix with filler solves) gives exactly what the same
+    solve gives on its own handle through rift_ile_adapt, and that solve's last batch
+    meets the oracle: ln Z of the last iteration within 1e-9 (float64) or 1e-3 (float32)
+    of the oracle's float64 reduction of the same samples."""
+    orc = oracle_lib
+    prec = G.RIFT_FP64 if precision == "fp64" else G.RIFT_FP32
+    reqs = requests()
+    with G.Server(hbm_budget_bytes=8 << 30, max_slots=4) as srv:
+        filler = S.plain_fp64_problem()
+        for k, (tag, p, n) in enumerate(reqs):
+            srv.submit(filler, 1, 20000, 1000 + k, precision=prec, seed=7 + k)
+            srv.submit(p, 2, n, tag, precision=prec, seed=300 + tag)
+        got = {c["tag"]: c for c in srv.drain(2 * len(reqs))}
+    for tag, p, n in reqs:
+        c = got[tag]
+        assert c["status"] == 0
+        with G.ILE(p, precision=prec, max_samples=n, n_bins=64, seed=300 + tag) as s:
+            r = s.adapt(2, n)
+            th, lr, ll, lw = s.last_batch(n)
+        assert r["lnZ_iter"] == c["lnZ_iter"] and r["lnZ"] == c["lnZ"], (tag, r["lnZ_iter"], c["lnZ_iter"])
+        red = orc.reduce(orc.lnL(p, th) + lr)
+        tol = 1e-9 * max(1.0, abs(red["lnZ"])) if precision == "fp64" else 1e-3
+        assert abs(c["lnZ_iter"][-1] - red["lnZ"]) <= tol, (tag, c["lnZ_iter"][-1], red["lnZ"])
