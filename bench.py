@@ -60,6 +60,7 @@ N_SAMPLES = 1_000_000
 TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", f) for f in ("k_tile_tc.cu", "k_fixup.cu")]
 TRAFFIC_BY_SOURCE = {
     "3e98ac2b2f6e30de16cf5dde8c8e0c1c184a69bbe778eea4e7a9c189816e4061": 5.98e7,
+    "02d8362c4117749bf193a68eea6c4ee9c70af5751d9d82631086b1437d6f8777": 5.97e7,
 }
 
 
