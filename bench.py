@@ -107,7 +107,8 @@ def unit_peaks(G):
     microbenchmarks (rift_ile_peak_rate) before the timed region."""
     out = {}
     for name, what in (("fp32_fma_tflops", G.RIFT_PEAK_FP32_FMA), ("tc_f16_n128_tflops", G.RIFT_PEAK_TC_F16_N128),
-                       ("tc_f16_n256_tflops", G.RIFT_PEAK_TC_F16_N256)):
+                       ("tc_f16_n256_tflops", G.RIFT_PEAK_TC_F16_N256), ("ex2_tops", G.RIFT_PEAK_EX2),
+                       ("fp64_fma_tflops", G.RIFT_PEAK_FP64_FMA)):
         try:
             out[name] = G.rift_ile_peak_rate(what)
         except Exception as e:   # a failed measurement is reported, not hidden
@@ -184,8 +185,17 @@ def cpu_baseline(prob, budget_s=12.0):
     t_small = step(500, 0)
     n = int(max(500, min(2_000_000, 500 * budget_s / max(t_small, 1e-6))))
     dt = step(n, 1)
+    # the plain configuration (2 detectors, 2 modes, 401 bins) in full: 1e4 samples
+    P1 = oracle.Problem(S.plain_fp64_problem())
+    sm1 = oracle.Sampler(n_bins=64, seed=1)
+    t0 = time.perf_counter()
+    th1, lr1, bins1 = sm1.draw(10000)
+    oracle.reduce(oracle.lnL(P1, th1) + lr1)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{n} samples of the same workload (one draw+lnL+reduce+adapt pass), {dt:.1f} s"}
+            "sample": f"{n} samples of the same workload (one draw+lnL+reduce+adapt pass), {dt:.1f} s",
+            "plain_config_full": {"value": 10000 / dt1, "unit": UNIT,
+                                  "sample": f"10000 samples of the plain configuration, {dt1:.2f} s"}}
 
 
 def emit(obj):
@@ -445,6 +455,11 @@ def run_ours(args, rank, world, local_rank):
             out["roofline"]["algorithmic_vs_fp32_fma"] = achieved / up["fp32_fma_tflops"]
         if up.get("tc_f16_n128_tflops"):
             out["roofline"]["frac_vs_tc_f16_n128_measured"] = achieved / up["tc_f16_n128_tflops"]
+        if up.get("ex2_tops"):
+            # one exponential per bin in the time marginal (the method's ex2 count)
+            ex2_rate = prob.n_t * n / (lnl_avg / 1e3) / 1e12
+            out["roofline"]["ex2_tops_achieved"] = ex2_rate
+            out["roofline"]["frac_vs_ex2_measured"] = ex2_rate / up["ex2_tops"]
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         out["cpu_baseline"] = cpu_baseline(prob)
     ile.close()

@@ -409,8 +409,11 @@ int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, dou
  *   RIFT_PEAK_FP32_FMA     float32 FMA (2 flop), independent chains on every SM;
  *   RIFT_PEAK_TC_F16_N128  tcgen05.mma kind::f16, M = 128, N = 128, K = 16, A in tensor
  *                          memory, float32 accumulation (the likelihood kernel's shape);
- *   RIFT_PEAK_TC_F16_N256  the same with N = 256.
- * One CTA per SM; the tensor-core runs allocate 512 tensor-memory columns per SM, so run
+ *   RIFT_PEAK_TC_F16_N256  the same with N = 256;
+ *   RIFT_PEAK_EX2          ex2.approx.ftz.f32 on the special-function unit, in tera
+ *                          operations per second (one exponential counts as one);
+ *   RIFT_PEAK_FP64_FMA     float64 FMA (2 flop), independent chains on every SM.
+ * The tensor-core runs use one CTA per SM; the tensor-core runs allocate 512 tensor-memory columns per SM, so run
  * them on an otherwise idle device.  Allocates and frees its own small buffers and stream.
  * RIFT_EINVAL for an unknown `what` or a tensor-core rate on a device outside the sm_100
  * family, RIFT_ETIMEOUT if the MMAs did not complete within 2 s, RIFT_ECUDA on a CUDA
@@ -418,6 +421,8 @@ int rift_ile_reduce_noalloc(const double *lnw, const double *lnL, int64_t n, dou
 #define RIFT_PEAK_FP32_FMA 0
 #define RIFT_PEAK_TC_F16_N128 1
 #define RIFT_PEAK_TC_F16_N256 2
+#define RIFT_PEAK_EX2 3
+#define RIFT_PEAK_FP64_FMA 4
 int rift_ile_peak_rate(int32_t what, double *tflops);
 
 void rift_ile_destroy(rift_ile_t *h);

@@ -315,11 +315,12 @@ def rift_ile_wait_selftest(h, limit_ns):
     return int(load().rift_ile_wait_selftest(h, int(limit_ns)))
 
 
-RIFT_PEAK_FP32_FMA, RIFT_PEAK_TC_F16_N128, RIFT_PEAK_TC_F16_N256 = 0, 1, 2
+RIFT_PEAK_FP32_FMA, RIFT_PEAK_TC_F16_N128, RIFT_PEAK_TC_F16_N256, RIFT_PEAK_EX2, RIFT_PEAK_FP64_FMA = 0, 1, 2, 3, 4
 
 
 def rift_ile_peak_rate(what):
-    """Measured peak rate (TFLOP/s) of the float32 FMA pipe or of tcgen05 kind::f16 MMAs."""
+    """Measured peak rate (tera-operations/s) of a unit: RIFT_PEAK_FP32_FMA, _TC_F16_N128,
+    _TC_F16_N256, _EX2 (exponentials/s) or _FP64_FMA."""
     v = C.c_double()
     _check(load().rift_ile_peak_rate(int(what), C.byref(v)), "rift_ile_peak_rate")
     return v.value

@@ -1,6 +1,7 @@
 // Peak-rate microbenchmarks of the units the likelihood kernels use (rift_ile_peak_rate):
-// the float32 FMA pipe and the tcgen05 kind::f16 tensor-core MMA with the A operand in
-// tensor memory (the form the tensor-core likelihood kernel issues).  Measured on the
+// the float32 FMA pipe, the special-function unit's ex2, the float64 FMA pipe, and the
+// tcgen05 kind::f16 tensor-core MMA with the A operand in tensor memory (the form the
+// tensor-core likelihood kernel issues).  Measured on the
 // device with CUDA events, so that roofline fractions are taken against this part's
 // measured rates rather than datasheet figures.
 #include <algorithm>
@@ -39,6 +40,54 @@ __global__ void __launch_bounds__(kFmaThreads) peak_fma_kernel(int iters, float 
     for (int c = 0; c < kFmaChains; ++c)
         s += a[c];
     if (s == -12345.f)
+        sink[threadIdx.x] = s;
+}
+
+// The same structure for the special-function unit: each chain is x <- 2^(x c), with c < 0
+// chosen so that the values stay in a normal range; and for the float64 FMA pipe.
+__global__ void __launch_bounds__(kFmaThreads) peak_ex2_kernel(int iters, float *sink)
+{
+    float a[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c)
+        a[c] = 1e-3f * (float)(threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll 16
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < kFmaChains; ++c) {
+                float y;
+                asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-a[c]));
+                a[c] = y;
+            }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c)
+        s += a[c];
+    if (s == -12345.f)
+        sink[threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kFmaThreads) peak_dfma_kernel(int iters, double *sink)
+{
+    double a[kFmaChains];
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c)
+        a[c] = 1e-3 * (double)(threadIdx.x + c);
+    const double b = 0.9999999, d = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll 16
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < kFmaChains; ++c)
+                a[c] = fma(a[c], b, d);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFmaChains; ++c)
+        s += a[c];
+    if (s == -12345.0)
         sink[threadIdx.x] = s;
 }
 
@@ -108,8 +157,9 @@ using namespace rift;
 
 extern "C" int rift_ile_peak_rate(int32_t what, double *tflops)
 {
-    if (!tflops || (what != RIFT_PEAK_FP32_FMA && what != RIFT_PEAK_TC_F16_N128 && what != RIFT_PEAK_TC_F16_N256))
+    if (!tflops || what < RIFT_PEAK_FP32_FMA || what > RIFT_PEAK_FP64_FMA)
         return RIFT_EINVAL;
+    const bool tc = what == RIFT_PEAK_TC_F16_N128 || what == RIFT_PEAK_TC_F16_N256;
     int dev = 0, sms = 0, major = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -117,7 +167,7 @@ extern "C" int rift_ile_peak_rate(int32_t what, double *tflops)
         cudaGetLastError();
         return RIFT_ECUDA;
     }
-    if (what != RIFT_PEAK_FP32_FMA && major != 10)
+    if (tc && major != 10)
         return RIFT_EINVAL;   // tcgen05 needs the sm_100 family
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -125,9 +175,9 @@ extern "C" int rift_ile_peak_rate(int32_t what, double *tflops)
     int *err = nullptr;
     int rc = RIFT_OK;
     double best = 0.0;
-    if ((what != RIFT_PEAK_FP32_FMA && allow_max_dynamic_smem(peak_tc_kernel) != cudaSuccess) ||
+    if ((tc && allow_max_dynamic_smem(peak_tc_kernel) != cudaSuccess) ||
         cudaStreamCreate(&st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-        cudaEventCreate(&e1) != cudaSuccess || cudaMallocAsync(&sink, 4 * kFmaThreads, st) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess || cudaMallocAsync(&sink, 8 * kFmaThreads, st) != cudaSuccess ||
         cudaMallocAsync(&err, sizeof(int), st) != cudaSuccess || cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) {
         rc = RIFT_ECUDA;
     } else {
@@ -139,6 +189,16 @@ extern "C" int rift_ile_peak_rate(int32_t what, double *tflops)
                 const int iters = 4096;
                 const int blocks = sms * kFmaBlocksPerSm;
                 peak_fma_kernel<<<blocks, kFmaThreads, 0, st>>>(iters, sink);
+                flop = 2.0 * kFmaChains * 16.0 * iters * (double)blocks * kFmaThreads;
+            } else if (what == RIFT_PEAK_EX2) {
+                const int iters = 1024;
+                const int blocks = sms * kFmaBlocksPerSm;
+                peak_ex2_kernel<<<blocks, kFmaThreads, 0, st>>>(iters, sink);
+                flop = kFmaChains * 16.0 * iters * (double)blocks * kFmaThreads;   // exponentials
+            } else if (what == RIFT_PEAK_FP64_FMA) {
+                const int iters = 64;
+                const int blocks = sms * kFmaBlocksPerSm;
+                peak_dfma_kernel<<<blocks, kFmaThreads, 0, st>>>(iters, reinterpret_cast<double *>(sink));
                 flop = 2.0 * kFmaChains * 16.0 * iters * (double)blocks * kFmaThreads;
             } else {
                 const int n_cols = what == RIFT_PEAK_TC_F16_N128 ? 128 : 256;
