@@ -391,8 +391,7 @@ int64_t rift_ile_kernel_launches(const rift_ile_t *h);
  * GPU that loads the library until the process exits; nothing is allocated per
  * call (no cudaMalloc, cudaFree or allocating library routine).  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current) and caches it: make that first call on a device before any stream
- * capture begins there.
+ * device current) and caches it.
  * All calls share the one array, which keeps the last call's contents; the error
  * word is cleared by each call.  Calls that overlap on the GPU (different streams
  * or threads at the same time) race on the array and must be serialised by the
