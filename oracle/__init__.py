@@ -74,8 +74,12 @@ def lib():
             L.orc_uniforms.argtypes = [C.c_uint64, C.c_uint32, i64, vp]
             L.orc_uniforms.restype = None
             L.orc_draw.argtypes = [vp, C.c_int, C.c_uint64, C.c_uint32, i64, i64, dbl, dbl, C.c_int, vp, vp, vp, vp]
-            L.orc_portfolio_members.argtypes = [C.c_uint64, C.c_uint32, i64, dbl, vp]
+            L.orc_portfolio_members.argtypes = [C.c_uint64, C.c_uint32, i64, dbl, dbl, vp]
             L.orc_portfolio_members.restype = None
+            L.orc_ndtri.argtypes = [dbl]
+            L.orc_ndtri.restype = dbl
+            L.orc_gmm_draw.argtypes = [vp, vp, vp, C.c_int, C.c_uint64, C.c_uint32, i64, dbl, dbl, vp, vp, vp]
+            L.orc_gmm_draw.restype = None
             L.orc_draw.restype = None
             L.orc_adapt.argtypes = [vp, C.c_int, vp, vp, i64, dbl, dbl, C.c_int]
             L.orc_adapt.restype = None

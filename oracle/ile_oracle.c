@@ -592,11 +592,12 @@ void orc_av_draw(const uint64_t *cells, int64_t n_cells, int level, uint64_t see
 /* ---------------------------------------------------------------- portfolio member choice */
 
 /* The portfolio integrator (Sec. IV, "Portfolio integrator") draws each sample from one
- * member, member 0 with probability W0 (the weights normalised to sum 1).  Draw i of
- * portfolio iteration `iter` uses Philox4x32-10 with key = seed and counter
- * (i low, i high, iter, 7): words (0,1) give the 53-bit integer U, and the sample comes
- * from member 0 when U 2^-53 < W0 (exact in double precision), else member 1. */
-void orc_portfolio_members(uint64_t seed, uint32_t iter, int64_t n, double w0, int32_t *member)
+ * member, with the members' weights normalised to sum 1.  Draw i of portfolio iteration
+ * `iter` uses Philox4x32-10 with key = seed and counter (i low, i high, iter, 7): words
+ * (0,1) give the 53-bit integer U, and with x = U 2^-53 the sample comes from member 0
+ * when x < t0, from member 1 when t0 <= x < t1, else from member 2 (t0 = W0, t1 = W0 + W1,
+ * or a value above 1 when member 2 is not active; exact comparisons in double precision). */
+void orc_portfolio_members(uint64_t seed, uint32_t iter, int64_t n, double t0, double t1, int32_t *member)
 {
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
 #pragma omp parallel for schedule(static)
@@ -604,7 +605,99 @@ void orc_portfolio_members(uint64_t seed, uint32_t iter, int64_t n, double w0, i
         const uint32_t ctr[4] = {(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, 7u};
         uint32_t r[4];
         orc_philox4x32_10(ctr, key, r);
-        member[i] = orc_u53(r[0], r[1]) < w0 ? 0 : 1;
+        const double x = orc_u53(r[0], r[1]);
+        member[i] = x < t0 ? 0 : (x < t1 ? 1 : 2);
+    }
+}
+
+/* ---------------------------------------------------------------- Gaussian-mixture draws */
+
+/* Standard normal CDF and its inverse.  The inverse refines a starting value by Newton's
+ * method on Phi (Phi' = the normal density), taking the smaller tail so that the relative
+ * precision of p is kept: x with Phi(x) = p to ~1 ulp in a handful of steps. */
+static double orc_phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+double orc_ndtri(double p)
+{
+    if (!(p > 0.0))
+        return -INFINITY;
+    if (!(p < 1.0))
+        return INFINITY;
+    const int upper = p > 0.5;
+    const double q = upper ? 1.0 - p : p;   /* exact for p > 0.5 */
+    /* x < 0 with Phi(x) = q: start from the tail asymptote, then Newton on Phi */
+    double x = -sqrt(-2.0 * log(q));   /* the tail asymptote (below the root) */
+    for (int it = 0; it < 100; ++it) {
+        const double f = orc_phi(x) - q;
+        const double d = exp(-0.5 * x * x) / sqrt(2.0 * ORC_PI);
+        if (!(d > 0.0))
+            break;
+        const double step = f / d;
+        x -= step;
+        if (fabs(step) <= 1e-16 * fmax(1.0, fabs(x)))
+            break;
+    }
+    return upper ? -x : x;
+}
+
+/* Draws of the Gaussian-mixture sampling prior on the unit cube of prior-CDF coordinates:
+ * C components with weights pi[c], per-dimension means mu[c][d] in [0, 1] and widths
+ * sig[c][d] (diagonal covariances), each dimension truncated to [0, 1].  Draw i of
+ * iteration `iter`: Philox4x32-10 with key = seed and counter (i low, i high, iter, p);
+ * p = 8: words (0,1) give the 53-bit U of the component, the first c with
+ * U 2^-53 < pi[0] + ... + pi[c] (pi normalised to sum 1, the last component otherwise);
+ * p = 9, 10, 11: word pairs (0,1), (2,3) give the six uniforms u_d, and
+ * v_d = mu + sig Phi^-1(Phi(a) + u_d (Phi(b) - Phi(a))), a = -mu/sig, b = (1 - mu)/sig,
+ * kept in [0, 1).  theta follows from v as for the histogram sampler. */
+void orc_gmm_draw(const double *pi, const double *mu, const double *sig, int C, uint64_t seed, uint32_t iter,
+                  int64_t n, double d_min, double d_max, double *theta, double *v_out, int32_t *comp)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    double tot = 0.0;
+    for (int c = 0; c < C; ++c)
+        tot += pi[c];
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t r[4];
+        uint32_t ctr[4] = {(uint32_t)(uint64_t)i, (uint32_t)((uint64_t)i >> 32), iter, 8u};
+        orc_philox4x32_10(ctr, key, r);
+        const double U = orc_u53(r[0], r[1]);
+        int c = C - 1;
+        double run = 0.0;
+        for (int k = 0; k < C - 1; ++k) {
+            run += pi[k] / tot;
+            if (U < run) {
+                c = k;
+                break;
+            }
+        }
+        double u[6], v[6];
+        for (uint32_t p = 0; p < 3; ++p) {
+            ctr[3] = 9u + p;
+            orc_philox4x32_10(ctr, key, r);
+            u[2 * p] = orc_u53(r[0], r[1]);
+            u[2 * p + 1] = orc_u53(r[2], r[3]);
+        }
+        for (int d = 0; d < 6; ++d) {
+            const double m = mu[c * 6 + d], s = sig[c * 6 + d];
+            const double pa = orc_phi(-m / s), pb = orc_phi((1.0 - m) / s);
+            double x = m + s * orc_ndtri(pa + u[d] * (pb - pa));
+            if (!(x >= 0.0))
+                x = 0.0;
+            if (x >= 1.0)
+                x = nextafter(1.0, 0.0);
+            v[d] = x;
+        }
+        double *th = theta + 6 * i;
+        th[0] = 2.0 * ORC_PI * v[0];
+        th[1] = asin(2.0 * v[1] - 1.0);
+        th[2] = ORC_PI * v[2];
+        th[3] = 2.0 * ORC_PI * v[3];
+        th[4] = acos(1.0 - 2.0 * v[4]);
+        th[5] = cbrt(d_min * d_min * d_min + v[5] * (d_max * d_max * d_max - d_min * d_min * d_min));
+        for (int d = 0; d < 6; ++d)
+            v_out[6 * i + d] = v[d];
+        comp[i] = c;
     }
 }
 

@@ -50,14 +50,14 @@ def test_member_choice_follows_the_weight(oracle_lib):
     m = {}
     for g, w0 in ((0, 0.3), (1, 0.3), (2, 0.9)):
         m[g] = np.empty(n, np.int32)
-        lib().orc_portfolio_members(11, g, n, w0, _p(m[g]))
+        lib().orc_portfolio_members(11, g, n, w0, 2.0, _p(m[g]))
         frac = float(np.mean(m[g] == 0))
         assert abs(frac - w0) < 5 * math.sqrt(w0 * (1 - w0) / n)
     agree = float(np.mean(m[0] == m[1]))
     assert abs(agree - (0.3 ** 2 + 0.7 ** 2)) < 5 * math.sqrt(0.25 / n)
     # W = 1 and W = 0 are exact
-    lib().orc_portfolio_members(11, 3, n, 1.0, _p(m[0]))
-    lib().orc_portfolio_members(11, 3, n, 0.0, _p(m[1]))
+    lib().orc_portfolio_members(11, 3, n, 1.0, 2.0, _p(m[0]))
+    lib().orc_portfolio_members(11, 3, n, 0.0, 2.0, _p(m[1]))
     assert np.all(m[0] == 0) and np.all(m[1] == 1)
 
 
@@ -185,8 +185,8 @@ def test_three_gaussian_mixture_lnZ(oracle_lib, PF):
     late = PF.reduce(np.concatenate([it["lnw"] for it in res["iterations"][-4:]]))
     assert abs(late["lnZ"] - truth) < 4 * late["sigma_lnZ"] and late["n_eff"] > 100, (late, truth)
     for it in res["iterations"]:
-        W = it["W"]
-        assert abs(W.sum() - 1) < 1e-14 and W.min() >= 0.025 - 1e-15
+        W = it["W"][:2]   # the two active members
+        assert abs(W.sum() - 1) < 1e-14 and W.min() >= 0.025 - 1e-15 and it["W"][2] == 0.0
         k = it["n_drawn"][0]
         assert abs(k - 20000 * W[0]) < 6 * math.sqrt(20000 * W[0] * W[1])
     # the weights moved away from the initial (1/2, 1/2)
@@ -201,13 +201,13 @@ def test_freeze_rule_below_five_percent(oracle_lib, PF):
     P0 = pf.hist.P.copy()
     for _ in range(3):
         rec = pf.step(_peak, 20000)
-        assert rec["frozen"].tolist() == [False, True] and rec["n_drawn"][1] > 0
+        assert rec["frozen"].tolist() == [False, True, True] and rec["n_drawn"][1] > 0
     assert (pf.av.level, pf.av.cells.size, pf.av.V, pf.av.live_lnL.size) == (0, 1, 1.0, 0)
     assert not np.array_equal(pf.hist.P, P0)
     pf = PF.Portfolio(adapt_weights=False, w_init=(0.03, 0.97), seed=4, n_min_star=100)
     for _ in range(3):
         rec = pf.step(_peak, 20000)
-        assert rec["frozen"].tolist() == [True, False]
+        assert rec["frozen"].tolist() == [True, False, True]
     assert np.array_equal(pf.hist.P, np.full((6, 64), 1.0 / 64)) and pf.av.level >= 1
 
 
@@ -216,8 +216,8 @@ def test_av_member_joins_at_its_start_iteration(oracle_lib, PF):
     for g in range(4):
         rec = pf.step(_peak, 10000)
         if g < 2:
-            assert np.all(rec["member"] == 0) and rec["W"].tolist() == [1.0, 0.0]
+            assert np.all(rec["member"] == 0) and rec["W"].tolist() == [1.0, 0.0, 0.0]
             assert rec["frozen"][1] and pf.av.level == 0
         elif g == 2:
-            assert np.allclose(rec["W"], [0.4, 0.6], rtol=0, atol=1e-15)
+            assert np.allclose(rec["W"], [0.4, 0.6, 0.0], rtol=0, atol=1e-15)
             assert 0 < rec["n_drawn"][0] < 10000
