@@ -395,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
                 dml.append(rd["time_ms"][1])
         dm = {"sample_evals_per_s": n / (statistics.mean(dms) / 1e3), "ms_per_step": statistics.mean(dms),
               "lnl_kernel_ms": statistics.mean(dml), "lnZ": rd["lnZ"], "n_eff": rd["n_eff"],
-              "quadrature": "per bin: 3 panels x 8 Gauss-Legendre nodes in ln x (float32)"}
+              "quadrature": "per bin: 2 panels x 10 Gauss-Legendre nodes in ln x (float32)"}
     # the portfolio sampling prior (histogram + AV mixture) on the same problem and batch:
     # per-iteration cost against the histogram sampler's step above
     pfo = None

@@ -94,7 +94,7 @@ typedef struct rift_ile rift_ile_t;
  *                             data and template terms at D = D_ref), and each bin's value is
  *                             ln int p(D) e^{a x - b x^2} dD with p(D) = 3 D^2/(D_max^3 - D_min^3)
  *                             on [d_min, d_max], by Gauss-Legendre quadrature in ln x over the
- *                             range where the exponent is within 24 (float32: 3 panels of 8
+ *                             range where the exponent is within 18 (float32: 2 panels of 10
  *                             nodes) or 44 (float64: 4 panels of 16) of its maximum; the
  *                             sampler's distance coordinate then carries no weight and keeps
  *                             its masses (theta[5] of the draws is not used).  The paper only

@@ -602,11 +602,14 @@ int rift_ile_create(const rift_ile_config *cfg, void *cuda_stream, rift_ile_t **
                          cfg->d_min_mpc * cfg->d_min_mpc * cfg->d_min_mpc));
     P.dm_lnub = P.dm_lnC + std::log((1.0 / (P.dm_xlo * P.dm_xlo * P.dm_xlo) -
                                      1.0 / (P.dm_xhi * P.dm_xhi * P.dm_xhi)) / 3.0);
-    gauss_legendre(8, P.gl8_t, P.gl8_w);
     gauss_legendre(16, P.gl16_t, P.gl16_w);
-    for (int i = 0; i < 8; ++i) {
-        P.gl8_tf[i] = (float)P.gl8_t[i];
-        P.gl8_wf[i] = (float)P.gl8_w[i];
+    {
+        double t10[10], w10[10];
+        gauss_legendre(10, t10, w10);
+        for (int i = 0; i < 10; ++i) {
+            P.gl10_tf[i] = (float)t10[i];
+            P.gl10_wf[i] = (float)w10[i];
+        }
     }
     P.dm_xlo_f = (float)P.dm_xlo;
     P.dm_xhi_f = (float)P.dm_xhi;

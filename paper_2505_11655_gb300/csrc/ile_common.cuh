@@ -38,9 +38,9 @@ struct Problem {
     int dist_marg;
     double dm_xlo, dm_xhi, dm_lnC;
     double dm_lnub;   // dm_lnC + ln((dm_xlo^-3 - dm_xhi^-3) / 3): upper bound offset of the marginal
-    double gl8_t[8], gl8_w[8], gl16_t[16], gl16_w[16];
-    // float copies for the float32 quadrature (no float64 conversions in the kernels)
-    float gl8_tf[8], gl8_wf[8];
+    double gl16_t[16], gl16_w[16];
+    // the float32 quadrature's 10-node rule, as floats (no float64 conversions in the kernels)
+    float gl10_tf[10], gl10_wf[10];
     float dm_xlo_f, dm_xhi_f, dm_lnC_f, dm_lnub_f;
     double Dten[kMaxDet][6];   // response tensor: xx, yy, zz, xy, xz, yz
     float Dten_f[kMaxDet][6];  // float copy for the float32 response
@@ -389,7 +389,7 @@ __device__ __forceinline__ float dm_bound32(const Problem &P, float a, float b)
 
 __device__ __forceinline__ float ln_dist_marg32(const Problem &P, float a, float b)
 {
-    return ln_dist_marg<float, 8, 3>(P.gl8_tf, P.gl8_wf, P.dm_xlo_f, P.dm_xhi_f, P.dm_lnC_f, a, b, 24.f);
+    return ln_dist_marg<float, 10, 2>(P.gl10_tf, P.gl10_wf, P.dm_xlo_f, P.dm_xhi_f, P.dm_lnC_f, a, b, 18.f);
 }
 
 __device__ __forceinline__ double ln_dist_marg64(const Problem &P, double a, double b)

@@ -57,7 +57,7 @@ def test_portfolio_fp64_matches_oracle_step_by_step(G, orc, problem, av_start):
             assert info["iteration"] == g + 1
             if g < av_start:
                 assert info["n_drawn"] == [n, 0] and info["active"] == [1, 0]
-            assert info["n_drawn"] == rec["n_drawn"].tolist(), g
+            assert info["n_drawn"] == rec["n_drawn"][:2].tolist(), g
             # before any training the two draw streams agree to the last bits; afterwards the
             # histogram masses agree to ~1e-10 (weighted sums of a wide dynamic range in
             # another order), which moves a histogram draw in a light bin by up to ~1e-7
@@ -65,9 +65,9 @@ def test_portfolio_fp64_matches_oracle_step_by_step(G, orc, problem, av_start):
             assert np.allclose(th, rec["theta"], rtol=1e-12 if first else 1e-6, atol=1e-12 if first else 1e-9), g
             assert _rel(lr, rec["lr"]) < (1e-11 if first else 1e-6), g
             assert np.allclose(info["W_last"], rec["W"], rtol=1e-12 if first else 1e-6, atol=1e-15), (g, info)
-            assert np.allclose(info["W_next"], rec["W_next"], rtol=1e-9 if first else 1e-4, atol=1e-12), (g, info)
-            assert np.allclose(info["n_ess"], rec["n_ess"], rtol=1e-9 if first else 1e-4, atol=1e-9), (g, info)
-            assert info["frozen"] == rec["frozen"].astype(int).tolist(), g
+            assert np.allclose(info["W_next"], rec["W_next"][:2], rtol=1e-9 if first else 1e-4, atol=1e-12), (g, info)
+            assert np.allclose(info["n_ess"], rec["n_ess"][:2], rtol=1e-9 if first else 1e-4, atol=1e-9), (g, info)
+            assert info["frozen"] == rec["frozen"][:2].astype(int).tolist(), g
             # the AV member learns from its own draws, which do not depend on the masses: exact
             assert (av["level"], av["n_cells"], av["n_live"], av["V"]) == \
                 (pf.av.level, pf.av.cells.size, pf.av.live_lnL.size, pf.av.V), (g, av)
@@ -148,3 +148,26 @@ def test_portfolio_arguments(G):
         with pytest.raises(G.RiftError) as e:
             s.portfolio(1, 1000, capacity=4000)
         assert e.value.code == G.RIFT_EINVAL
+
+
+@pytest.mark.parametrize("n", [1, 7, 129, 4097])
+def test_portfolio_ragged_batches_match_oracle(G, orc, n):
+    """Batch sizes that leave partial blocks and warps everywhere (including a single
+    draw): three float64 iterations follow the oracle's portfolio (draws, weights, member
+    counts, ln Z)."""
+    from oracle import portfolio as PF
+    p = S.plain_fp64_problem()
+    kw = dict(p_thr=0.99, n_min_star=min(n, 50))
+    pf = PF.Portfolio(seed=23, n_bins=16, capacity=8 * n, d_min=p.d_min, d_max=p.d_max, **kw)
+    with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, n_bins=16, seed=23) as s:
+        for g in range(3):
+            r = s.portfolio(1, n, capacity=8 * n, restart=(g == 0), **kw)
+            info = s.portfolio_info()
+            th, lr, ll, lw = s.last_batch(n)
+            rec = pf.step(lambda t, v: orc.lnL(p, t), n)
+            assert info["n_drawn"] == rec["n_drawn"][:2].tolist(), (n, g)
+            first = g == 0
+            assert np.allclose(th, rec["theta"], rtol=1e-12 if first else 1e-6, atol=1e-12 if first else 1e-9), (n, g)
+            assert np.allclose(info["W_next"], rec["W_next"][:2], rtol=1e-9 if first else 1e-4, atol=1e-12), (n, g)
+            own = orc.reduce(orc.lnL(p, th) + lr)
+            assert abs(r["lnZ"] - own["lnZ"]) <= 1e-9 * max(1.0, abs(own["lnZ"])), (n, g)
