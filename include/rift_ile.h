@@ -261,46 +261,72 @@ int rift_ile_av(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, double p_thr,
 int rift_ile_av_info(const rift_ile_t *h, int32_t *level, int64_t *n_cells, int64_t *n_live, double *volume);
 
 /* Portfolio integrator (arXiv:2505.11655 Sec. IV, "Portfolio integrator"): the sampling
- * prior is the weighted average of its members' priors, p_s = sum_a W_a p_s,a / sum_a W_a,
- * here over the histogram sampler (member 0: rift_ile_adapt's, the handle's masses) and
- * the adaptive-volume integrator (member 1: rift_ile_av's, the handle's AV state).  Both
- * draw through the prior-CDF cube, where g_hist = prod_d B P_d[b_d] / sum_b P_d[b] and
- * g_AV = 1/V on the active cells (0 elsewhere) are their densities relative to the prior.
- * Portfolio iteration g (counted from the last restart), weights W (sum 1):
- *   1. draw i comes from member 0 when U 2^-53 < W_0, U the 53-bit integer of words 0,1 of
- *      Philox4x32-10 (key = seed, counter (i low, i high, g, 7)); member 0 then draws as
- *      rift_ile_adapt's iteration g would, member 1 as rift_ile_av's iteration g would;
- *   2. ln p - ln p_s = -ln(W_0 g_hist(v) + W_1 g_AV(v)) (the bin of an AV draw is
- *      floor(v_d B); with one member active, that member's own value);
+ * prior is the weighted average of its members' priors, p_s = sum_a W_a p_s,a with
+ * sum_a W_a = 1 over the active members, here over the histogram sampler (member 0:
+ * rift_ile_adapt's, the handle's masses), the adaptive-volume integrator (member 1:
+ * rift_ile_av's, the handle's AV state) and a Gaussian-mixture sampling prior (member 2:
+ * the GMM sampler Sec. II B names; its state is held by the handle).  All draw through the
+ * prior-CDF cube, where their densities relative to the prior are
+ *   g_hist(v) = prod_d B P_d[b_d] / sum_b P_d[b],   g_AV(v) = 1/V on the active cells (0
+ *   elsewhere),   g_GMM(v) = sum_c pi_c prod_d phi((v_d - mu_cd)/sig_cd) /
+ *   (sig_cd (Phi(b_cd) - Phi(a_cd))),  a = -mu/sig, b = (1 - mu)/sig
+ * (C components, diagonal covariances, each dimension truncated to [0, 1]; phi, Phi the
+ * standard normal density and CDF).  Portfolio iteration g (counted from the last restart):
+ *   1. with x = U 2^-53, U the 53-bit integer of words 0,1 of Philox4x32-10 (key = seed,
+ *      counter (i low, i high, g, 7)), draw i comes from member 0 when x < W_0, from member
+ *      1 when x < W_0 + W_1, else from member 2 (with one member active, from it); member 0
+ *      draws as rift_ile_adapt's iteration g would, member 1 as rift_ile_av's iteration g
+ *      would, member 2 with counters (i low, i high, g, 8..11): words 0,1 of counter 8 give
+ *      the uniform of the component, the first c whose running sum of pi / sum pi exceeds
+ *      it; the word pairs of counters 9..11 the six uniforms u_d, and
+ *      v_d = mu_cd + sig_cd Phi^-1(Phi(a_cd) + u_d (Phi(b_cd) - Phi(a_cd))) (kept in [0, 1));
+ *   2. ln p - ln p_s = -ln(sum over the active members of W_a g_a(v)) (the bin of another
+ *      member's draw is floor(v_d B)); with one member active, that member's own value;
  *   3. time-marginalised ln L, ln w, the iteration's record;
- *   4. weights (adapt_weights = 1, both members active): n_ESS,a = (sum w)^2 / sum w^2 over
- *      the batch's draws from member a; W' proportional to n_ESS; no weight below 0.05/N_s
- *      (N_s = 2): weights below are set to it, the other scaled to fill the rest;
+ *   4. weights (adapt_weights = 1, two or more members active): n_ESS,a = (sum w)^2 /
+ *      sum w^2 over the batch's draws from member a; W' proportional to n_ESS; no weight
+ *      below 0.05/N_s (N_s the active members): those below are set to it and the others
+ *      scaled to fill the rest, until none is below;
  *   5. training: a member whose new weight is below 0.05 is frozen (not trained); member 0
- *      adapts its masses on every sample of the batch (bins, ln w), member 1 updates its
+ *      adapts its masses on every sample of the batch (bins, ln w); member 1 updates its
  *      live set, threshold and grid (rift_ile_av steps 3-5) from its own draws in index
- *      order (none: not trained).
- *   cfg->members       RIFT_MEMBER_HIST | RIFT_MEMBER_AV (at least one)
- *   cfg->av_start      first iteration in which member 1 draws (before it member 0 alone,
- *                      W = (1, 0)); at av_start the weights restart from w_init; 0 when
- *                      member 1 is the only member
- *   cfg->adapt_weights 1: step 4; 0: the weights stay at w_init
- *   cfg->w_init[2]     initial weights, >= 0, normalised over the active members (an
- *                      active member's must be > 0 unless the other's is)
+ *      order (none: not trained); member 2 takes one weighted EM step on every sample:
+ *      omega_i = exp(ln w_i - max ln w), responsibilities r_ic proportional to pi_c g_c(v_i),
+ *      S_c = sum_i omega r_ic, S = sum_c S_c; pi_c <- 0.98 S_c / S + 0.02 / C,
+ *      mu_cd <- sum omega r v_d / S_c, sig_cd^2 <- sum omega r v_d^2 / S_c - mu_cd^2, mu kept
+ *      in [0, 1] and sig in [1e-3, 1]; a component with S_c <= 1e-300 S keeps its mu and
+ *      sig; nothing changes when no ln w is finite.
+ *   cfg->members        RIFT_MEMBER_HIST | RIFT_MEMBER_AV | RIFT_MEMBER_GMM; at least one
+ *                       member active in iteration 0
+ *   cfg->av_start       first iteration in which member 1 draws; when it joins at
+ *                       av_start > 0 the weights restart from w_init
+ *   cfg->gmm_start      the same for member 2
+ *   cfg->gmm_components C of member 2, 1..RIFT_GMM_MAX_COMPONENTS; its initial state is
+ *                       pi_c = 1/C, sig = 0.25, mu_cd = frac((c + 1/2) frac(sqrt(p_d))) with
+ *                       p_d = 2, 3, 5, 7, 11, 13
+ *   cfg->adapt_weights  1: step 4; 0: the weights stay at w_init
+ *   cfg->w_init[3]      initial weights, finite and > 0 for every member (normalised over
+ *                       the active members)
  *   cfg->p_thr, n_min_star, capacity   member 1's settings, as for rift_ile_av (the
- *                      capacity is fixed by the first rift_ile_av or portfolio call)
+ *                       capacity is fixed by the first rift_ile_av or portfolio call)
  * restart = 1 (or the first call): weights from w_init, iteration 0, uniform histogram
- * masses, the AV member on the whole cube.  Results pool the call's iterations like
- * rift_ile_adapt; the last iteration's draws are the handle's most recent batch.  Not
- * with distance_marg.  RIFT_EINVAL for bad arguments (as rift_ile_av, and the above). */
+ * masses, the AV member on the whole cube, the GMM at its initial state; without a restart
+ * the members and C must be those of the calls since the last one (else RIFT_EINVAL).
+ * Results pool the call's iterations like rift_ile_adapt; the last iteration's draws are
+ * the handle's most recent batch.  Not with distance_marg.  RIFT_EINVAL for bad arguments
+ * (as rift_ile_av, and the above). */
 #define RIFT_MEMBER_HIST 1
 #define RIFT_MEMBER_AV 2
+#define RIFT_MEMBER_GMM 4
+#define RIFT_GMM_MAX_COMPONENTS 16
 typedef struct {
     int32_t members;
     int32_t av_start;
+    int32_t gmm_start;
+    int32_t gmm_components;
     int32_t adapt_weights;
     int32_t reserved;
-    double w_init[2];
+    double w_init[3];
     double p_thr;
     int64_t n_min_star;
     int64_t capacity;
@@ -310,18 +336,25 @@ int rift_ile_portfolio(rift_ile_t *h, int32_t n_iter, int64_t n_per_iter, const 
 /* State after the last portfolio iteration: iterations since restart, the weights the
  * last batch was drawn with and those of the next, each member's n_ESS and draw count in
  * the last batch, whether it took part (active) and whether it was frozen (not trained
- * after that batch). */
+ * after that batch); entries 0, 1, 2 are members 0, 1, 2. */
 typedef struct {
     int32_t iteration;
-    int32_t active[2];
-    int32_t frozen[2];
+    int32_t active[3];
+    int32_t frozen[3];
     int32_t reserved;
-    double W_last[2];
-    double W_next[2];
-    double n_ess[2];
-    int64_t n_drawn[2];
+    double W_last[3];
+    double W_next[3];
+    double n_ess[3];
+    int64_t n_drawn[3];
 } rift_portfolio_info;
 int rift_ile_portfolio_info(const rift_ile_t *h, rift_portfolio_info *info);
+/* Member 2's state after the last portfolio iteration (its training included): weights
+ * pi [C], means mu [C][6] and widths sig [C][6] in prior-CDF coordinates, host buffers of
+ * `capacity` components (outputs may be NULL), C in *n_components (may be NULL).
+ * RIFT_ESTATE before a portfolio call with the GMM member since the handle was made;
+ * RIFT_EINVAL for capacity < C. */
+int rift_ile_portfolio_gmm(const rift_ile_t *h, int32_t capacity, int32_t *n_components, double *pi, double *mu,
+                           double *sig);
 
 /* Fair draws from the most recent batch (the final ILE pass: extrinsic samples drawn
  * fairly from the Monte Carlo integral's weighted samples, arXiv:2505.11655 Sec. II;

@@ -31,7 +31,7 @@ RIFT_KERNEL_FP64, RIFT_KERNEL_CUDA_CORE, RIFT_KERNEL_TENSOR = 0, 1, 2
 EXPORTED = ["rift_ile_create", "rift_ile_set_overlaps", "rift_ile_set_waveforms", "rift_ile_get_overlaps", "rift_ile_eval", "rift_ile_coeffs", "rift_ile_marginalize",
             "rift_ile_adapt", "rift_ile_last_batch", "rift_ile_get_state", "rift_ile_set_state",
             "rift_ile_get_sampler", "rift_ile_kernel_launches", "rift_ile_reduce_noalloc", "rift_ile_footprint",
-            "rift_ile_get_plan", "rift_ile_peak_rate", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_portfolio", "rift_ile_portfolio_info", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
+            "rift_ile_get_plan", "rift_ile_peak_rate", "rift_ile_wait_selftest", "rift_ile_fair_draws", "rift_ile_av", "rift_ile_av_info", "rift_ile_portfolio", "rift_ile_portfolio_info", "rift_ile_portfolio_gmm", "rift_ile_destroy", "rift_ile_strerror", "rift_batch_create", "rift_batch_run",
             "rift_batch_kernel_launches", "rift_batch_destroy", "rift_srv_create", "rift_srv_submit", "rift_srv_poll",
             "rift_srv_pending", "rift_srv_destroy"]
 
@@ -56,18 +56,21 @@ class rift_ile_config(C.Structure):
 
 RIFT_MEMBER_HIST = 1
 RIFT_MEMBER_AV = 2
+RIFT_MEMBER_GMM = 4
+RIFT_GMM_MAX_COMPONENTS = 16
 
 
 class rift_portfolio_config(C.Structure):
-    _fields_ = [("members", C.c_int32), ("av_start", C.c_int32), ("adapt_weights", C.c_int32),
-                ("reserved", C.c_int32), ("w_init", C.c_double * 2), ("p_thr", C.c_double),
-                ("n_min_star", C.c_int64), ("capacity", C.c_int64)]
+    _fields_ = [("members", C.c_int32), ("av_start", C.c_int32), ("gmm_start", C.c_int32),
+                ("gmm_components", C.c_int32), ("adapt_weights", C.c_int32), ("reserved", C.c_int32),
+                ("w_init", C.c_double * 3), ("p_thr", C.c_double), ("n_min_star", C.c_int64),
+                ("capacity", C.c_int64)]
 
 
 class rift_portfolio_info(C.Structure):
-    _fields_ = [("iteration", C.c_int32), ("active", C.c_int32 * 2), ("frozen", C.c_int32 * 2),
-                ("reserved", C.c_int32), ("W_last", C.c_double * 2), ("W_next", C.c_double * 2),
-                ("n_ess", C.c_double * 2), ("n_drawn", C.c_int64 * 2)]
+    _fields_ = [("iteration", C.c_int32), ("active", C.c_int32 * 3), ("frozen", C.c_int32 * 3),
+                ("reserved", C.c_int32), ("W_last", C.c_double * 3), ("W_next", C.c_double * 3),
+                ("n_ess", C.c_double * 3), ("n_drawn", C.c_int64 * 3)]
 
     def as_dict(self):
         return dict(iteration=self.iteration, active=list(self.active), frozen=list(self.frozen),
@@ -150,6 +153,7 @@ def load(build_if_missing: bool = False):
     L.rift_ile_av_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64), C.POINTER(i64), C.POINTER(C.c_double)]
     L.rift_ile_portfolio.argtypes = [vp, i32, i64, C.POINTER(rift_portfolio_config), i32, C.POINTER(rift_ile_result)]
     L.rift_ile_portfolio_info.argtypes = [vp, C.POINTER(rift_portfolio_info)]
+    L.rift_ile_portfolio_gmm.argtypes = [vp, i32, C.POINTER(i32), vp, vp, vp]
     L.rift_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(i32), C.POINTER(i64), vp, C.POINTER(vp)]
     L.rift_batch_run.argtypes = [vp, C.POINTER(rift_ile_result)]
     L.rift_batch_kernel_launches.argtypes = [vp]
@@ -368,6 +372,17 @@ def rift_ile_portfolio_info(h):
     info = rift_portfolio_info()
     _check(load().rift_ile_portfolio_info(h, C.byref(info)), "rift_ile_portfolio_info")
     return info.as_dict()
+
+
+def rift_ile_portfolio_gmm(h):
+    """The GMM member's (pi [C], mu [C][6], sig [C][6])."""
+    k = RIFT_GMM_MAX_COMPONENTS
+    pi, mu, sig = np.zeros(k), np.zeros((k, 6)), np.zeros((k, 6))
+    nc = C.c_int32(0)
+    _check(load().rift_ile_portfolio_gmm(h, k, C.byref(nc), pi.ctypes.data, mu.ctypes.data, sig.ctypes.data),
+           "rift_ile_portfolio_gmm")
+    c = nc.value
+    return pi[:c].copy(), mu[:c].copy(), sig[:c].copy()
 
 
 def rift_ile_av_info(h):
@@ -609,17 +624,24 @@ class ILE:
     def av_info(self):
         return rift_ile_av_info(self.h)
 
-    def portfolio(self, n_iter, n_per_iter, members=RIFT_MEMBER_HIST | RIFT_MEMBER_AV, av_start=0, adapt_weights=True,
-                  w_init=(0.5, 0.5), p_thr=0.9999, n_min_star=1000, capacity=None, restart=False):
-        """Portfolio iterations over {histogram, AV} (rift_ile_portfolio); capacity
-        defaults to 4 n_per_iter."""
-        cfg = rift_portfolio_config(int(members), int(av_start), 1 if adapt_weights else 0, 0,
-                                    (C.c_double * 2)(*[float(x) for x in w_init]), float(p_thr), int(n_min_star),
+    def portfolio(self, n_iter, n_per_iter, members=RIFT_MEMBER_HIST | RIFT_MEMBER_AV, av_start=0, gmm_start=0,
+                  gmm_components=4, adapt_weights=True, w_init=None, p_thr=0.9999, n_min_star=1000, capacity=None,
+                  restart=False):
+        """Portfolio iterations over {histogram, AV, GMM} (rift_ile_portfolio); capacity
+        defaults to 4 n_per_iter, w_init to equal weights over the members."""
+        if w_init is None:
+            w_init = [1.0 if (members >> m) & 1 else 0.0 for m in range(3)]
+        w = [float(x) for x in w_init] + [0.0] * (3 - len(w_init))
+        cfg = rift_portfolio_config(int(members), int(av_start), int(gmm_start), int(gmm_components),
+                                    1 if adapt_weights else 0, 0, (C.c_double * 3)(*w), float(p_thr), int(n_min_star),
                                     int(capacity if capacity is not None else 4 * n_per_iter))
         return rift_ile_portfolio(self.h, n_iter, n_per_iter, cfg, 1 if restart else 0).as_dict()
 
     def portfolio_info(self):
         return rift_ile_portfolio_info(self.h)
+
+    def portfolio_gmm(self):
+        return rift_ile_portfolio_gmm(self.h)
 
     def fair_draws(self, n_draws, seed=1):
         """Fair draws from the most recent batch: (theta [n][6], t [n], index [n])."""

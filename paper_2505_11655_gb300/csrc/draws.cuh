@@ -1,7 +1,7 @@
-// Per-sample draws of the two sampling priors on the unit cube of prior-CDF coordinates
-// v (internal): the product-form histogram (arXiv:2505.11655 Sec. II B) and the
-// adaptive-volume cells (Sec. IV A).  Shared by their own draw kernels and by the
-// portfolio's, which mixes them (Sec. IV, "Portfolio integrator").
+// Per-sample draws of the sampling priors on the unit cube of prior-CDF coordinates v
+// (internal): the product-form histogram and the Gaussian mixture (arXiv:2505.11655
+// Sec. II B) and the adaptive-volume cells (Sec. IV A).  Shared by their own draw
+// kernels and by the portfolio's, which mixes them (Sec. IV, "Portfolio integrator").
 #pragma once
 
 #include "ile_kernels.h"
@@ -138,6 +138,83 @@ __device__ __forceinline__ uint64_t av_cell_key(const double v[6], int level)
     for (int d = 0; d < 6; ++d)
         k |= (uint64_t)floor(__dmul_rn(v[d], side)) << (level * d);
     return k;
+}
+
+// Gaussian-mixture sampling prior: C <= kGmmMax components with weights pi_c and, per
+// dimension, a normal of mean mu_cd and width sig_cd truncated to [0, 1].  One iteration's
+// draws and densities read a table of kGmmTab doubles built on the host from (pi, mu, sig):
+//   [kGmmCum + c]   running sums of pi / sum pi (the component choice)
+//   [kGmmK + c]     ln(pi_c / sum pi) - sum_d ln(sig_cd (Phi(b_cd) - Phi(a_cd)) sqrt(2 pi))
+//   [kGmmMu + 6c + d], [kGmmSig + ...], [kGmmIsig + ...]   mu, sig, 1 / sig
+//   [kGmmPa + ...], [kGmmPd + ...]   Phi(a), Phi(b) - Phi(a), a = -mu/sig, b = (1 - mu)/sig
+constexpr int kGmmMax = RIFT_GMM_MAX_COMPONENTS;
+constexpr int kGmmCum = 0, kGmmK = kGmmMax, kGmmMu = 2 * kGmmMax, kGmmSig = kGmmMu + 6 * kGmmMax,
+              kGmmIsig = kGmmSig + 6 * kGmmMax, kGmmPa = kGmmIsig + 6 * kGmmMax, kGmmPd = kGmmPa + 6 * kGmmMax,
+              kGmmTab = kGmmPd + 6 * kGmmMax;
+
+// Draw i of GMM iteration `iter`: Philox4x32-10 (key = seed, counter (i lo, i hi, iter, p)):
+// p = 8, words 0,1: the 53-bit uniform U of the component, the first c with U < the running
+// sum of the weights (the last otherwise); p = 9..11, words (0,1), (2,3): the uniforms u_d;
+// v_d = mu + sig Phi^-1(Phi(a) + u_d (Phi(b) - Phi(a))) kept in [0, 1) (every operation
+// rounded as written).
+__device__ __forceinline__ void gmm_draw_one(const double *T, int C, uint32_t iter, int64_t i, uint32_t k0,
+                                             uint32_t k1, double v[6])
+{
+    const uint32_t lo = (uint32_t)(uint64_t)i, hi = (uint32_t)((uint64_t)i >> 32);
+    U4 r = philox10(U4{lo, hi, iter, 8u}, k0, k1);
+    const double U = unit53(r.x, r.y);
+    int c = C - 1;
+    for (int k = 0; k < C - 1; ++k)
+        if (U < T[kGmmCum + k]) {
+            c = k;
+            break;
+        }
+    double u[6];
+#pragma unroll
+    for (uint32_t p = 0; p < 3; ++p) {
+        r = philox10(U4{lo, hi, iter, 9u + p}, k0, k1);
+        u[2 * p] = unit53(r.x, r.y);
+        u[2 * p + 1] = unit53(r.z, r.w);
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const int e = 6 * c + d;
+        const double q = __dadd_rn(T[kGmmPa + e], __dmul_rn(u[d], T[kGmmPd + e]));
+        double x = __dadd_rn(T[kGmmMu + e], __dmul_rn(T[kGmmSig + e], normcdfinv(q)));
+        if (!(x >= 0.0))
+            x = 0.0;
+        if (x >= 1.0)
+            x = 0x1.fffffffffffffp-1;   // the largest double below 1
+        v[d] = x;
+    }
+}
+
+// ln(pi_c g_c(v)) of component c (pi normalised).
+__device__ __forceinline__ double gmm_ln_comp(const double *T, int c, const double v[6])
+{
+    double q = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const double z = (v[d] - T[kGmmMu + 6 * c + d]) * T[kGmmIsig + 6 * c + d];
+        q = fma(z, z, q);
+    }
+    return fma(-0.5, q, T[kGmmK + c]);
+}
+
+// ln g(v) of the mixture (running maximum: one exponential per component).
+__device__ __forceinline__ double gmm_ln_density(const double *T, int C, const double v[6])
+{
+    double mx = -INFINITY, s = 0.0;
+    for (int c = 0; c < C; ++c) {
+        const double l = gmm_ln_comp(T, c, v);
+        if (l > mx) {
+            s = s * exp(mx - l) + 1.0;
+            mx = l;
+        } else {
+            s += exp(l - mx);
+        }
+    }
+    return mx + log(s);
 }
 
 }  // namespace rift

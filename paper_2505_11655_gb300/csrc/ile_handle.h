@@ -114,15 +114,25 @@ struct rift_ile {
         uint8_t *member = nullptr;              // [max_samples] member that drew each sample
         double *v = nullptr;                    // [max_samples][6] prior-CDF coordinates of the draws
         double *v_av = nullptr, *lnL_av = nullptr;   // the AV member's draws, compacted
-        double *part = nullptr, *sums = nullptr;     // per-member weight sums: block partials, result
+        double *part = nullptr;                 // per-member weight sums: block partials
+        double *sums = nullptr;                 // [16 + 13 C] the member sums, then the EM sums
+        double *gmm_part = nullptr;             // EM sums: block partials
+        double *gmm_tab = nullptr;              // the GMM's draw and density table
         uint32_t iter = 0;                      // portfolio iterations since restart
+        int32_t members = 0;                    // member bits of the calls since the last restart
         bool have_w = false;
-        double W[2] = {0.0, 0.0};               // weights of the next batch
-        double W_last[2] = {0.0, 0.0};
-        double n_ess[2] = {0.0, 0.0};
-        int64_t n_drawn[2] = {0, 0};
-        int frozen[2] = {1, 1};
-        int active[2] = {0, 0};
+        double W[3] = {0.0, 0.0, 0.0};          // weights of the next batch
+        double W_last[3] = {0.0, 0.0, 0.0};
+        double n_ess[3] = {0.0, 0.0, 0.0};
+        int64_t n_drawn[3] = {0, 0, 0};
+        int frozen[3] = {1, 1, 1};
+        int active[3] = {0, 0, 0};
+        // the Gaussian-mixture member's state (host), C = 0 before it is started
+        int gmm_C = 0;
+        double gmm_pi[RIFT_GMM_MAX_COMPONENTS] = {};
+        double gmm_mu[RIFT_GMM_MAX_COMPONENTS * 6] = {};
+        double gmm_sig[RIFT_GMM_MAX_COMPONENTS * 6] = {};
+        std::vector<double> gmm_tab_host;      // staging of gmm_tab
     } pf;
 };
 
