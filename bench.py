@@ -396,29 +396,36 @@ def run_ours(args, rank, world, local_rank):
         dm = {"sample_evals_per_s": n / (statistics.mean(dms) / 1e3), "ms_per_step": statistics.mean(dms),
               "lnl_kernel_ms": statistics.mean(dml), "lnZ": rd["lnZ"], "n_eff": rd["n_eff"],
               "quadrature": "per bin: 2 panels x 10 Gauss-Legendre nodes in ln x (float32)"}
-    # the portfolio sampling prior (histogram + AV mixture) on the same problem and batch:
-    # per-iteration cost against the histogram sampler's step above
-    pfo = None
+    # the portfolio sampling prior on the same problem and batch, over {histogram, AV} and
+    # over {histogram, AV, Gaussian mixture}: per-iteration cost against the histogram
+    # sampler's step above
+    pfo = pfo3 = None
     if not args.quick:
-        with G.ILE(prob, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=1 + rank, stream=stream) as spf:
-            spf.portfolio(2, n, p_thr=0.999, n_min_star=1000, restart=True)   # warm-up (allocation, kernels)
-            torch.cuda.synchronize()
-            n_pf = 8
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rp = spf.portfolio(n_pf, n, p_thr=0.999, n_min_star=1000, restart=True)
-            e1.record(stream)
-            e1.synchronize()
-            pf_ms = e0.elapsed_time(e1)
-            pinfo = spf.portfolio_info()
-            av_info = spf.av_info()
-        pfo = {"iterations": n_pf, "samples_per_iter": n, "ms_per_iter": pf_ms / n_pf,
-               "histogram_ms_per_iter": statistics.mean(step_ms),
-               "sample_evals_per_s": n * n_pf / (pf_ms / 1e3), "lnZ": rp["lnZ"], "sigma_lnZ": rp["sigma_lnZ"],
-               "n_eff": rp["n_eff"], "lnZ_iter": rp["lnZ_iter"], "W_next": pinfo["W_next"],
-               "n_drawn_last": pinfo["n_drawn"], "n_ess_last": pinfo["n_ess"], "av_level": av_info["level"],
-               "av_volume": av_info["V"], "members": "histogram (64 bins) + adaptive volume (p_thr 0.999, "
-                                                    "N_min* 1000)"}
+        def run_pf(members, label):
+            with G.ILE(prob, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=1 + rank, stream=stream) as spf:
+                kw = dict(members=members, p_thr=0.999, n_min_star=1000, gmm_components=4)
+                spf.portfolio(2, n, restart=True, **kw)   # warm-up (allocation, kernels)
+                torch.cuda.synchronize()
+                n_pf = 8
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rp = spf.portfolio(n_pf, n, restart=True, **kw)
+                e1.record(stream)
+                e1.synchronize()
+                pf_ms = e0.elapsed_time(e1)
+                pinfo = spf.portfolio_info()
+                av_info = spf.av_info()
+            return {"iterations": n_pf, "samples_per_iter": n, "ms_per_iter": pf_ms / n_pf,
+                    "histogram_ms_per_iter": statistics.mean(step_ms),
+                    "sample_evals_per_s": n * n_pf / (pf_ms / 1e3), "lnZ": rp["lnZ"], "sigma_lnZ": rp["sigma_lnZ"],
+                    "n_eff": rp["n_eff"], "lnZ_iter": rp["lnZ_iter"], "W_next": pinfo["W_next"],
+                    "n_drawn_last": pinfo["n_drawn"], "n_ess_last": pinfo["n_ess"], "av_level": av_info["level"],
+                    "av_volume": av_info["V"], "members": label}
+        pfo = run_pf(G.RIFT_MEMBER_HIST | G.RIFT_MEMBER_AV,
+                     "histogram (64 bins) + adaptive volume (p_thr 0.999, N_min* 1000)")
+        pfo3 = run_pf(G.RIFT_MEMBER_HIST | G.RIFT_MEMBER_AV | G.RIFT_MEMBER_GMM,
+                      "histogram (64 bins) + adaptive volume (p_thr 0.999, N_min* 1000) + Gaussian mixture (4 "
+                      "components)")
     fps = flops_per_sample(prob)
     lnl_avg = statistics.mean(lnl_ms)
     achieved = fps * n / (lnl_avg / 1e3) / 1e12
@@ -447,6 +454,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches, "clocks": clocks,
         "lnZ_last": r["lnZ"], "n_eff_last": r["n_eff"], "precompute": pre, "distance_marg": dm,
         "portfolio": pfo,
+        "portfolio_gmm": pfo3,
     }
     if not args.quick:
         up = unit_peaks(G)
@@ -697,21 +705,26 @@ def run_high_snr(args, rank, world, local_rank):
                   "sigma_lnZ": ra["sigma_lnZ"], "n_eff": ra["n_eff"], "n_eff_iter": ra["n_eff_iter"],
                   "lnZ_iter": ra["lnZ_iter"], "final_level": info["level"], "final_cells": info["n_cells"],
                   "final_volume": info["V"], "p_thr": 0.9999, "n_min_star": 1000}
-    # the portfolio of both on the same problem and budget (10 x n, MIXED)
-    pf_res = None
+    # the portfolio on the same problem and budget (10 x n, MIXED): {histogram, AV},
+    # {histogram, AV, Gaussian mixture} and the Gaussian mixture alone
+    pf_res = {}
     if not args.quick:
-        with G.ILE(prob, precision=G.RIFT_MIXED, max_samples=n, n_bins=64, seed=1 + rank, stream=stream) as spf:
-            spf.portfolio(2, n, restart=True)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            rp = spf.portfolio(n_iter, n, restart=True)
-            torch.cuda.synchronize()
-            pf_ms = 1e3 * (time.perf_counter() - t0)
-            pinfo = spf.portfolio_info()
-        pf_res = {"ms_per_step": pf_ms, "sample_evals_per_s": n * n_iter / (pf_ms / 1e3), "lnZ": rp["lnZ"],
-                  "sigma_lnZ": rp["sigma_lnZ"], "n_eff": rp["n_eff"], "n_eff_iter": rp["n_eff_iter"],
-                  "lnZ_iter": rp["lnZ_iter"], "W_next": pinfo["W_next"], "n_drawn_last": pinfo["n_drawn"],
-                  "frozen_last": pinfo["frozen"], "p_thr": 0.9999, "n_min_star": 1000}
+        for label, members in (("histogram+av", G.RIFT_MEMBER_HIST | G.RIFT_MEMBER_AV),
+                               ("histogram+av+gmm", G.RIFT_MEMBER_HIST | G.RIFT_MEMBER_AV | G.RIFT_MEMBER_GMM),
+                               ("gmm", G.RIFT_MEMBER_GMM)):
+            with G.ILE(prob, precision=G.RIFT_MIXED, max_samples=n, n_bins=64, seed=1 + rank, stream=stream) as spf:
+                spf.portfolio(2, n, members=members, restart=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rp = spf.portfolio(n_iter, n, members=members, restart=True)
+                torch.cuda.synchronize()
+                pf_ms = 1e3 * (time.perf_counter() - t0)
+                pinfo = spf.portfolio_info()
+            pf_res[label] = {"ms_per_step": pf_ms, "sample_evals_per_s": n * n_iter / (pf_ms / 1e3),
+                             "lnZ": rp["lnZ"], "sigma_lnZ": rp["sigma_lnZ"], "n_eff": rp["n_eff"],
+                             "n_eff_iter": rp["n_eff_iter"], "lnZ_iter": rp["lnZ_iter"], "W_next": pinfo["W_next"],
+                             "n_drawn_last": pinfo["n_drawn"], "frozen_last": pinfo["frozen"], "p_thr": 0.9999,
+                             "n_min_star": 1000, "gmm_components": 4}
     # error of the last batch against the float64 path (1e-9 parity with the oracle):
     # every sample within 30 of the largest ln w, plus 4096 others
     th, lr, ll, lw = ile.last_batch(n)

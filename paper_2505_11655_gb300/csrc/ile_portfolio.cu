@@ -213,21 +213,32 @@ __global__ void __launch_bounds__(kPfThreads) member_sums_kernel(const double *_
     }
 }
 
-// Pass 2: thread m merges member m's partials in block order into out[m][4].
+// Pass 2: warp m merges member m's partials into out[m][4]: lane l takes blocks l, l + 32,
+// ... in order, then the lanes' results merge in a fixed tree (deterministic for a given
+// block count; a sequential merge over ~300 blocks is a chain of ~600 float64 exponentials).
 __global__ void member_sums_final_kernel(const double *__restrict__ partial, int nb, double *__restrict__ out)
 {
-    const int m = threadIdx.x;
+    const int m = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (m >= kNMembers)
         return;
     MAcc a{-INFINITY, 0.0, 0.0, 0.0};
-    for (int b = 0; b < nb; ++b) {
+    for (int b = lane; b < nb; b += 32) {
         const double *o = partial + 4 * kNMembers * b + 4 * m;
         a = macc_merge(a, MAcc{o[0], o[1], o[2], o[3]});
     }
-    out[4 * m] = a.mx;
-    out[4 * m + 1] = a.s1;
-    out[4 * m + 2] = a.s2;
-    out[4 * m + 3] = a.cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const MAcc q{__shfl_down_sync(0xffffffffu, a.mx, o), __shfl_down_sync(0xffffffffu, a.s1, o),
+                     __shfl_down_sync(0xffffffffu, a.s2, o), __shfl_down_sync(0xffffffffu, a.cnt, o)};
+        if (lane < o)
+            a = macc_merge(a, q);
+    }
+    if (lane == 0) {
+        out[4 * m] = a.mx;
+        out[4 * m + 1] = a.s1;
+        out[4 * m + 2] = a.s2;
+        out[4 * m + 3] = a.cnt;
+    }
 }
 
 // The GMM's weighted EM sums, pass 1.  A block takes a contiguous stripe of samples in
@@ -555,7 +566,7 @@ int portfolio_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, c
     // 3. per-member n_ESS, the EM sums, the new weights
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(kPfSumBlocks, (n + kPfThreads - 1) / kPfThreads));
     member_sums_kernel<<<nb, kPfThreads, 0, st>>>(h->lnw, p.member, n, p.part);
-    member_sums_final_kernel<<<1, 32, 0, st>>>(p.part, nb, p.sums);
+    member_sums_final_kernel<<<1, 32 * kNMembers, 0, st>>>(p.part, nb, p.sums);
     h->launches += 1 + sorted + 1 + 2 + 2;
     const int n_em = act[2] ? kEmStride * p.gmm_C : 0;
     if (act[2]) {
