@@ -147,10 +147,19 @@ __device__ __forceinline__ uint64_t av_cell_key(const double v[6], int level)
 //   [kGmmK + c]     ln(pi_c / sum pi) - sum_d ln(sig_cd (Phi(b_cd) - Phi(a_cd)) sqrt(2 pi))
 //   [kGmmMu + 6c + d], [kGmmSig + ...], [kGmmIsig + ...]   mu, sig, 1 / sig
 //   [kGmmPa + ...], [kGmmPd + ...]   Phi(a), Phi(b) - Phi(a), a = -mu/sig, b = (1 - mu)/sig
+// and behind them, as float32 (for the float32 modes), K, 1 / sig and mu as a float32 pair
+// (hi + lo = mu to ~2^-48).
 constexpr int kGmmMax = RIFT_GMM_MAX_COMPONENTS;
 constexpr int kGmmCum = 0, kGmmK = kGmmMax, kGmmMu = 2 * kGmmMax, kGmmSig = kGmmMu + 6 * kGmmMax,
               kGmmIsig = kGmmSig + 6 * kGmmMax, kGmmPa = kGmmIsig + 6 * kGmmMax, kGmmPd = kGmmPa + 6 * kGmmMax,
-              kGmmTab = kGmmPd + 6 * kGmmMax;
+              kGmmF32 = kGmmPd + 6 * kGmmMax;   // float32 section: [C] K, [C][6] 1 / sig, mu hi, mu lo
+constexpr int kGmmTab = kGmmF32 + (kGmmMax + 18 * kGmmMax) / 2;
+static_assert(kGmmMax % 2 == 0, "the float32 section fills whole doubles");
+__host__ __device__ inline float *gmm_kf(double *T) { return reinterpret_cast<float *>(T + kGmmF32); }
+__host__ __device__ inline const float *gmm_kf(const double *T) { return reinterpret_cast<const float *>(T + kGmmF32); }
+__host__ __device__ inline const float *gmm_isigf(const double *T) { return gmm_kf(T) + kGmmMax; }
+__host__ __device__ inline const float *gmm_muhf(const double *T) { return gmm_kf(T) + 7 * kGmmMax; }
+__host__ __device__ inline const float *gmm_mulf(const double *T) { return gmm_kf(T) + 13 * kGmmMax; }
 
 // Draw i of GMM iteration `iter`: Philox4x32-10 (key = seed, counter (i lo, i hi, iter, p)):
 // p = 8, words 0,1: the 53-bit uniform U of the component, the first c with U < the running
@@ -187,6 +196,84 @@ __device__ __forceinline__ void gmm_draw_one(const double *T, int C, uint32_t it
             x = 0x1.fffffffffffffp-1;   // the largest double below 1
         v[d] = x;
     }
+}
+
+// The float32 modes' draw: the same uniforms and probability q, the normal quantile in
+// float32 on the smaller tail (q or 1 - q, formed in float64), v = mu + sig x in float64.  The
+// draw's own density is then evaluated at this v (gmm_ln_density_f32), so the importance
+// weight stays consistent; the quantile's few-ulp error moves v by ~1e-7 sig |x|.
+__device__ __forceinline__ void gmm_draw_one_f32(const double *T, int C, uint32_t iter, int64_t i, uint32_t k0,
+                                                 uint32_t k1, double v[6])
+{
+    const uint32_t lo = (uint32_t)(uint64_t)i, hi = (uint32_t)((uint64_t)i >> 32);
+    U4 r = philox10(U4{lo, hi, iter, 8u}, k0, k1);
+    const double U = unit53(r.x, r.y);
+    int c = C - 1;
+    for (int k = 0; k < C - 1; ++k)
+        if (U < T[kGmmCum + k]) {
+            c = k;
+            break;
+        }
+    double u[6];
+#pragma unroll
+    for (uint32_t p = 0; p < 3; ++p) {
+        r = philox10(U4{lo, hi, iter, 9u + p}, k0, k1);
+        u[2 * p] = unit53(r.x, r.y);
+        u[2 * p + 1] = unit53(r.z, r.w);
+    }
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const int e = 6 * c + d;
+        const double q = __dadd_rn(T[kGmmPa + e], __dmul_rn(u[d], T[kGmmPd + e]));
+        const float xq = q <= 0.5 ? normcdfinvf((float)q) : -normcdfinvf((float)(1.0 - q));
+        double x = fma(T[kGmmSig + e], (double)xq, T[kGmmMu + e]);
+        if (!(x >= 0.0))
+            x = 0.0;
+        if (x >= 1.0)
+            x = 0x1.fffffffffffffp-1;
+        v[d] = x;
+    }
+}
+
+// v as a float32 pair (hi + lo = v to ~2^-48; three float64-pipe operations a dimension).
+__device__ __forceinline__ void gmm_split(const double v[6], float vh[6], float vl[6])
+{
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        vh[d] = (float)v[d];
+        vl[d] = (float)(v[d] - (double)vh[d]);
+    }
+}
+
+// ln(pi_c g_c(v)) of component c in float32: v - mu from the float32 pairs (the difference of
+// the high parts is exact when they are close, so z keeps its relative precision even for a
+// narrow component), error ~1e-6 in the result.
+__device__ __forceinline__ float gmm_ln_comp_f32(const double *T, int c, const float vh[6], const float vl[6])
+{
+    const float *isf = gmm_isigf(T), *mh = gmm_muhf(T), *ml = gmm_mulf(T);
+    float q = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const int e = 6 * c + d;
+        const float z = ((vh[d] - mh[e]) + (vl[d] - ml[e])) * isf[e];
+        q = fmaf(z, z, q);
+    }
+    return fmaf(-0.5f, q, gmm_kf(T)[c]);
+}
+
+__device__ __forceinline__ float gmm_ln_density_f32(const double *T, int C, const float vh[6], const float vl[6])
+{
+    float mx = -INFINITY, s = 0.f;
+    for (int c = 0; c < C; ++c) {
+        const float l = gmm_ln_comp_f32(T, c, vh, vl);
+        if (l > mx) {
+            s = s * __expf(mx - l) + 1.f;
+            mx = l;
+        } else {
+            s += __expf(l - mx);
+        }
+    }
+    return mx + __logf(s);
 }
 
 // ln(pi_c g_c(v)) of component c (pi normalised).

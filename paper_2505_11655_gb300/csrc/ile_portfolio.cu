@@ -58,12 +58,18 @@ __device__ __forceinline__ bool in_cells(const uint64_t *__restrict__ cells, int
 // What one iteration's draw kernel needs to know of the members: bit a of act = member a
 // active; multi: more than one active, the member is chosen with thresholds (t0, t1) and
 // ln p - ln p_s is the mixture's with weights W; otherwise every draw is member `single`'s.
+// lnWf: the float32 modes' ln W_0, ln W_1 - ln V, ln W_2.
 struct PfDraw {
     double W[kNMembers];
     double t0, t1;
+    float lnWf[kNMembers];
     int act, multi, single, gmm_C;
 };
 
+// kF32 (the float32 modes): the mixture's normal quantiles and densities in float32 (the
+// draws are then this path's own; the float64 mode keeps every draw and density equal to
+// the oracle's to the last bits)
+template <bool kF32>
 __global__ void __launch_bounds__(kPfThreads) portfolio_draw_kernel(
     SamplerDev S, SkyGrid G, const uint64_t *__restrict__ cells, int64_t n_cells, int level, double lnV,
     double invV, const double *__restrict__ gmm_tab, PfDraw P, uint32_t iter, int64_t n, double *__restrict__ theta,
@@ -99,12 +105,43 @@ __global__ void __launch_bounds__(kPfThreads) portfolio_draw_kernel(
             av_draw_one(cells, n_cells, level, iter, i, k0, k1, v);
             av_theta(v, d3lo, d3hi, th);
             lr = lnV;
+        } else if (kF32) {
+            gmm_draw_one_f32(sG, P.gmm_C, iter, i, k0, k1, v);
+            av_theta(v, d3lo, d3hi, th);
         } else {
             gmm_draw_one(sG, P.gmm_C, iter, i, k0, k1, v);
             av_theta(v, d3lo, d3hi, th);
             lr = -gmm_ln_density(sG, P.gmm_C, v);
         }
-        if (P.multi) {
+        float vh[6], vl[6];
+        if (kF32 && use_gmm) {
+            gmm_split(v, vh, vl);
+            if (m == 2)
+                lr = -(double)gmm_ln_density_f32(sG, P.gmm_C, vh, vl);
+        }
+        if (kF32 && P.multi) {
+            // -ln sum_a W_a g_a(v) as a log-sum-exp of ln W_a + ln g_a in float32
+            float l0 = -INFINITY, l1 = -INFINITY, l2 = -INFINITY;
+            if (use_hist) {
+                double lnd = -lr;
+                if (m != 0) {
+                    lnd = 0.0;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) {
+                        const int b = min((int)floor(v[d] * (double)B), B - 1);
+                        lnd += sL[d * B + b];
+                        packed |= (uint64_t)b << (10 * d);
+                    }
+                }
+                l0 = P.lnWf[0] + (float)lnd;
+            }
+            if (use_av && (m == 1 || in_cells(cells, n_cells, av_cell_key(v, level))))
+                l1 = P.lnWf[1];
+            if (use_gmm)
+                l2 = P.lnWf[2] + (m == 2 ? (float)(-lr) : gmm_ln_density_f32(sG, P.gmm_C, vh, vl));
+            const float mx = fmaxf(l0, fmaxf(l1, l2));
+            lr = -(double)(mx + __logf(__expf(l0 - mx) + __expf(l1 - mx) + __expf(l2 - mx)));
+        } else if (P.multi) {
             // sum over the active members of W_a g_a(v), in member order (each product and
             // sum rounded as written)
             double dens = 0.0;
@@ -247,6 +284,7 @@ __global__ void member_sums_final_kernel(const double *__restrict__ partial, int
 // thread j < 13 C owns the sum (c, k) = (j / 13, j % 13) of omega r times 1, v_d (k = 1..6)
 // or v_d^2 (k = 7..12) and adds the tile's samples to it in index order.
 // partial[blk][13 C].
+template <bool kF32>
 __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double *__restrict__ tab, int C,
                                                                     const double *__restrict__ v,
                                                                     const double *__restrict__ lnw, int64_t n,
@@ -278,20 +316,40 @@ __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double
                 vs[d] = vi[d];
             }
             const double x = lnw[i];
-            const double om = isfinite(x) ? exp(x - mx) : 0.0;
-            double lmax = -INFINITY;
-            for (int c = 0; c < C; ++c) {
-                w[c] = gmm_ln_comp(sT, c, vi);
-                lmax = fmax(lmax, w[c]);
+            if (kF32) {
+                // the responsibilities and weights in float32 (they only shape the next
+                // proposal; its density is evaluated from the parameters it is drawn with)
+                const float om = isfinite(x) ? __expf((float)(x - mx)) : 0.f;
+                float vh[6], vl[6];
+                gmm_split(vi, vh, vl);
+                float lmax = -INFINITY;
+                for (int c = 0; c < C; ++c)
+                    lmax = fmaxf(lmax, gmm_ln_comp_f32(sT, c, vh, vl));
+                float tot = 0.f;
+                for (int c = 0; c < C; ++c) {
+                    const float e = __expf(gmm_ln_comp_f32(sT, c, vh, vl) - lmax);
+                    w[c] = (double)e;
+                    tot += e;
+                }
+                const double f = (double)(om / tot);
+                for (int c = 0; c < C; ++c)
+                    w[c] *= f;
+            } else {
+                const double om = isfinite(x) ? exp(x - mx) : 0.0;
+                double lmax = -INFINITY;
+                for (int c = 0; c < C; ++c) {
+                    w[c] = gmm_ln_comp(sT, c, vi);
+                    lmax = fmax(lmax, w[c]);
+                }
+                double tot = 0.0;
+                for (int c = 0; c < C; ++c) {
+                    w[c] = exp(w[c] - lmax);
+                    tot += w[c];
+                }
+                const double f = om / tot;
+                for (int c = 0; c < C; ++c)
+                    w[c] *= f;
             }
-            double tot = 0.0;
-            for (int c = 0; c < C; ++c) {
-                w[c] = exp(w[c] - lmax);
-                tot += w[c];
-            }
-            const double f = om / tot;
-            for (int c = 0; c < C; ++c)
-                w[c] *= f;
         }
         __syncthreads();
         if (j < n_sums) {
@@ -440,6 +498,17 @@ void gmm_table(rift_ile_t::PortfolioState &p)
         }
         T[kGmmK + c] = k;
     }
+    float *F = gmm_kf(T.data());
+    for (int c = 0; c < C; ++c) {
+        F[c] = (float)T[kGmmK + c];
+        for (int d = 0; d < 6; ++d) {
+            const int e = 6 * c + d;
+            const float hi = (float)p.gmm_mu[e];
+            F[kGmmMax + e] = (float)(1.0 / p.gmm_sig[e]);
+            F[7 * kGmmMax + e] = hi;
+            F[13 * kGmmMax + e] = (float)(p.gmm_mu[e] - (double)hi);
+        }
+    }
 }
 
 // One weighted EM step from the sums [C][13] (S_c, sum omega r v_d, sum omega r v_d^2).
@@ -481,8 +550,10 @@ int pf_alloc(rift_ile_t *h)
         (rc = dalloc(h, &p.gmm_part, (size_t)kEmStride * kGmmMax * kPfSumBlocks)) ||
         (rc = dalloc(h, &p.gmm_tab, (size_t)kGmmTab)))
         return rc;
-    CK(allow_max_dynamic_smem(portfolio_draw_kernel));
-    CK(allow_max_dynamic_smem(gmm_em_partial_kernel));
+    CK(allow_max_dynamic_smem(portfolio_draw_kernel<false>));
+    CK(allow_max_dynamic_smem(portfolio_draw_kernel<true>));
+    CK(allow_max_dynamic_smem(gmm_em_partial_kernel<false>));
+    CK(allow_max_dynamic_smem(gmm_em_partial_kernel<true>));
     p.alloc = true;
     return RIFT_OK;
 }
@@ -543,9 +614,16 @@ int portfolio_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, c
         CK(cudaMemcpyAsync(p.gmm_tab, p.gmm_tab_host.data(), sizeof(double) * kGmmTab, cudaMemcpyHostToDevice, st));
     }
     const size_t smem = sizeof(double) * ((act[0] ? hist_table_doubles(S.B) : 0) + (act[2] ? kGmmTab : 0));
-    portfolio_draw_kernel<<<grid_n(n), kPfThreads, smem, st>>>(
-        S, h->grid, a.cells, a.n_cells, a.level, has_av ? std::log(a.V) : 0.0, has_av ? 1.0 / a.V : 0.0, p.gmm_tab, P,
-        g, n, h->theta, h->lnpw, h->bins, h->key, p.v, p.member);
+    const bool f32 = use_fp32(h);
+    if (f32) {
+        P.lnWf[0] = (float)std::log(W[0]);
+        P.lnWf[1] = has_av ? (float)(std::log(W[1]) - std::log(a.V)) : -INFINITY;
+        P.lnWf[2] = (float)std::log(W[2]);
+    }
+    auto draw = f32 ? portfolio_draw_kernel<true> : portfolio_draw_kernel<false>;
+    draw<<<grid_n(n), kPfThreads, smem, st>>>(S, h->grid, a.cells, a.n_cells, a.level,
+                                              has_av ? std::log(a.V) : 0.0, has_av ? 1.0 / a.V : 0.0, p.gmm_tab, P,
+                                              g, n, h->theta, h->lnpw, h->bins, h->key, p.v, p.member);
     CK(cudaGetLastError());
     int sorted = 0;
     if (use_fp32(h))
@@ -571,8 +649,8 @@ int portfolio_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, c
     const int n_em = act[2] ? kEmStride * p.gmm_C : 0;
     if (act[2]) {
         const size_t em_smem = sizeof(double) * (kGmmTab + 6 * kPfThreads + (size_t)kPfThreads * p.gmm_C);
-        gmm_em_partial_kernel<<<nb, kPfThreads, em_smem, st>>>(p.gmm_tab, p.gmm_C, p.v, h->lnw, n, h->stats, slot,
-                                                               p.gmm_part);
+        auto em = f32 ? gmm_em_partial_kernel<true> : gmm_em_partial_kernel<false>;
+        em<<<nb, kPfThreads, em_smem, st>>>(p.gmm_tab, p.gmm_C, p.v, h->lnw, n, h->stats, slot, p.gmm_part);
         gmm_em_final_kernel<<<1, 224, 0, st>>>(p.gmm_part, nb, n_em, p.sums + kSumsGmm);
         CK(cudaGetLastError());
         h->launches += 2;
