@@ -36,7 +36,7 @@
 
 namespace rift {
 
-constexpr int kFixWarps = 4;
+constexpr int kFixMaxWarps = 16;   // warps per block: as many as the shared memory holds, up to this
 
 // --------------------------------------------------------------- double-float copies
 
@@ -105,7 +105,7 @@ __host__ __device__ inline size_t fix_warp_bytes(int K, int M, int dmax)
     return (size_t)(K + 1) * 32 * 8 + (size_t)fix_float_rows(K, M, dmax) * 32 * 4 + 32 * 4;
 }
 
-__global__ void __launch_bounds__(32 * kFixWarps)
+__global__ void __launch_bounds__(32 * kFixMaxWarps)
 fix_kernel(Problem P, BinTable bt, FixTables T, const double *__restrict__ theta, const uint32_t *__restrict__ idx,
            const uint32_t *__restrict__ count, PeakOut po, int blen, double *__restrict__ lnL_tmarg,
            double *__restrict__ lnL_t, const double *__restrict__ lnpw, double *__restrict__ lnw, int *err)
@@ -123,10 +123,11 @@ fix_kernel(Problem P, BinTable bt, FixTables T, const double *__restrict__ theta
     const int rs = 0, rdl = 4 * K, rph = 4 * K + 2 * M;
     const double beta = P.t_step * P.fs;
     const uint32_t cnt = *count;
-    if ((int64_t)blockIdx.x * kFixWarps * 32 >= (int64_t)cnt)
+    const int nw = (int)(blockDim.x >> 5);
+    if ((int64_t)blockIdx.x * nw * 32 >= (int64_t)cnt)
         return;   // no listed sample for this block (the grid is sized for every sample)
     // the pair tables and the double-float U, V of every detector, staged once per block
-    float4 *sua = reinterpret_cast<float4 *>(fsm + fix_warp_bytes(K, M, T.dmax) * kFixWarps);
+    float4 *sua = reinterpret_cast<float4 *>(fsm + fix_warp_bytes(K, M, T.dmax) * nw);
     float4 *svb = sua + K * T.nA;
     uint16_t *saij = reinterpret_cast<uint16_t *>(svb + K * T.nB);
     uint16_t *sbij = saij + T.nA;
@@ -142,8 +143,8 @@ fix_kernel(Problem P, BinTable bt, FixTables T, const double *__restrict__ theta
     // this lane's sample: the double-float value at rows (row, row + 1)
     auto ld = [&](int row) { return df{rf[row * 32 + lane], rf[(row + 1) * 32 + lane]}; };
 
-    for (int64_t base = ((int64_t)blockIdx.x * kFixWarps + warp) * 32; base < (int64_t)cnt;
-         base += (int64_t)gridDim.x * kFixWarps * 32) {
+    for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * 32; base < (int64_t)cnt;
+         base += (int64_t)gridDim.x * nw * 32) {
         const int64_t e = base + lane;
         const bool active = e < (int64_t)cnt;
         const uint32_t g = active ? idx[e] : 0u;
@@ -435,11 +436,20 @@ cudaError_t launch_fix(const Problem &P, BinTable bt, FixTables T, const double 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t per_block = 32 * kFixWarps;
-    const int grid = (int)std::min<int64_t>((n + per_block - 1) / per_block, (int64_t)sms * 4);
-    const size_t smem = fix_warp_bytes(P.K, P.M, T.dmax) * kFixWarps + (size_t)P.K * (T.nA + T.nB) * 16 +
-                        (size_t)(T.nA + T.nB) * 2;
-    fix_kernel<<<grid, 32 * kFixWarps, smem, st>>>(P, bt, T, theta, idx, count, po, blen, lnL_tmarg, lnL_t, lnpw,
+    // one block per SM with as many warps as its shared memory holds (the pair tables are
+    // staged once per block, the per-warp scratch grows with the warps): latency-bound
+    // double-float chains want the warps
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t wbytes = fix_warp_bytes(P.K, P.M, T.dmax);
+    const size_t tbytes = (size_t)P.K * (T.nA + T.nB) * 16 + (size_t)(T.nA + T.nB) * 2;
+    int nw = kFixMaxWarps;
+    while (nw > 1 && wbytes * nw + tbytes > (size_t)max_smem)
+        --nw;
+    const int64_t per_block = 32 * nw;
+    const int grid = (int)std::min<int64_t>((n + per_block - 1) / per_block, (int64_t)sms);
+    const size_t smem = wbytes * nw + tbytes;
+    fix_kernel<<<grid, 32 * nw, smem, st>>>(P, bt, T, theta, idx, count, po, blen, lnL_tmarg, lnL_t, lnpw,
                                                     lnw, err);
     if (launched)
         *launched = 2;
