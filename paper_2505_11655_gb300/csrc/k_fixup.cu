@@ -124,7 +124,9 @@ fix_kernel(Problem P, BinTable bt, FixTables T, const double *__restrict__ theta
     const double beta = P.t_step * P.fs;
     const uint32_t cnt = *count;
     const int nw = (int)(blockDim.x >> 5);
-    if ((int64_t)blockIdx.x * nw * 32 >= (int64_t)cnt)
+    // batch b of 32 listed samples goes to block b % gridDim.x, warp b / gridDim.x (round
+    // robin over the blocks first, so that a short list still spreads over every SM)
+    if ((int64_t)blockIdx.x * 32 >= (int64_t)cnt)
         return;   // no listed sample for this block (the grid is sized for every sample)
     // the pair tables and the double-float U, V of every detector, staged once per block
     float4 *sua = reinterpret_cast<float4 *>(fsm + fix_warp_bytes(K, M, T.dmax) * nw);
@@ -143,7 +145,7 @@ fix_kernel(Problem P, BinTable bt, FixTables T, const double *__restrict__ theta
     // this lane's sample: the double-float value at rows (row, row + 1)
     auto ld = [&](int row) { return df{rf[row * 32 + lane], rf[(row + 1) * 32 + lane]}; };
 
-    for (int64_t base = ((int64_t)blockIdx.x * nw + warp) * 32; base < (int64_t)cnt;
+    for (int64_t base = ((int64_t)warp * gridDim.x + blockIdx.x) * 32; base < (int64_t)cnt;
          base += (int64_t)gridDim.x * nw * 32) {
         const int64_t e = base + lane;
         const bool active = e < (int64_t)cnt;
