@@ -61,6 +61,7 @@ TRAFFIC_SOURCES = [os.path.join(ROOT, "paper_2505_11655_gb300", "csrc", f) for f
 TRAFFIC_BY_SOURCE = {
     "3e98ac2b2f6e30de16cf5dde8c8e0c1c184a69bbe778eea4e7a9c189816e4061": 5.98e7,
     "02d8362c4117749bf193a68eea6c4ee9c70af5751d9d82631086b1437d6f8777": 5.97e7,
+    "a1a0f3fa500f237d67cded3cf3f47eaac17dae8af6c99f541d525a7f85a14ff1": 6.03e7,
 }
 
 
