@@ -3,10 +3,15 @@
 // Which tile kernel wins (128-sample tensor-core tiles or 64-sample CUDA-core tiles)
 // and how densely the sky sort fills its Hilbert cells depend on the problem class:
 // the detector count, the mode count (padded to the 16-wide MMA K step), the time
-// grid, the Q length and the batch size.  The first batch of a class times every
-// candidate plan on samples drawn from the sampler (keys + sort + likelihood, best of
-// two runs) and the winner is cached for the process; with RIFT_ILE_TUNE_CACHE set
-// to a file path the cache is also read from and appended to that file.
+// grid, the Q length and the batch size, and on how far the sampler has adapted (the
+// samples of an adapted sampler crowd into fewer sky cells and delays, which changes the
+// best sort).  The first batch of a class times every candidate plan on samples drawn
+// from the sampler (keys + sort + likelihood, best of two runs) and the winner is cached
+// for the process; a handle whose sampler has adapted twice or more looks up a second
+// class, tuned the same way on its first adapted batch.  The plan thus depends only on
+// the problem class and whether the handle has adapted twice, never on another handle's
+// history.  With RIFT_ILE_TUNE_CACHE set to a file path the cache is also read from and
+// appended to that file.
 #include <cmath>
 #include <cstring>
 #include <fstream>
@@ -22,6 +27,7 @@ namespace host {
 namespace {
 
 constexpr int64_t kTuneMinBatch = 4096;   // smaller batches take the untuned default
+constexpr uint32_t kAdaptedAfter = 2;      // iterations after which a sampler counts as adapted
 
 struct TuneCache {
     std::mutex mu;
@@ -179,7 +185,7 @@ int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed)
         h->plan = LaunchPlan{1, 4, 0};
         return RIFT_OK;
     }
-    const std::string key = class_key(h, n);
+    const std::string key = class_key(h, n) + (h->iteration >= kAdaptedAfter ? "_adapted" : "");
     TuneCache &c = cache();
     {
         std::lock_guard<std::mutex> lock(c.mu);
