@@ -28,6 +28,7 @@ namespace {
 
 constexpr int64_t kTuneMinBatch = 4096;   // smaller batches take the untuned default
 constexpr uint32_t kAdaptedAfter = 2;      // iterations after which a sampler counts as adapted
+constexpr int64_t kAdaptedMinBatch = 1 << 19;   // smaller batches keep their first plan
 
 struct TuneCache {
     std::mutex mu;
@@ -109,11 +110,11 @@ int time_plan(rift_ile_t *h, int64_t n, const LaunchPlan &p, cudaEvent_t e0, cud
     return RIFT_OK;
 }
 
-int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
+int measure(rift_ile_t *h, int64_t n, LaunchPlan *out, bool tc_only)
 {
     // CUDA-core tiles; tensor-core tiles at three sky-cell fills; with three or more
     // detectors also tensor-core tiles sorted by a Morton key of three delays (fewer
-    // tile sub-groups at low sample density)
+    // tile sub-groups at low sample density).  tc_only: the tensor-core plans alone.
     static const LaunchPlan candidates[] = {{0, 4, 0}, {1, 2, 0}, {1, 4, 0}, {1, 8, 0}, {1, 4, 1}};
     const int n_cand = h->prob.K >= 3 ? 5 : 4;
     h->plan = LaunchPlan{};
@@ -128,7 +129,7 @@ int measure(rift_ile_t *h, int64_t n, LaunchPlan *out)
     }
     float best = INFINITY;
     int rc = RIFT_OK;
-    for (int ci = 0; ci < n_cand; ++ci) {
+    for (int ci = tc_only ? 1 : 0; ci < n_cand; ++ci) {
         const LaunchPlan &p = candidates[ci];
         float t = 0;
         rc = time_plan(h, n, p, e0, e1, &t);
@@ -185,8 +186,13 @@ int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed)
         h->plan = LaunchPlan{1, 4, 0};
         return RIFT_OK;
     }
-    const std::string key = class_key(h, n) + (h->iteration >= kAdaptedAfter ? "_adapted" : "");
+    // an adapted sampler's large batch re-tunes the tensor-core plan (sky-cell fill and sort
+    // key) once per class; the kernel family stays that of the first plan
+    const std::string base = class_key(h, n);
+    const bool adapted = h->iteration >= kAdaptedAfter && n >= kAdaptedMinBatch;
+    const std::string key = adapted ? base + "_adapted" : base;
     TuneCache &c = cache();
+    bool tc_only = false;
     {
         std::lock_guard<std::mutex> lock(c.mu);
         load_file(c);
@@ -195,6 +201,16 @@ int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed)
             h->plan = it->second;
             return RIFT_OK;
         }
+        if (adapted) {
+            auto first = c.plans.find(base);
+            if (first != c.plans.end()) {
+                if (first->second.tc != 1) {   // CUDA-core tiles: nothing to re-tune
+                    h->plan = first->second;
+                    return RIFT_OK;
+                }
+                tc_only = true;
+            }
+        }
     }
     const char *env = std::getenv("RIFT_ILE_TUNE");
     if (!measure_allowed || n < kTuneMinBatch || (env && env[0] == '0')) {
@@ -202,7 +218,7 @@ int choose_plan_tuned(rift_ile_t *h, int64_t n, bool measure_allowed)
         return RIFT_OK;
     }
     LaunchPlan best{};
-    RK(measure(h, n, &best));
+    RK(measure(h, n, &best, tc_only));
     {
         std::lock_guard<std::mutex> lock(c.mu);
         if (c.plans.emplace(key, best).second)
