@@ -7,11 +7,13 @@
 // samples of an adapted sampler crowd into fewer sky cells and delays, which changes the
 // best sort).  The first batch of a class times every candidate plan on samples drawn
 // from the sampler (keys + sort + likelihood, best of two runs) and the winner is cached
-// for the process; a handle whose sampler has adapted twice or more looks up a second
-// class, tuned the same way on its first adapted batch.  The plan thus depends only on
-// the problem class and whether the handle has adapted twice, never on another handle's
-// history.  With RIFT_ILE_TUNE_CACHE set to a file path the cache is also read from and
-// appended to that file.
+// for the process.  A handle whose sampler has adapted twice or more, on a batch of 2^19
+// samples or more, looks up a second class whose tensor-core plans (sky-cell fill, sort
+// key) are timed the same way on its first adapted batch (a class whose first plan is the
+// CUDA-core kernel keeps it).  The plan thus depends only on the problem class and on
+// whether the handle has adapted twice, never on another handle's history.  With
+// RIFT_ILE_TUNE_CACHE set to a file path the cache is also read from and appended to that
+// file.
 #include <cmath>
 #include <cstring>
 #include <fstream>
