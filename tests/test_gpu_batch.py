@@ -146,6 +146,34 @@ def test_tuner_appends_new_classes_to_cache_file(G, monkeypatch, tmp_path):
     assert lines[3] == "0"   # the three-delay key is a candidate only with three detectors
 
 
+def test_tuner_adapted_class(G, monkeypatch, tmp_path):
+    """A sampler adapted twice, on a batch of 2^19 samples or more, re-times the
+    tensor-core plans once for its class (a second cache line, "_adapted"); smaller
+    batches keep their first plan."""
+    path = tmp_path / "plans.txt"
+    monkeypatch.setenv("RIFT_ILE_TUNE_CACHE", str(path))
+    p = S.make_problem(("H1", "L1", "V1"), 7, 4096.0, n_t=301, snr=20.0, seed=S.config_seed(3, 9002))
+    n = 1 << 19
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n) as s:
+        plans = []
+        for _ in range(4):
+            r = s.adapt(1, n)
+            assert r["status"] == 0
+            plans.append(s.plan())
+    lines = [ln.split() for ln in path.read_text().splitlines()]
+    keys = [ln[0] for ln in lines]
+    assert len(lines) == 2 and keys[1] == keys[0] + "_adapted", lines
+    if int(lines[0][1]) == 1:
+        assert int(lines[1][1]) == 1   # the kernel family stays
+    else:
+        assert lines[1][1:] == lines[0][1:]
+    assert plans[0] == plans[1]   # iterations 0 and 1: the first plan
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n // 4) as s:
+        for _ in range(3):
+            s.adapt(1, n // 4)
+    assert len(path.read_text().splitlines()) == 3   # its own first class only, no adapted class
+
+
 @pytest.mark.slow
 def test_batched_workload_every_point_meets_oracle(G, orc):
     """All 512 points of the batched uneven workload (sizes, detectors, modes, rates and
