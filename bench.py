@@ -93,7 +93,8 @@ def kernel_traffic():
 
 
 def measured_peaks():
-    """The measured HBM copy and bf16 GEMM rates of the GB300s."""
+    """The measured HBM copy and bf16 GEMM rates of this machine (MEASURED_PEAKS.json), else
+    fixed fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
