@@ -261,18 +261,20 @@ __device__ __forceinline__ uint32_t sky_cell_v(double a, double z, const SkyGrid
 __device__ __forceinline__ uint32_t sky_cell(double alpha, double delta, const SkyGrid &G)
 {
     if (G.mode != kSortSky) {
-        // delays dt_k = -x_k . s with s the unit vector to the source (Earth frame)
-        double sa, ca, sd, cd;
-        sincos(alpha - G.gmst, &sa, &ca);
-        sincos(delta, &sd, &cd);
-        const double s0 = cd * ca, s1 = cd * sa, s2 = sd;
+        // delays dt_k = -x_k . s with s the unit vector to the source (Earth frame), in
+        // float32: the key only orders the samples (at most 2^10 levels per delay; float64
+        // transcendentals run on this part's slow float64 pipe)
+        float sa, ca, sd, cd;
+        sincosf((float)(alpha - G.gmst), &sa, &ca);
+        sincosf((float)delta, &sd, &cd);
+        const float s0 = cd * ca, s1 = cd * sa, s2 = sd;
         uint32_t q[3];
         const int nd = G.mode == kSortDelay1 ? 1 : G.mode == kSortDelay2 ? 2 : 3;
         const int levels = G.mode == kSortDelay1 ? G.n_cells : (1 << G.order);
         for (int k = 0; k < nd; ++k) {
-            const double dt = -(G.x[k][0] * s0 + G.x[k][1] * s1 + G.x[k][2] * s2);
-            const double u = G.span[k] > 0.0 ? 0.5 * (dt / G.span[k] + 1.0) : 0.5;
-            q[k] = (uint32_t)min(levels - 1, max(0, (int)(u * levels)));
+            const float dt = -((float)G.x[k][0] * s0 + (float)G.x[k][1] * s1 + (float)G.x[k][2] * s2);
+            const float u = G.span[k] > 0.0 ? 0.5f * (dt / (float)G.span[k] + 1.0f) : 0.5f;
+            q[k] = (uint32_t)min(levels - 1, max(0, (int)(u * (float)levels)));
         }
         if (G.mode == kSortDelay3) {   // Morton interleave of the three quantised delays
             uint32_t key = 0;

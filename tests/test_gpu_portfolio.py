@@ -257,13 +257,14 @@ def test_three_member_portfolio_fp64_matches_oracle_step_by_step(G, orc, problem
     assert info["n_drawn"][2] > 0
 
 
-def test_gmm_only_portfolio_matches_oracle(G, orc):
-    """The Gaussian mixture alone (6 components): every draw is its own, ln p - ln p_s is
-    minus its log density, and it trains on every sample; four float64 iterations against
-    the oracle's GMM-only portfolio."""
+@pytest.mark.parametrize("Cg", [6, 16])
+def test_gmm_only_portfolio_matches_oracle(G, orc, Cg):
+    """The Gaussian mixture alone (6 components, and the largest count, 16): every draw is
+    its own, ln p - ln p_s is minus its log density, and it trains on every sample; four
+    float64 iterations against the oracle's GMM-only portfolio."""
     from oracle import portfolio as PF
     p = S.single_large_problem()
-    n, Cg = 20000, 6
+    n = 20000
     pf = PF.Portfolio(members=(False, False, True), w_init=(0, 0, 1), gmm_components=Cg, seed=29, d_min=p.d_min,
                       d_max=p.d_max)
     with G.ILE(p, precision=G.RIFT_FP64, max_samples=n, seed=29) as s:
