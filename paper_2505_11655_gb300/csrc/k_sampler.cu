@@ -674,31 +674,56 @@ __global__ void __launch_bounds__(256) hist_partial_kernel(SamplerDev S, const u
 }
 
 // Sum the partial histograms exactly (128-bit); P <- (1-eps) H / sum H + eps / B; rebuild C.
-__global__ void adapt_final_kernel(SamplerDev S, const uint64_t *__restrict__ partial, int nb)
+// One block per dimension: the bins' sums over the block partials are split across the
+// block's threads (integer sums, so the same H in any split), then one warp finishes.
+constexpr int kAdaptFinalThreads = 256;
+__global__ void __launch_bounds__(kAdaptFinalThreads) adapt_final_kernel(SamplerDev S,
+                                                                         const uint64_t *__restrict__ partial, int nb)
 {
-    const int B = S.B;
-    const int d = threadIdx.x >> 5, lane = threadIdx.x & 31;   // one warp per dimension
+    const int B = S.B, d = blockIdx.x;
     if (d >= 6 || (S.marg && d == 5))   // a marginalised distance keeps its masses
         return;
-    double tot = 0.0;
-    for (int b = lane; b < B; b += 32) {
+    __shared__ unsigned long long acc[3][kAdaptFinalThreads];
+    const int tpb = B < kAdaptFinalThreads ? kAdaptFinalThreads / B : 1;   // threads per bin
+    const int t = threadIdx.x, j = t % tpb, b0 = t / tpb, bstride = kAdaptFinalThreads / tpb;
+    for (int bb = 0; bb < B; bb += bstride) {
+        const int b = bb + b0;
+        const bool mine = b0 < bstride && b < B;
         // the low words are summed as two 32-bit halves (no carry chain between the
         // loads), then recombined exactly
         uint64_t l0 = 0, l1 = 0, hi = 0;
-#pragma unroll 8
-        for (int k = 0; k < nb; ++k) {
-            const uint64_t *q = partial + (size_t)k * 12 * B + 2 * (d * B + b);
-            const uint64_t lo = q[0];
-            l0 += lo & 0xffffffffull;
-            l1 += lo >> 32;
-            hi += q[1];
+        if (mine) {
+#pragma unroll 4
+            for (int k = j; k < nb; k += tpb) {
+                const uint64_t *q = partial + (size_t)k * 12 * B + 2 * (d * B + b);
+                const uint64_t lo = q[0];
+                l0 += lo & 0xffffffffull;
+                l1 += lo >> 32;
+                hi += q[1];
+            }
         }
-        const uint64_t a = l0 + (l1 << 32);
-        hi += (l1 >> 32) + (a < l0 ? 1u : 0u);
-        const double h = ldexp((double)hi, 64 - kFixShift) + ldexp((double)a, -kFixShift);
-        S.C[d * (B + 1) + b + 1] = h;   // stash H in the C slots while reducing
-        tot += h;
+        acc[0][t] = l0;
+        acc[1][t] = l1;
+        acc[2][t] = hi;
+        __syncthreads();
+        if (mine && j == 0) {
+            for (int u = 1; u < tpb; ++u) {
+                l0 += acc[0][t + u];
+                l1 += acc[1][t + u];
+                hi += acc[2][t + u];
+            }
+            const uint64_t a = l0 + (l1 << 32);
+            hi += (l1 >> 32) + (a < l0 ? 1u : 0u);
+            S.C[d * (B + 1) + b + 1] = ldexp((double)hi, 64 - kFixShift) + ldexp((double)a, -kFixShift);   // H
+        }
+        __syncthreads();
     }
+    if (t >= 32)
+        return;
+    const int lane = t;
+    double tot = 0.0;
+    for (int b = lane; b < B; b += 32)
+        tot += S.C[d * (B + 1) + b + 1];   // H stashed in the C slots while reducing
 #pragma unroll
     for (int o = 16; o; o >>= 1)
         tot += __shfl_xor_sync(0xffffffffu, tot, o);
@@ -737,7 +762,7 @@ cudaError_t launch_adapt(const SamplerDev &S, const uint64_t *bins, const double
             return e;
     }
     hist_partial_kernel<<<nb, 256, smem, st>>>(S, bins, lnw, n, stats, slot, hist_partial, f32_terms);
-    adapt_final_kernel<<<1, 6 * 32, 0, st>>>(S, hist_partial, nb);
+    adapt_final_kernel<<<6, kAdaptFinalThreads, 0, st>>>(S, hist_partial, nb);
     return cudaGetLastError();
 }
 
