@@ -283,16 +283,17 @@ def test_gmm_only_portfolio_matches_oracle(G, orc, Cg):
             assert abs(r["lnZ"] - own["lnZ"]) <= 1e-9 * max(1.0, abs(own["lnZ"])), g
 
 
-def test_three_member_portfolio_fp32_meets_oracle_on_its_draws(G, orc):
-    """Five float32 iterations of the three-member portfolio on the single large problem:
-    weights normalised and above 0.05/3, every member draws, the mixture's parameters
-    stay in range, and the last iteration's ln L and ln Z on the device's own draws are
-    within 1e-3 of the oracle's float64 values."""
+@pytest.mark.parametrize("Cg", [4, 16])
+def test_three_member_portfolio_fp32_meets_oracle_on_its_draws(G, orc, Cg):
+    """Five float32 iterations of the three-member portfolio on the single large problem
+    (4 and 16 mixture components): weights normalised and above 0.05/3, every member draws,
+    the mixture's parameters stay in range, and the last iteration's ln L and ln Z on the
+    device's own draws are within 1e-3 of the oracle's float64 values."""
     p = S.single_large_problem()
     n = 30000
     with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, seed=17) as s:
         for g in range(5):
-            r = s.portfolio(1, n, members=7, p_thr=0.999, n_min_star=500, restart=(g == 0))
+            r = s.portfolio(1, n, members=7, gmm_components=Cg, p_thr=0.999, n_min_star=500, restart=(g == 0))
             info = s.portfolio_info()
             assert abs(sum(info["W_next"]) - 1.0) < 1e-12 and min(info["W_next"]) >= 0.05 / 3 - 1e-15
             assert min(info["n_drawn"]) > 0 and sum(info["n_drawn"]) == n
