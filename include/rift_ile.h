@@ -351,7 +351,7 @@ int rift_ile_portfolio_info(const rift_ile_t *h, rift_portfolio_info *info);
 /* Member 2's state after the last portfolio iteration (its training included): weights
  * pi [C], means mu [C][6] and widths sig [C][6] in prior-CDF coordinates, host buffers of
  * `capacity` components (outputs may be NULL), C in *n_components (may be NULL).
- * RIFT_ESTATE before a portfolio call with the GMM member since the handle was made;
+ * RIFT_ESTATE when no portfolio call since the last restart had the GMM member;
  * RIFT_EINVAL for capacity < C. */
 int rift_ile_portfolio_gmm(const rift_ile_t *h, int32_t capacity, int32_t *n_components, double *pi, double *mu,
                            double *sig);

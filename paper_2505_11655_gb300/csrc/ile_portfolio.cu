@@ -573,6 +573,8 @@ int pf_restart(rift_ile_t *h, bool with_av, int gmm_components)
         RK(av_restart(h));
     if (gmm_components > 0)
         gmm_init(p, gmm_components);
+    else
+        p.gmm_C = 0;   // no mixture member since this restart
     return RIFT_OK;
 }
 

@@ -164,6 +164,12 @@ def test_portfolio_arguments(G):
         with pytest.raises(G.RiftError) as e:
             s.portfolio_gmm()   # no GMM member yet
         assert e.value.code == G.RIFT_ESTATE
+        s.portfolio(1, 1000, capacity=4000, members=7, restart=True)
+        assert s.portfolio_gmm()[0].shape == (4,)
+        s.portfolio(1, 1000, capacity=4000, restart=True)   # restarted without the mixture
+        with pytest.raises(G.RiftError) as e:
+            s.portfolio_gmm()
+        assert e.value.code == G.RIFT_ESTATE
     pd = S.plain_fp64_problem()
     with G.ILE(pd, precision=G.RIFT_FP64, max_samples=1000, seed=1, distance_marg=True) as s:
         with pytest.raises(G.RiftError) as e:
