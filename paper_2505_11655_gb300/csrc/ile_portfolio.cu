@@ -282,8 +282,9 @@ __global__ void member_sums_final_kernel(const double *__restrict__ partial, int
 // tiles of kPfThreads: each thread turns one sample into omega_i r_ic (omega_i =
 // exp(ln w_i - max ln w), 0 for a non-finite ln w; r_ic = pi_c g_c / sum_c pi_c g_c), then
 // thread j < 13 C owns the sum (c, k) = (j / 13, j % 13) of omega r times 1, v_d (k = 1..6)
-// or v_d^2 (k = 7..12) and adds the tile's samples to it in index order.
-// partial[blk][13 C].
+// or v_d^2 (k = 7..12) and adds the tile's samples to it in index order.  In the float32
+// modes the sums are of (v_d - mu_cd) and (v_d - mu_cd)^2 about the component's current
+// mean, per tile in float32 and across tiles in float64.  partial[blk][13 C].
 template <bool kF32>
 __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double *__restrict__ tab, int C,
                                                                     const double *__restrict__ v,
@@ -295,6 +296,9 @@ __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double
     double *sT = sm;                         // [kGmmTab]
     double *sV = sT + kGmmTab;               // [kPfThreads][6]
     double *sW = sV + 6 * kPfThreads;        // [kPfThreads][C]
+    // the float32 modes: v as float32 pairs and the weights as float32 in the same bytes
+    float *sVh = reinterpret_cast<float *>(sV), *sVl = sVh + 6 * kPfThreads;
+    float *sWf = reinterpret_cast<float *>(sW);
     for (int e = threadIdx.x; e < kGmmTab; e += blockDim.x)
         sT[e] = tab[e];
     const double mx = stats[8 * slot + 4];   // max ln w of the batch (finite entries)
@@ -313,7 +317,8 @@ __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
                 vi[d] = v[6 * i + d];
-                vs[d] = vi[d];
+                if (!kF32)
+                    vs[d] = vi[d];
             }
             const double x = lnw[i];
             if (kF32) {
@@ -322,18 +327,24 @@ __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double
                 const float om = isfinite(x) ? __expf((float)(x - mx)) : 0.f;
                 float vh[6], vl[6];
                 gmm_split(vi, vh, vl);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    sVh[6 * threadIdx.x + d] = vh[d];
+                    sVl[6 * threadIdx.x + d] = vl[d];
+                }
                 float lmax = -INFINITY;
                 for (int c = 0; c < C; ++c)
                     lmax = fmaxf(lmax, gmm_ln_comp_f32(sT, c, vh, vl));
                 float tot = 0.f;
+                float *wf = sWf + threadIdx.x * C;
                 for (int c = 0; c < C; ++c) {
                     const float e = __expf(gmm_ln_comp_f32(sT, c, vh, vl) - lmax);
-                    w[c] = (double)e;
+                    wf[c] = e;
                     tot += e;
                 }
-                const double f = (double)(om / tot);
+                const float f = om / tot;
                 for (int c = 0; c < C; ++c)
-                    w[c] *= f;
+                    wf[c] *= f;
             } else {
                 const double om = isfinite(x) ? exp(x - mx) : 0.0;
                 double lmax = -INFINITY;
@@ -352,7 +363,24 @@ __global__ void __launch_bounds__(kPfThreads) gmm_em_partial_kernel(const double
             }
         }
         __syncthreads();
-        if (j < n_sums) {
+        if (kF32 && j < n_sums) {
+            // float32 sums over the tile of the moments about the component's current mean
+            // (no cancellation for a narrow component), added to the float64 total
+            const int cnt = (int)min((int64_t)kPfThreads, b1 - t0);
+            float a = 0.f;
+            if (jk == 0) {
+                for (int q = 0; q < cnt; ++q)
+                    a += sWf[q * C + jc];
+            } else {
+                const int dd = jk <= 6 ? jk - 1 : jk - 7, e = 6 * jc + dd;
+                const float mh = gmm_muhf(sT)[e], ml = gmm_mulf(sT)[e];
+                for (int q = 0; q < cnt; ++q) {
+                    const float z = (sVh[6 * q + dd] - mh) + (sVl[6 * q + dd] - ml);
+                    a = fmaf(sWf[q * C + jc], jk <= 6 ? z : z * z, a);
+                }
+            }
+            acc += (double)a;
+        } else if (j < n_sums) {
             const int cnt = (int)min((int64_t)kPfThreads, b1 - t0);
             if (jk == 0) {
                 for (int q = 0; q < cnt; ++q)
@@ -511,8 +539,9 @@ void gmm_table(rift_ile_t::PortfolioState &p)
     }
 }
 
-// One weighted EM step from the sums [C][13] (S_c, sum omega r v_d, sum omega r v_d^2).
-void gmm_em_apply(rift_ile_t::PortfolioState &p, const double *sums)
+// One weighted EM step from the sums [C][13] (S_c, sum omega r v_d, sum omega r v_d^2;
+// shifted: the last two about the component's current mean).
+void gmm_em_apply(rift_ile_t::PortfolioState &p, const double *sums, bool shifted)
 {
     const int C = p.gmm_C;
     double S = 0.0;
@@ -527,7 +556,13 @@ void gmm_em_apply(rift_ile_t::PortfolioState &p, const double *sums)
         for (int d = 0; d < 6; ++d) {
             const int e = 6 * c + d;
             double mu = p.gmm_mu[e], var = p.gmm_sig[e] * p.gmm_sig[e];
-            if (live) {
+            if (live && shifted) {
+                // the table's float32 pair of the mean, about which the sums were taken
+                const double m0 = (double)gmm_muhf(p.gmm_tab_host.data())[e] + (double)gmm_mulf(p.gmm_tab_host.data())[e];
+                const double dm = q[1 + d] / Sc;
+                mu = m0 + dm;
+                var = q[7 + d] / Sc - dm * dm;
+            } else if (live) {
                 mu = q[1 + d] / Sc;
                 var = q[7 + d] / Sc - mu * mu;
             }
@@ -692,7 +727,7 @@ int portfolio_iteration(rift_ile_t *h, int64_t n, int slot, bool reset_pooled, c
         }
     }
     if (!frozen[2])
-        gmm_em_apply(p, sums + kSumsGmm);
+        gmm_em_apply(p, sums + kSumsGmm, f32);
     CK(mark(h, slot, 3));
     for (int m = 0; m < kNMembers; ++m) {
         p.W_last[m] = W[m];
