@@ -62,6 +62,7 @@ TRAFFIC_BY_SOURCE = {
     "3e98ac2b2f6e30de16cf5dde8c8e0c1c184a69bbe778eea4e7a9c189816e4061": 5.98e7,
     "02d8362c4117749bf193a68eea6c4ee9c70af5751d9d82631086b1437d6f8777": 5.97e7,
     "a1a0f3fa500f237d67cded3cf3f47eaac17dae8af6c99f541d525a7f85a14ff1": 6.03e7,
+    "70258efe81120ca38cdd3f22b5ffc4ac29c4003ba3fdf3b4467adb6ac9f57fc1": 5.97e7,
 }
 
 
