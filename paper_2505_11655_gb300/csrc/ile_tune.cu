@@ -3,9 +3,9 @@
 // Which tile kernel wins (128-sample tensor-core tiles or 64-sample CUDA-core tiles)
 // and how densely the sky sort fills its Hilbert cells depend on the problem class:
 // the detector count, the mode count (padded to the 16-wide MMA K step), the time
-// grid, the Q length and the batch size, and on how far the sampler has adapted (the
-// samples of an adapted sampler crowd into fewer sky cells and delays, which changes the
-// best sort).  The first batch of a class times every candidate plan on samples drawn
+// grid, the Q length, the batch size and whether the distance is marginalised, and on how
+// far the sampler has adapted (the samples of an adapted sampler crowd into fewer sky
+// cells and delays, which changes the best sort).  The first batch of a class times every candidate plan on samples drawn
 // from the sampler (keys + sort + likelihood, best of two runs) and the winner is cached
 // for the process.  A handle whose sampler has adapted twice or more, on a batch of 2^19
 // samples or more, looks up a second class whose tensor-core plans (sky-cell fill, sort
@@ -88,6 +88,8 @@ std::string class_key(const rift_ile_t *h, int64_t n)
     const int nb = (int)std::floor(std::log2((double)n) / 2.0);   // batch size in factors of 4
     std::ostringstream s;
     s << "K" << h->prob.K << "_kp" << kp << "_nt" << h->prob.n_t << "_nq" << h->prob.n_q << "_n4^" << nb;
+    if (h->prob.dist_marg)   // the distance-marginalised instance is a kernel of its own
+        s << "_dm";
     return s.str();
 }
 

@@ -53,19 +53,6 @@ __device__ __forceinline__ float ex2_approx(float x)
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
-// float32 <-> unsigned integers ordered like the floats (for an atomic maximum); 0 encodes
-// no value (below the encoding of -inf)
-__device__ __forceinline__ unsigned int dm_enc(float x)
-{
-    const unsigned int u = __float_as_uint(x);
-    return u ^ ((unsigned int)((int)u >> 31) | 0x80000000u);
-}
-__device__ __forceinline__ float dm_dec(unsigned int e)
-{
-    if (e == 0u)
-        return -INFINITY;
-    return __uint_as_float((e & 0x80000000u) ? (e ^ 0x80000000u) : ~e);
-}
 // A tile whose samples span more than this many Q samples at some detector is cut
 // into contiguous sub-groups (compact along the sort order) that are windowed apart.
 constexpr int kTcSpreadLimit = 64;
@@ -301,9 +288,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
     // word) and the first bin of the block of bins holding it (NT - bin, low word, so that
     // the lowest bin wins among equals), by one 64-bit shared atomic max per chunk and thread
     unsigned long long *peak = reinterpret_cast<unsigned long long *>(lse + 2 * kTcQ * kTcS);
-    // with the distance marginal (no peak output) the same bytes hold [2][kTcS] running
-    // maxima, encoded as ordered integers (0: none), reset with the peaks
-    unsigned int *dmx = reinterpret_cast<unsigned int *>(peak);
     float *qsum = lse;                                          // [kTcQ][kTcS] template term partials
     float2 *Ys = reinterpret_cast<float2 *>(Rs);               // [M][kTcS] -2Y_lm(iota, -phi)
     __shared__ int lo_s[kMaxDet], hi_s[kMaxDet];        // current sub-group's offset range
@@ -672,16 +656,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
             auto win0 = [&](int k, int j0) {
                 return min(max(glo[grp][k] + bins[j0].x, 0), 8 * (P.tc_groups - 16)) & ~7;
             };
-            // First bin of the i-th chunk in processing order.  With the distance marginal the
-            // chunks run from the middle of the time grid outward (c0, c0 + 1, c0 - 1, c0 + 2,
-            // ..., c0 = (n - 1) / 2): a bin is left out when its bound lies 40 below the best
-            // value known for the sample, and the likelihood's peak in time is usually near
-            // the middle of the grid, so it is met early.  Otherwise in time order.
-            auto chunk_j0 = [&](int i) {
-                const int c0 = (n_chunks - 1) >> 1;
-                const int c = !kDM ? i : i == 0 ? c0 : (i & 1) ? c0 + ((i + 1) >> 1) : c0 - (i >> 1);
-                return c * jnom;
-            };
 
             if (warp == kTcIssuerWarp) {
                 // ============ issuer warp, lane 0: one MMA batch per staged window
@@ -731,7 +705,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             failed = 1;
                             break;
                         }
-                        const int g0 = win0(sk, chunk_j0(sch)) >> 3;
+                        const int g0 = win0(sk, sch * jnom) >> 3;
                         const __half *src = P.Qtc + ((size_t)sk * 2 * P.tc_groups + g0) * (size_t)kp * 8;
                         __half *dst = Bs + (size_t)b * 2 * part_halves;
                         tc::mbar_expect_tx(bbar + b, 2 * part_bytes);
@@ -758,7 +732,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     bfj[i] = 0.f;
                     bj[i] = 0;
                 }
-                for (int t = 0, k = 0, ci = 0, j0 = chunk_j0(0); t < n_steps; ++t) {
+                for (int t = 0, k = 0, j0 = 0; t < n_steps; ++t) {
                     const int b = t & 1, J = min(jnom, NT - j0);
                     const int jq = (J + kTcQ - 1) / kTcQ;                 // bins per quarter
                     const int jb = j0 + gh * jq, jn = max(0, min(jq, j0 + J - jb));   // this thread's bins
@@ -839,107 +813,25 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             // distance marginal per bin: a cheap upper bound first; the bin
                             // with the highest bound is evaluated, and a bin whose bound lies
                             // more than 40 below the larger of that value and the running
-                            // maximum cannot move the marginal (< e^-40): left out.  (The
-                            // bound is recomputed rather than kept: it is a handful of
-                            // operations, a register array of it is not.)
+                            // maximum cannot move the marginal (< e^-40): left out
+                            // (the bound is recomputed in the second loop rather than kept: it is
+                            // a handful of operations, a register array of it is not)
                             float bmax = -INFINITY, abest = 0.f;
-                            int ibest = 0;
 #pragma unroll
                             for (int i = 0; i < kTcBPT; ++i) {
                                 const float bd = i < jn ? dm_bound32(P, lin[i], gqd) : -INFINITY;
                                 if (bd > bmax) {
                                     bmax = bd;
                                     abest = lin[i];
-                                    ibest = i;
                                 }
                             }
-                            // the best value known for the sample: this thread's running
-                            // maximum and the largest of its four bin quarters' after the
-                            // previous chunk (atomicMax into a slot per chunk parity: the
-                            // quarter barriers of the steps between order every write before
-                            // the reads, and the next write to the same slot after them)
-                            const float shared = ci > 0 ? dm_dec(dmx[((ci - 1) & 1) * kTcS + gs]) : -INFINITY;
-                            const float pre = fmaxf(run_mx, shared);
-                            // the best-bound bin, unless the chunk cannot matter; (every bin
-                            // exact when the per-bin values are written out)
-                            const float vbest = jn > 0 && (lnL_t || bmax >= pre - 40.f) ? ln_dist_marg32(P, abest, gqd)
-                                                                                        : -INFINITY;
-                            const float thr = lnL_t ? -INFINITY : fmaxf(pre, vbest) - 40.f;
-                            uint32_t need = 0u;   // the other bins to evaluate (this sample's)
-#pragma unroll
-                            for (int i = 0; i < kTcBPT; ++i)
-                                if (in_grp && i < jn && i != ibest && dm_bound32(P, lin[i], gqd) >= thr)
-                                    need |= 1u << i;
-                            // The needed (sample, bin) pairs differ from lane to lane, so they
-                            // are compacted across the warp and evaluated 32 at a time instead
-                            // of bin by bin (where a bin costs the warp whenever one lane needs
-                            // it).  Scratch: this warp's own 32 x 32 block of the other R tile
-                            // (the columns it drains into at the next step; the quarter's
-                            // gathers finished reading that tile before this step's barrier):
-                            // item k (bin-major, then lane) at row k / 32, lane k % 32; rows
-                            // 16, 17 hold each bin's lane mask and first item.
-                            float *scr = ((t & 1) ? Rs : Rs2) + (32 * (warp >> 2)) * kTcS + 32 * (warp & 3);
-                            const uint32_t lt = (1u << lane) - 1u;
-                            int nitem = 0;
-                            uint32_t my_mask = 0u;
-                            int my_first = 0;
+                            const float vbest = jn > 0 ? ln_dist_marg32(P, abest, gqd) : -INFINITY;
+                            // (every bin exact when the per-bin values are written out)
+                            const float thr = lnL_t ? -INFINITY : fmaxf(run_mx, vbest) - 40.f;
 #pragma unroll
                             for (int i = 0; i < kTcBPT; ++i) {
-                                const bool nd = (need >> i) & 1u;
-                                const uint32_t bm = __ballot_sync(0xffffffffu, nd);
-                                if (nd) {
-                                    const int kk = nitem + __popc(bm & lt);
-                                    scr[(kk >> 5) * kTcS + (kk & 31)] = lin[i];
-                                }
-                                if (lane == i) {
-                                    my_mask = bm;
-                                    my_first = nitem;
-                                }
-                                nitem += __popc(bm);
-                            }
-                            scr[16 * kTcS + lane] = __uint_as_float(my_mask);
-                            scr[17 * kTcS + lane] = __int_as_float(my_first);
-                            __syncwarp();
-                            // items two per lane at a time (two independent quadratures in flight)
-                            auto item_in = [&](int kk, float &a, float &bq) {
-                                // its bin: the last of the 16 whose first item is <= kk (a bin
-                                // without items shares the next bin's first item)
-                                int ii = 0;
-#pragma unroll
-                                for (int st = 8; st > 0; st >>= 1)
-                                    if (__float_as_int(scr[17 * kTcS + ii + st]) <= kk)
-                                        ii += st;
-                                const uint32_t bm = __float_as_uint(scr[16 * kTcS + ii]);
-                                const int rk = kk - __float_as_int(scr[17 * kTcS + ii]);
-                                const int owner = kk < nitem ? (int)__fns(bm, 0u, rk + 1) : 0;
-                                bq = __shfl_sync(0xffffffffu, gqd, owner & 31);
-                                a = kk < nitem ? scr[(kk >> 5) * kTcS + (kk & 31)] : 0.f;
-                            };
-                            for (int k0 = 0; k0 < nitem; k0 += 64) {
-                                const int ka = k0 + lane, kb = k0 + 32 + lane;
-                                float aa, ba, ab, bb;
-                                item_in(ka, aa, ba);
-                                item_in(kb, ab, bb);
-                                const float va = ln_dist_marg32(P, aa, ba);
-                                const float vb = ln_dist_marg32(P, ab, bb);
-                                if (ka < nitem)
-                                    scr[(ka >> 5) * kTcS + (ka & 31)] = va;
-                                if (kb < nitem)
-                                    scr[(kb >> 5) * kTcS + (kb & 31)] = vb;
-                            }
-                            __syncwarp();
-                            nitem = 0;
-#pragma unroll
-                            for (int i = 0; i < kTcBPT; ++i) {
-                                const bool nd = (need >> i) & 1u;
-                                const uint32_t bm = __ballot_sync(0xffffffffu, nd);
-                                float val = (i == ibest && jn > 0 && bmax >= thr) ? vbest : -INFINITY;
-                                if (nd) {
-                                    const int kk = nitem + __popc(bm & lt);
-                                    val = scr[(kk >> 5) * kTcS + (kk & 31)];
-                                }
-                                nitem += __popc(bm);
-                                lin[i] = i < jn ? val : -INFINITY;
+                                lin[i] = (i < jn && dm_bound32(P, lin[i], gqd) >= thr) ? ln_dist_marg32(P, lin[i], gqd)
+                                                                                      : -INFINITY;
                                 if (i < jn)
                                     cmx = fmaxf(cmx, lin[i]);
                             }
@@ -976,7 +868,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                                         lnL_t[(lnl_t_compact ? (int64_t)tile_s * kTcS + gs : (int64_t)gid[gs]) * NT + jb + i] =
                                             kDM ? (double)lin[u] : (double)lin[u] - (double)gqd;
                         }
-                        if (jn > 0 && in_grp && cmx != -INFINITY) {
+                        if (jn > 0 && in_grp) {
                             const float nm = fmaxf(run_mx, cmx);
                             float cs = 0.f;
                             if (kDM) {
@@ -1001,8 +893,6 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                             }
                             run_sum = (run_mx == -INFINITY ? 0.f : run_sum * __expf(run_mx - nm)) + cs;
                             run_mx = nm;
-                            if (kDM)
-                                atomicMax(dmx + (ci & 1) * kTcS + gs, dm_enc(nm));
                         }
 #pragma unroll
                         for (int i = 0; i < kTcBPT; ++i)
@@ -1010,7 +900,7 @@ lnl_tc_kernel(Problem P, BinTable bt, const double *__restrict__ theta, const ui
                     }
                     if (++k == K) {
                         k = 0;
-                        j0 = chunk_j0(++ci);
+                        j0 += jnom;
                     }
                 }
             }
