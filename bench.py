@@ -383,7 +383,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.quick:
         with G.ILE(prob, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=1 + rank, stream=stream,
                    distance_marg=True) as sdm:
-            for _ in range(2):
+            for _ in range(3):   # warm-up, including the adapted class's plan timing (third iteration)
                 sdm.adapt(1, n)
             dms, dml = [], []
             for _ in range(3):
