@@ -2,7 +2,7 @@
 
 The oracle integrates x^-4 exp(a x - b x^2) by 200 panels of 16-point Gauss-Legendre
 (pinned to scipy's adaptive quadrature and to a brute-force distance grid); the device
-uses 4 panels of 16 nodes in float64 and 3 of 8 in float32 over the same closed-form
+uses 4 panels of 16 nodes in float64 and 2 of 10 in float32 over the same closed-form
 support, whose quadrature error is below 1e-10 and 1e-5 in ln of the integral.
 """
 import numpy as np
@@ -107,3 +107,22 @@ def test_refusals(G):
         with pytest.raises(G.RiftError) as e:
             s.av(1, 1000)
         assert e.value.code == G.RIFT_EINVAL
+
+
+@pytest.mark.slow
+def test_full_size_sampled_against_oracle(G, orc):
+    """The bench's configuration: 1e6 samples per iteration, float32, after three adaptive
+    iterations; the 100 samples of largest ln w and 300 others at random, each against the
+    oracle's own quadrature, to the float32 bar."""
+    p = S.single_large_problem()
+    n = 1_000_000
+    with G.ILE(p, precision=G.RIFT_FP32, max_samples=n, n_bins=64, seed=1, distance_marg=True) as s:
+        for _ in range(4):
+            r = s.adapt(1, n)
+            assert r["status"] == 0
+        th, lr, ll, lw = s.last_batch(n)
+    heavy = np.argsort(lw)[-100:]
+    rest = np.random.default_rng(7).choice(n, 300, replace=False)
+    idx = np.unique(np.concatenate([heavy, rest]))
+    exp, _, _ = oracle_marg(orc, p, th[idx])
+    close32(ll[idx], exp)
